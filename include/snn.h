@@ -1,0 +1,226 @@
+/*
+ * snn.h -- C-ABI of the GB300 spiking-network library.
+ *
+ * The library advances a conductance-based Hodgkin-Huxley network in time
+ * steps of dt (Sec. 2 of Balaji, Yavuz, Nowotny, "Scalability and
+ * optimization strategies for GPU enhanced neural networks"): every step
+ * updates each neuron's membrane potential and Na/K gating variables, detects
+ * threshold crossings into an ascending spike list, and delivers those spikes
+ * over compressed-row connectivity (Sec. 3) whose conductances are scaled per
+ * projection by gScale = k1 / (k2 + nConn) + k3 (Sec. 5.1, Tables 1 and 2).
+ *
+ * Conventions for every entry point:
+ *   - Units: mV, ms, nS, pF, pA, Hz.
+ *   - Pointers are plain host or device pointers; a flag next to each array
+ *     says which.  The library never keeps a caller pointer past the call:
+ *     inputs are deep-copied.
+ *   - `stream` is a cudaStream_t (NULL = the legacy default stream).  Calls
+ *     that only enqueue GPU work return before it finishes.
+ *   - Every call returns an snn_status; SNN_OK is 0.  On any other value,
+ *     snn_last_error() returns a message for the calling thread.  No C++
+ *     exception crosses this boundary.
+ *   - Ownership: an snn_net owns its device memory, obtained from the
+ *     allocator given at creation (cudaMalloc when NULL) and released by
+ *     snn_destroy.
+ *   - Device-side failures (a bounded wait that ran out, a malformed input
+ *     found on the GPU) set a sticky error word; the next call that
+ *     synchronises (snn_read_state, snn_sync) returns it.
+ */
+#ifndef SNN_H
+#define SNN_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum snn_status {
+    SNN_OK = 0,
+    SNN_ERR_INVALID_ARG = 1, /* a size, index, flag or pointer is invalid */
+    SNN_ERR_CSR = 2,         /* row starts not monotone, post index out of range or not ascending */
+    SNN_ERR_GSCALE = 3,      /* nConn + k2 <= 0: the scaling law has no value (Sec. 5.1) */
+    SNN_ERR_OOM = 4,         /* the allocator returned NULL */
+    SNN_ERR_CUDA = 5,        /* a CUDA runtime call failed */
+    SNN_ERR_TIMEOUT = 6,     /* a bounded device-side wait ran out */
+    SNN_ERR_STATE = 7,       /* the call needs state the network does not have */
+    SNN_ERR_SIZE = 8         /* a destination buffer is too small */
+} snn_status;
+
+enum { SNN_POP_HH = 0, SNN_POP_SOURCE = 1 };
+enum { SNN_LAYOUT_CSR = 0, SNN_LAYOUT_DENSE = 1 };
+enum { SNN_SYN_EXP = 0, SNN_SYN_GRADED = 1 };
+
+/* State fields for snn_read_state / snn_write_state. */
+enum {
+    SNN_FIELD_V = 0,           /* float[n], membrane potential (mV) */
+    SNN_FIELD_M = 1,           /* float[n], Na activation */
+    SNN_FIELD_H = 2,           /* float[n], Na inactivation */
+    SNN_FIELD_N = 3,           /* float[n], K activation */
+    SNN_FIELD_G0 = 4,          /* float[n], conductance of channel 0 (nS) */
+    SNN_FIELD_G1 = 5,          /* float[n], conductance of channel 1 (nS) */
+    SNN_FIELD_IEXT = 6,        /* float[n], drive current (pA) */
+    SNN_FIELD_ISYN = 7,        /* float[n], synaptic current of the last step (pA); needs SNN_OPT_RECORD_ISYN */
+    SNN_FIELD_SPIKES = 8,      /* int32[nspk], ascending spike list of the last step (read only) */
+    SNN_FIELD_NSPK = 9,        /* int32, length of that list (read only) */
+    SNN_FIELD_SPIKE_COUNT = 10,/* int64, spikes since creation or reset (Fig. 1 avgSpike numerator) */
+    SNN_FIELD_NAN_COUNT = 11   /* int64, neuron-steps that ended with a NaN V (Fig. 1 sumNANs) */
+};
+
+/* Options for snn_set_option. */
+enum {
+    SNN_OPT_RECORD_ISYN = 0,   /* 1: store I_syn of every step (for checking); default 0 */
+    SNN_OPT_GRAPH_STEPS = 1,   /* steps per captured CUDA graph, 0 = no graph; default 100 */
+    SNN_OPT_PROP_BLOCKS = 2,   /* CTAs of the propagation kernels; 0 = library choice */
+    SNN_OPT_CHUNK = 3,         /* synapses per warp work item of the row kernel (multiple of 128) */
+    SNN_OPT_SPIN_LIMIT = 4     /* iterations of a bounded device wait before SNN_ERR_TIMEOUT */
+};
+
+/* A population.  kind SNN_POP_HH: Traub-Miles HH neurons with the given
+ * conductances; kind SNN_POP_SOURCE: Poisson spike sources at src_rate_hz. */
+typedef struct snn_pop_desc {
+    int32_t kind;
+    int32_t n;                 /* neurons, 0 <= n < 2^30 */
+    double C, gNa, ENa, gK, EK, gL, EL;  /* pF, nS, mV (HH only) */
+    double E_syn[2];           /* reversal potential of conductance channel 0 / 1 (mV) */
+    double tau_syn[2];         /* decay time constant of channel 0 / 1 (ms); <= 0 clears each step */
+    double v_thresh;           /* spike threshold (mV): V(t) < v_thresh <= V(t+dt) */
+    double src_rate_hz;        /* SNN_POP_SOURCE rate */
+    double drive_rate_hz;      /* HH: Bernoulli(rate*dt) drive events per step; 0 = no drive */
+    double drive_amp;          /* pA added to I_ext by each drive event */
+    double drive_tau;          /* ms, decay of I_ext */
+    const float* v0;           /* n initial potentials; NULL = EL.  Gating starts at steady state. */
+    int32_t v0_on_device;      /* 1 if v0 is a device pointer */
+    int32_t reserved;
+} snn_pop_desc;
+
+/* A projection from population `pre` to `post`.  Input connectivity is either
+ * compressed rows (Sec. 3: row_ptr[n_pre+1] int64, col[nnz] int32 post
+ * indices ascending within each row, w[nnz] float weights in nS) or, with
+ * input_dense = 1, a row-major n_pre x n_post weight matrix in w.  `layout`
+ * is the storage the library keeps and propagates from (Eq. 1 vs Eq. 2).
+ * Conductance scale s = (k1 / (k2 + nConn) + k3) * user_scale, computed in
+ * FP64 and rounded to FP32; nConn = n_conn if > 0, else density * n_pre. */
+typedef struct snn_proj_desc {
+    int32_t pre, post;
+    int32_t layout;            /* SNN_LAYOUT_CSR or SNN_LAYOUT_DENSE */
+    int32_t channel;           /* post conductance channel 0 or 1 */
+    int32_t synapse;           /* SNN_SYN_EXP (spiking) or SNN_SYN_GRADED */
+    int32_t on_device;         /* 1 if row_ptr, col, w are device pointers */
+    int32_t input_dense;       /* 1 if w is a dense n_pre x n_post matrix */
+    int32_t reserved;
+    int64_t nnz;
+    const int64_t* row_ptr;
+    const int32_t* col;
+    const float* w;
+    double k1, k2, k3;         /* scaling law constants */
+    double density;            /* p */
+    double n_conn;             /* explicit nConn, or <= 0 to use density * n_pre */
+    double user_scale;         /* extra factor c */
+    double v_thr, v_slope;     /* graded release 1 / (1 + exp((v_thr - V_pre) / v_slope)) */
+} snn_proj_desc;
+
+/* Device memory provider.  alloc returns a device pointer of at least
+ * `bytes` (aligned to 256 B) usable on `stream`, or NULL; free releases it. */
+typedef struct snn_allocator {
+    void* (*alloc)(size_t bytes, void* stream, void* ctx);
+    void (*free)(void* ptr, void* stream, void* ctx);
+    void* ctx;
+} snn_allocator;
+
+typedef struct snn_net snn_net;
+
+/* Creates a network (Sec. 2 model, Sec. 3 storage, Sec. 5.1 scaling).
+ * Copies every input array, validates connectivity on the GPU
+ * (SNN_ERR_CSR), computes each projection's scale (SNN_ERR_GSCALE at the
+ * law's pole), initialises V from v0 and m, h, n at their steady state, and
+ * zeroes conductances, drive currents and counters.  Synchronises `stream`.
+ * `rng_instance` (< 2^24) is folded into every random-number counter so that
+ * instance b of a batch reproduces a stand-alone network created with b.
+ * At most 4096 populations and 4096 projections. */
+snn_status snn_create_network(const snn_pop_desc* pops, int32_t n_pops,
+                              const snn_proj_desc* projs, int32_t n_projs,
+                              double dt, int32_t n_substeps, uint64_t seed, uint32_t rng_instance,
+                              const snn_allocator* alloc, void* stream, snn_net** out);
+
+/* Releases the network and all its device memory (synchronises its streams). */
+snn_status snn_destroy(snn_net* net);
+
+/* Enqueues n_steps time steps on `stream`.  Each step: Poisson sources draw
+ * spikes; driven neurons draw drive events; I_syn = sum_c g_c (E_c - V);
+ * n_substeps forward-Euler substeps of V, m, h, n; upward threshold crossings
+ * are listed in ascending order; conductances and drive decay by
+ * exp(-dt / tau); each spike adds s * w to its targets' conductance (one-step
+ * delay).  Full blocks of SNN_OPT_GRAPH_STEPS steps replay a captured graph.
+ * Does not synchronise; returns a sticky device error seen earlier. */
+snn_status snn_step(snn_net* net, int64_t n_steps, void* stream);
+
+/* Waits for `stream` and returns any sticky device error (SNN_ERR_TIMEOUT,
+ * SNN_ERR_CSR). */
+snn_status snn_sync(snn_net* net, void* stream);
+
+/* Copies a state field of population `pop` into dst (host or device).
+ * `bytes` must cover the field (SNN_ERR_SIZE otherwise); for SNN_FIELD_SPIKES
+ * it must cover n * 4 bytes.  Synchronises `stream`. */
+snn_status snn_read_state(snn_net* net, int32_t pop, int32_t field, void* dst, size_t bytes,
+                          int32_t dst_is_device, void* stream);
+
+/* Overwrites a float state field (V, M, H, N, G0, G1, IEXT) of population
+ * `pop` from src (host or device), `bytes` = n * 4.  Synchronises `stream`. */
+snn_status snn_write_state(snn_net* net, int32_t pop, int32_t field, const void* src, size_t bytes,
+                           int32_t src_is_device, void* stream);
+
+/* Restores the state the network had at creation and sets the step counter
+ * (and hence the random-number counters) back to 0.  Enqueued on `stream`. */
+snn_status snn_reset(snn_net* net, void* stream);
+
+/* Sets an SNN_OPT_* option (see the enum). */
+snn_status snn_set_option(snn_net* net, int32_t option, int64_t value);
+
+/* Steps simulated since creation or the last reset (synchronises `stream`). */
+snn_status snn_get_step(snn_net* net, int64_t* step, void* stream);
+
+/* Conductance scale s of projection `proj` as the GPU uses it (FP32). */
+snn_status snn_proj_scale(snn_net* net, int32_t proj, float* scale);
+
+/* Number of synapses stored for projection `proj` (nnz; n_pre * n_post for dense). */
+snn_status snn_proj_nnz(snn_net* net, int32_t proj, int64_t* nnz);
+
+/* Runs the production propagation kernel of projection `proj` once on the
+ * given ascending spike list of its pre population (host or device, n
+ * entries), adding s * w to the post conductances.  For checking delivery
+ * against the dense product of Sec. 3's Eq. 2 storage.  Synchronises. */
+snn_status snn_debug_propagate(snn_net* net, int32_t proj, const int32_t* spk, int32_t n,
+                               int32_t spk_on_device, void* stream);
+
+/* Event list of a spike list over projection `proj` (compressed rows only):
+ * for each spike in list order, the (post index, weight) pairs of its row in
+ * storage order, written to device arrays post_out / w_out of `capacity`
+ * entries.  *n_events receives the total; SNN_ERR_SIZE if it exceeds
+ * capacity (nothing written).  Spikes are host or device.  Synchronises. */
+snn_status snn_event_list(snn_net* net, int32_t proj, const int32_t* spk, int32_t n,
+                          int32_t spk_on_device, int32_t* post_out, float* w_out,
+                          int64_t capacity, int64_t* n_events, void* stream);
+
+/* Compressed-row connectivity drawn on the GPU from a seed (Sec. 3 format):
+ * one Bernoulli(p) draw per (pre i, post j) pair, event when word (j mod 4)
+ * of Philox4x32-10(counter = (j / 4, i, tag, 3), key = seed) is below
+ * round(p * 2^32).  Pass 1 writes row_ptr[n_pre + 1] (device) and *nnz
+ * (host); pass 2 writes col[nnz] (device), ascending within each row.
+ * Scratch memory comes from `alloc` (cudaMalloc when NULL).  Synchronises
+ * `stream`.  n_pre, n_post < 2^31; 0 <= p <= 1. */
+snn_status snn_csr_bernoulli_rows(uint64_t seed, uint32_t tag, int64_t n_pre, int64_t n_post,
+                                  double p, int64_t* row_ptr, int64_t* nnz,
+                                  const snn_allocator* alloc, void* stream);
+snn_status snn_csr_bernoulli_fill(uint64_t seed, uint32_t tag, int64_t n_pre, int64_t n_post,
+                                  double p, const int64_t* row_ptr, int32_t* col, void* stream);
+
+/* Message of the last failed call on this thread ("" if none). */
+const char* snn_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SNN_H */

@@ -1,0 +1,106 @@
+// Device-side building blocks: the Philox4x32-10 counter-based generator,
+// FP32 Traub-Miles HH rates and one forward-Euler substep, and the
+// acquire/release accesses used by the bounded device-side waits.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace snn {
+
+// ---------------------------------------------------------------------------
+// Philox4x32-10 (Salmon et al., SC'11): ten rounds of two 32x32->64-bit
+// multiplies whose halves are cross-xored with the other two words and the
+// round key; the key advances by the golden-ratio / sqrt(3) Weyl increments.
+// ---------------------------------------------------------------------------
+struct PhiloxKey {
+    uint32_t k0, k1;
+};
+
+__device__ __forceinline__ uint4 philox_4x32_10(uint4 x, PhiloxKey key) {
+    constexpr uint32_t kMulA = 0xD2511F53u, kMulB = 0xCD9E8D57u;
+    constexpr uint32_t kWeylA = 0x9E3779B9u, kWeylB = 0xBB67AE85u;
+#pragma unroll
+    for (int round = 0; round < 10; ++round) {
+        const uint32_t a_hi = __umulhi(kMulA, x.x), a_lo = kMulA * x.x;
+        const uint32_t b_hi = __umulhi(kMulB, x.z), b_lo = kMulB * x.z;
+        x = make_uint4(b_hi ^ x.y ^ key.k0, b_lo, a_hi ^ x.w ^ key.k1, a_lo);
+        key.k0 += kWeylA;
+        key.k1 += kWeylB;
+    }
+    return x;
+}
+
+// Bernoulli event: the 32-bit draw is below the integer threshold round(p*2^32).
+__device__ __forceinline__ bool below(uint32_t u, unsigned long long thr) {
+    return (unsigned long long)u < thr;
+}
+
+// ---------------------------------------------------------------------------
+// Traub-Miles HH in FP32 (V in mV, t in ms, g in nS, C in pF, I in pA).
+// ---------------------------------------------------------------------------
+// x / (exp(x) - 1), continuous through x = 0 (removable singularity of the
+// linoid rates); the series 1 - x/2 + x^2/12 is exact to FP32 for |x| < 1e-3.
+__device__ __forceinline__ float linoid(float x) {
+    if (fabsf(x) < 1e-3f) return fmaf(x, fmaf(x, 1.0f / 12.0f, -0.5f), 1.0f);
+    return x / expm1f(x);
+}
+
+struct HHCell {
+    float gNa, ENa, gK, EK, gL, EL;
+};
+
+// One forward-Euler substep with every right-hand side at the substep start.
+__device__ __forceinline__ void hh_substep(const HHCell& c, float hs, float hs_over_C, float I_in,
+                                           float& V, float& m, float& h, float& n) {
+    const float am = 1.28f * linoid((-52.0f - V) * 0.25f);
+    const float bm = 1.4f * linoid((V + 25.0f) * 0.2f);
+    const float ah = 0.128f * expf((-48.0f - V) * (1.0f / 18.0f));
+    const float bh = 4.0f / (expf((-25.0f - V) * 0.2f) + 1.0f);
+    const float an = 0.16f * linoid((-50.0f - V) * 0.2f);
+    const float bn = 0.5f * expf((-55.0f - V) * 0.025f);
+    const float m3h = m * m * m * h;
+    const float n2 = n * n;
+    const float I = I_in - c.gNa * m3h * (V - c.ENa) - c.gK * (n2 * n2) * (V - c.EK) - c.gL * (V - c.EL);
+    const float dm = am * (1.0f - m) - bm * m;
+    const float dh = ah * (1.0f - h) - bh * h;
+    const float dn = an * (1.0f - n) - bn * n;
+    V = fmaf(hs_over_C, I, V);
+    m = fmaf(hs, dm, m);
+    h = fmaf(hs, dh, h);
+    n = fmaf(hs, dn, n);
+}
+
+// Steady-state gating alpha / (alpha + beta) at V.
+__device__ __forceinline__ void hh_steady(float V, float& m, float& h, float& n) {
+    const float am = 1.28f * linoid((-52.0f - V) * 0.25f);
+    const float bm = 1.4f * linoid((V + 25.0f) * 0.2f);
+    const float ah = 0.128f * expf((-48.0f - V) * (1.0f / 18.0f));
+    const float bh = 4.0f / (expf((-25.0f - V) * 0.2f) + 1.0f);
+    const float an = 0.16f * linoid((-50.0f - V) * 0.2f);
+    const float bn = 0.5f * expf((-55.0f - V) * 0.025f);
+    m = am / (am + bm);
+    h = ah / (ah + bh);
+    n = an / (an + bn);
+}
+
+// ---------------------------------------------------------------------------
+// Memory-model helpers for flags shared between CTAs.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ unsigned long long ld_acquire_u64(const unsigned long long* p) {
+    unsigned long long v;
+    asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+    return v;
+}
+
+__device__ __forceinline__ void st_release_u64(unsigned long long* p, unsigned long long v) {
+    asm volatile("st.release.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+
+__device__ __forceinline__ uint32_t ld_acquire_u32(const uint32_t* p) {
+    uint32_t v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+}  // namespace snn

@@ -1,0 +1,193 @@
+// Internal declarations of the GB300 spiking-network library: device-side
+// descriptors, the network object and the kernel launchers shared by the
+// translation units.  Not part of the public C-ABI (include/snn.h).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "snn.h"
+
+namespace snn {
+
+constexpr int kTile = 256;                 // neurons per compaction tile (one CTA)
+constexpr int kMaxPops = 4096;
+constexpr int kMaxProjs = 4096;
+
+// Sticky device error bits.
+constexpr uint32_t kDevErrTimeout = 1u;
+constexpr uint32_t kDevErrCsr = 2u;
+
+// Philox stream identifiers (counter word 3).
+constexpr uint32_t kStreamSource = 1u;
+constexpr uint32_t kStreamDrive = 2u;
+constexpr uint32_t kStreamCsr = 3u;
+
+// Tile status word of the ordered spike compaction:
+// [63:32] step epoch, [31:30] flag (1 = tile total, 2 = inclusive prefix), [29:0] count.
+constexpr unsigned long long kFlagAgg = 1ull << 30;
+constexpr unsigned long long kFlagPrefix = 2ull << 30;
+constexpr unsigned long long kCountMask = (1ull << 30) - 1;
+
+struct DevPop {
+    int32_t kind;          // SNN_POP_HH or SNN_POP_SOURCE
+    int32_t n;
+    int32_t offset;        // first index in the SoA state arrays (multiple of kTile)
+    int32_t first_tile;    // first compaction tile
+    int32_t n_tiles;
+    uint32_t tag;          // RNG tag (instance << 8 | population index mod 256 within instance)
+    float gNa, ENa, gK, EK, gL, EL;
+    float hs_over_C;       // substep length / C
+    float E0, E1;          // channel reversal potentials
+    float d0, d1;          // channel decay factors exp(-dt / tau)
+    float v_thresh;
+    float drive_amp, drive_dec;
+    unsigned long long thr_src;    // Bernoulli thresholds round(p * 2^32)
+    unsigned long long thr_drive;
+    int32_t* spk;          // spike list of the last step
+    int32_t* nspk;
+    unsigned long long* spike_count;
+    unsigned long long* nan_count;
+};
+
+struct DevProj {
+    int32_t layout;        // SNN_LAYOUT_CSR / SNN_LAYOUT_DENSE
+    int32_t n_pre, n_post;
+    int32_t chunks;        // work items per spiking row (CSR) or per row block (dense)
+    float scale;
+    const int64_t* row_ptr;
+    const int32_t* col;
+    const float* w;        // nnz (CSR) or n_pre * n_post (dense)
+    float* g;              // post conductance channel, already offset to the post population
+    const int32_t* spk;    // pre spike list
+    const int32_t* nspk;
+};
+
+struct NeuronArgs {
+    const DevPop* pops;
+    const int32_t* tile_pop;       // compaction tile -> population
+    float *V, *m, *h, *n, *g0, *g1, *iext;
+    float* isyn_rec;               // nullptr unless recording
+    unsigned long long* ticket;    // monotone tile ticket
+    unsigned long long* tile_status;
+    const unsigned long long* epoch_base;
+    uint32_t* error;
+    int32_t num_tiles;
+    int32_t n_sub;
+    float hs;                      // substep length dt / n_sub (ms)
+    uint32_t spin_limit;
+    uint32_t seed_lo, seed_hi;
+};
+
+struct PropArgs {
+    const DevProj* projs;
+    int32_t n_projs;
+    int32_t chunk;                 // synapses per CSR work item
+};
+
+// Memory obtained from the user allocator (or cudaMalloc).
+struct Alloc {
+    snn_allocator a{};
+    bool have = false;
+    void* stream = nullptr;
+    void* get(size_t bytes);
+    void put(void* p);
+};
+
+struct PopHost {
+    snn_pop_desc d;
+    int32_t offset, first_tile, n_tiles;
+};
+
+struct ProjHost {
+    snn_proj_desc d;
+    float scale;
+    int64_t nnz;
+    int32_t max_row;
+    int64_t* row_ptr = nullptr;
+    int32_t* col = nullptr;
+    float* w = nullptr;
+};
+
+}  // namespace snn
+
+struct snn_net {
+    snn::Alloc mem;
+    std::vector<void*> owned;
+    std::vector<snn::PopHost> pops;
+    std::vector<snn::ProjHost> projs;
+    double dt = 0.1;
+    int32_t n_sub = 4;
+    uint64_t seed = 0;
+    uint32_t instance = 0;
+    int32_t n_total = 0;           // padded SoA length
+    int32_t num_tiles = 0;
+    int sm_count = 148;
+    // device state
+    float *V = nullptr, *m = nullptr, *h = nullptr, *n = nullptr, *g0 = nullptr, *g1 = nullptr,
+          *iext = nullptr, *isyn = nullptr;
+    float* init_state = nullptr;   // 7 * n_total floats saved at creation
+    int32_t* spk = nullptr;
+    int32_t* nspk = nullptr;
+    unsigned long long* counters = nullptr;   // 2 * n_pops
+    unsigned long long* ticket = nullptr;     // [0] ticket, [1] epoch base
+    unsigned long long* tile_status = nullptr;
+    int32_t* tile_pop = nullptr;
+    uint32_t* error = nullptr;
+    snn::DevPop* d_pops = nullptr;
+    snn::DevProj* d_projs = nullptr;          // one descriptor per projection
+    snn::DevProj* d_dbg_proj = nullptr;       // one-projection scratch descriptor
+    int32_t* d_dbg_spk = nullptr;
+    int32_t dbg_cap = 0;
+    // options
+    bool record_isyn = false;
+    int64_t graph_steps = 100;
+    int32_t prop_blocks = 0;
+    int32_t chunk = 1024;
+    uint32_t spin_limit = 1u << 22;
+    // graph
+    cudaStream_t cap_stream = nullptr;
+    cudaGraphExec_t graph = nullptr;
+    int64_t graph_len = 0;
+};
+
+namespace snn {
+
+// Thread-local error message helpers (api.cu).
+snn_status fail(snn_status s, const std::string& msg);
+snn_status cuda_fail(cudaError_t e, const char* what);
+
+// Kernel launchers (neuron.cu, propagate.cu, csr.cu).
+cudaError_t launch_neuron_step(const NeuronArgs& a, cudaStream_t s);
+cudaError_t launch_init_state(const DevPop* pops, int n_pops_total, const int32_t* tile_pop,
+                              int num_tiles, float* V, float* m, float* h, float* n, float* g0,
+                              float* g1, float* iext, cudaStream_t s);
+cudaError_t launch_propagate(const PropArgs& a, int blocks, cudaStream_t s);
+int dense_rows_per_item();
+int dense_posts_per_item();
+cudaError_t launch_validate_csr(const int64_t* row_ptr, const int32_t* col, int32_t n_pre,
+                                int32_t n_post, int64_t nnz, uint32_t* error, cudaStream_t s);
+cudaError_t launch_densify(const int64_t* row_ptr, const int32_t* col, const float* w, int32_t n_pre,
+                           int32_t n_post, float* W, cudaStream_t s);
+cudaError_t launch_max_row(const int64_t* row_ptr, int32_t n_pre, int32_t* out, cudaStream_t s);
+cudaError_t launch_event_list(const int64_t* row_ptr, const int32_t* col, const float* w,
+                              const int32_t* spk, int32_t n, const int64_t* offsets,
+                              int32_t* post_out, float* w_out, cudaStream_t s);
+cudaError_t launch_row_lengths(const int64_t* row_ptr, const int32_t* spk, int32_t n,
+                               int64_t* lens, cudaStream_t s);
+cudaError_t launch_scan_i64(const int64_t* in, int64_t* out, int64_t n, int64_t* scratch,
+                            cudaStream_t s);
+size_t scan_scratch_elems(int64_t n);
+cudaError_t launch_csr_count(uint64_t seed, uint32_t tag, int64_t n_pre, int64_t n_post,
+                             unsigned long long thr, int64_t* counts, cudaStream_t s);
+cudaError_t launch_csr_fill(uint64_t seed, uint32_t tag, int64_t n_pre, int64_t n_post,
+                            unsigned long long thr, const int64_t* row_ptr, int32_t* col,
+                            cudaStream_t s);
+cudaError_t launch_set_epoch_base(unsigned long long* ticket, int num_tiles, cudaStream_t s);
+
+unsigned long long bernoulli_threshold(double p);
+
+}  // namespace snn

@@ -1,0 +1,282 @@
+"""Python layer over the C-ABI: device memory and streams come from PyTorch,
+every step of the simulation runs in the CUDA library.
+
+``Network``  -- a conductance-based HH network (Sec. 2) with compressed-row or
+               dense projections (Sec. 3) scaled by gScale (Sec. 5.1).
+``csr_bernoulli`` -- compressed rows drawn on the GPU from a seed.
+"""
+from __future__ import annotations
+
+import ctypes as C
+
+import numpy as np
+import torch
+
+from . import _lib as L
+from ._lib import check
+
+_F32 = {"V", "m", "h", "n", "g0", "g1", "iext", "isyn"}
+
+
+def _stream(stream=None) -> int:
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return s.cuda_stream if hasattr(s, "cuda_stream") else int(s)
+
+
+class TorchAllocator:
+    """snn_allocator backed by PyTorch's caching allocator."""
+
+    def __init__(self, device=None):
+        self.device = torch.device("cuda", torch.cuda.current_device() if device is None else device).index
+
+        def _alloc(nbytes, stream, ctx):
+            try:
+                return torch.cuda.caching_allocator_alloc(int(nbytes), self.device, int(stream or 0))
+            except Exception:        # out of memory: the library reports SNN_ERR_OOM
+                return None
+
+        def _free(ptr, stream, ctx):
+            torch.cuda.caching_allocator_delete(ptr)
+
+        self._a = L.ALLOC_FN(_alloc)
+        self._f = L.FREE_FN(_free)
+        self.struct = L.Allocator(self._a, self._f, None)
+
+    def ref(self):
+        return C.byref(self.struct)
+
+
+def _dev(x, dtype, device):
+    if isinstance(x, torch.Tensor):
+        return x.to(device=device, dtype=dtype).contiguous()
+    return torch.as_tensor(np.ascontiguousarray(x), dtype=dtype, device=device)
+
+
+def csr_bernoulli(seed, tag, n_pre, n_post, p, device=None, stream=None):
+    """Compressed rows (row_ptr int64[n_pre+1], col int32[nnz]) drawn on the
+    GPU: post j is in row i when word j%4 of Philox4x32-10(counter=(j/4, i,
+    tag, 3), key=seed) is below round(p * 2^32)."""
+    device = torch.device("cuda") if device is None else torch.device(device)
+    row_ptr = torch.empty(n_pre + 1, dtype=torch.int64, device=device)
+    nnz = C.c_int64()
+    alloc = TorchAllocator(device.index)
+    s = _stream(stream)
+    check(L.lib.snn_csr_bernoulli_rows(int(seed), int(tag), int(n_pre), int(n_post), float(p),
+                                       row_ptr.data_ptr(), C.byref(nnz), alloc.ref(), s))
+    col = torch.empty(max(nnz.value, 1), dtype=torch.int32, device=device)
+    check(L.lib.snn_csr_bernoulli_fill(int(seed), int(tag), int(n_pre), int(n_post), float(p),
+                                       row_ptr.data_ptr(), col.data_ptr(), s))
+    return row_ptr, col[:nnz.value]
+
+
+class Network:
+    """An HH spiking network living on one GPU.
+
+    pops:  list of dicts (keys of ``snn_inputs.hh_pop`` / ``source_pop``), with
+           optional ``v0`` (array or tensor of n FP32 potentials).
+    projs: list of dicts with pre, post, layout ('csr' | 'dense'), channel,
+           k1, k2, k3, density (p), optional n_conn, user_scale, and either
+           row_ptr/col/w (compressed rows) or w of n_pre*n_post (dense input).
+    """
+
+    def __init__(self, pops, projs, dt, n_sub=4, seed=0, instance=0, device=None, stream=None,
+                 torch_alloc=True):
+        self.device = torch.device("cuda") if device is None else torch.device(device)
+        if self.device.index is None:
+            self.device = torch.device("cuda", torch.cuda.current_device())
+        self.sizes = [int(d["n"]) for d in pops]
+        self.n_projs = len(projs)
+        self._alloc = TorchAllocator(self.device.index) if torch_alloc else None
+        keep = []
+        P = (L.PopDesc * len(pops))()
+        for k, d in enumerate(pops):
+            p = P[k]
+            p.kind = L.POP_SOURCE if d["kind"] == "source" else L.POP_HH
+            p.n = int(d["n"])
+            for f, v in (d.get("hh") or {}).items():
+                setattr(p, f, float(v))
+            E = d.get("E_syn", (0.0, -92.0))
+            tau = d.get("tau_syn", (1.0, 1.0))
+            p.E_syn[0], p.E_syn[1] = float(E[0]), float(E[1])
+            p.tau_syn[0], p.tau_syn[1] = float(tau[0]), float(tau[1])
+            p.v_thresh = float(d.get("v_thresh", 0.0))
+            p.src_rate_hz = float(d.get("rate_hz", 0.0))
+            drv = d.get("drive") or {}
+            p.drive_rate_hz = float(drv.get("rate_hz", 0.0))
+            p.drive_amp = float(drv.get("amp", 0.0))
+            p.drive_tau = float(drv.get("tau", 0.0))
+            v0 = d.get("v0")
+            if v0 is not None and p.kind == L.POP_HH:
+                t = _dev(v0, torch.float32, self.device)
+                assert t.numel() == p.n
+                keep.append(t)
+                p.v0, p.v0_on_device = t.data_ptr(), 1
+        Q = (L.ProjDesc * max(len(projs), 1))()
+        for k, d in enumerate(projs):
+            q = Q[k]
+            q.pre, q.post = int(d["pre"]), int(d["post"])
+            q.layout = L.LAYOUT_DENSE if d["layout"] == "dense" else L.LAYOUT_CSR
+            q.channel = int(d.get("channel", 0))
+            q.synapse = L.SYN_GRADED if d.get("synapse") == "graded" else L.SYN_EXP
+            q.on_device = 1
+            w = _dev(d["w"], torch.float32, self.device)
+            keep.append(w)
+            q.w = w.data_ptr()
+            if d.get("row_ptr") is None:
+                q.input_dense = 1
+                q.nnz = w.numel()
+            else:
+                rp = _dev(d["row_ptr"], torch.int64, self.device)
+                col = _dev(d["col"], torch.int32, self.device)
+                keep += [rp, col]
+                q.row_ptr, q.col, q.nnz = rp.data_ptr(), col.data_ptr(), col.numel()
+            q.k1, q.k2, q.k3 = float(d.get("k1", 1.0)), float(d.get("k2", 0.0)), float(d.get("k3", 0.0))
+            q.density = float(d.get("p", d.get("density", 1.0)))
+            q.n_conn = float(d.get("n_conn", 0.0) or 0.0)
+            q.user_scale = float(d.get("user_scale", 1.0))
+            q.v_thr = float(d.get("v_thr", -20.0))
+            q.v_slope = float(d.get("v_slope", 2.0))
+        h = C.c_void_p()
+        torch.cuda.synchronize(self.device)
+        check(L.lib.snn_create_network(P, len(pops), Q, len(projs), float(dt), int(n_sub), int(seed),
+                                       int(instance), self._alloc.ref() if self._alloc else None,
+                                       _stream(stream), C.byref(h)))
+        self.h = h.value
+        self.dt = float(dt)
+
+    # ------------------------------------------------------------------ build
+    @classmethod
+    def from_spec(cls, spec, device=None, stream=None, instance=None, **kw):
+        """Builds the network of a ``snn_inputs`` description: connectivity is
+        drawn on the GPU from the seed, weights and initial potentials are the
+        shared seeded arrays, nConn = p * N_pre inside the library."""
+        import snn_inputs as I
+        inst = spec["instance"] if instance is None else instance
+        device = torch.device("cuda") if device is None else torch.device(device)
+        pops = []
+        for k, d in enumerate(spec["pops"]):
+            e = dict(d)
+            v0 = I.v0(spec, k)
+            if v0 is not None:
+                e["v0"] = torch.from_numpy(v0).to(device)
+            pops.append(e)
+        projs = []
+        for q, d in enumerate(spec["projs"]):
+            n_pre, n_post = I.n_pre_post(spec, q)
+            e = dict(d)
+            if d["layout"] == "dense" and d["p"] >= 1.0:
+                e["w"] = torch.from_numpy(I.weights(spec, q, n_pre * n_post)).to(device)
+                e["row_ptr"] = None
+            else:
+                rp, col = csr_bernoulli(spec["seed"], I.rng_tag(inst, q), n_pre, n_post, d["p"], device, stream)
+                e["row_ptr"], e["col"] = rp, col
+                e["w"] = torch.from_numpy(I.weights(spec, q, col.numel())).to(device)
+            projs.append(e)
+        return cls(pops, projs, spec["dt"], spec["n_sub"], spec["seed"], inst, device=device, stream=stream, **kw)
+
+    # ------------------------------------------------------------------ run
+    def close(self):
+        if getattr(self, "h", None):
+            L.lib.snn_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def step(self, n=1, stream=None):
+        check(L.lib.snn_step(self.h, int(n), _stream(stream)))
+
+    def sync(self, stream=None):
+        check(L.lib.snn_sync(self.h, _stream(stream)))
+
+    def reset(self, stream=None):
+        check(L.lib.snn_reset(self.h, _stream(stream)))
+
+    def set_option(self, name, value):
+        check(L.lib.snn_set_option(self.h, L.OPT[name], int(value)))
+
+    @property
+    def t(self):
+        v = C.c_int64()
+        check(L.lib.snn_get_step(self.h, C.byref(v), _stream(None)))
+        return v.value
+
+    def scale(self, q):
+        v = C.c_float()
+        check(L.lib.snn_proj_scale(self.h, int(q), C.byref(v)))
+        return v.value
+
+    def nnz(self, q):
+        v = C.c_int64()
+        check(L.lib.snn_proj_nnz(self.h, int(q), C.byref(v)))
+        return v.value
+
+    # ------------------------------------------------------------------ state
+    def read(self, pop, field, stream=None) -> torch.Tensor:
+        """A field of population `pop` as a device tensor (copied)."""
+        s = _stream(stream)
+        fid = L.FIELD[field]
+        if field in _F32:
+            out = torch.empty(self.sizes[pop], dtype=torch.float32, device=self.device)
+            nbytes = 4 * out.numel()
+        elif field == "spikes":
+            out = torch.empty(max(self.sizes[pop], 1), dtype=torch.int32, device=self.device)
+            nbytes = 4 * out.numel()
+        elif field == "nspk":
+            out = torch.empty(1, dtype=torch.int32, device=self.device)
+            nbytes = 4
+        else:
+            out = torch.empty(1, dtype=torch.int64, device=self.device)
+            nbytes = 8
+        check(L.lib.snn_read_state(self.h, int(pop), fid, out.data_ptr(), nbytes, 1, s))
+        if field == "spikes":
+            return out[: int(self.read(pop, "nspk", stream).item())]
+        return out
+
+    def read_host(self, pop, field):
+        """Same as read() but through a host buffer (numpy)."""
+        s = _stream(None)
+        if field in _F32:
+            out = np.empty(self.sizes[pop], dtype=np.float32)
+        elif field == "nspk":
+            out = np.empty(1, dtype=np.int32)
+        elif field in ("spike_count", "nan_count"):
+            out = np.empty(1, dtype=np.int64)
+        else:
+            out = np.empty(max(self.sizes[pop], 1), dtype=np.int32)
+        check(L.lib.snn_read_state(self.h, int(pop), L.FIELD[field], out.ctypes.data, out.nbytes, 0, s))
+        if field == "spikes":
+            return out[: int(self.read_host(pop, "nspk")[0])]
+        return out
+
+    def write(self, pop, field, values, stream=None):
+        t = _dev(values, torch.float32, self.device)
+        assert t.numel() == self.sizes[pop]
+        check(L.lib.snn_write_state(self.h, int(pop), L.FIELD[field], t.data_ptr(), 4 * t.numel(), 1,
+                                    _stream(stream)))
+
+    def counters(self, pop):
+        return int(self.read(pop, "spike_count").item()), int(self.read(pop, "nan_count").item())
+
+    # ------------------------------------------------------------------ checks
+    def debug_propagate(self, q, spk, stream=None):
+        t = _dev(spk, torch.int32, self.device)
+        check(L.lib.snn_debug_propagate(self.h, int(q), t.data_ptr() if t.numel() else None, t.numel(), 1,
+                                        _stream(stream)))
+
+    def event_list(self, q, spk, stream=None):
+        t = _dev(spk, torch.int32, self.device)
+        n = C.c_int64()
+        s = _stream(stream)
+        st = L.lib.snn_event_list(self.h, int(q), t.data_ptr() if t.numel() else None, t.numel(), 1, None, None, 0,
+                                  C.byref(n), s)
+        if st not in (L.SNN_OK, 8):
+            check(st)
+        post = torch.empty(max(n.value, 1), dtype=torch.int32, device=self.device)
+        w = torch.empty(max(n.value, 1), dtype=torch.float32, device=self.device)
+        check(L.lib.snn_event_list(self.h, int(q), t.data_ptr() if t.numel() else None, t.numel(), 1,
+                                   post.data_ptr(), w.data_ptr(), n.value, C.byref(n), s))
+        return post[: n.value], w[: n.value]

@@ -1,0 +1,248 @@
+"""CUDA path vs the FP64 oracle, through the C-ABI (needs a GPU).
+
+Tolerances: integer work (connectivity, spike lists, event lists, counters of
+identical draws) bit-exact; I_syn within 1e-5 relative; V within 1e-3 mV on
+subthreshold trajectories; population rates within 2 % (+ one spike).
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import snn_inputs as I
+
+pytestmark = pytest.mark.gpu
+
+
+def _rel_ok(got, want, rel=1e-5):
+    got = np.asarray(got, np.float64)
+    want = np.asarray(want, np.float64)
+    floor = 1e-5 * np.abs(want).max() if want.size else 0.0
+    return np.all(np.abs(got - want) <= rel * np.maximum(np.abs(want), floor) + 1e-30)
+
+
+# ---------------------------------------------------------------- connectivity
+@pytest.mark.parametrize("n_pre,n_post,p", [
+    (1, 1, 0.5), (3, 7, 0.3), (64, 129, 0.1), (100, 1000, 0.1), (37, 4099, 0.5),
+    (200, 5003, 0.05), (10, 10, 0.0), (9, 33, 1.0), (0, 50, 0.5), (50, 0, 0.5)])
+def test_csr_builder_bit_exact(gpu, n_pre, n_post, p):
+    seed, tag = 987654321, 0x102
+    rp, col = gpu.csr_bernoulli(seed, tag, n_pre, n_post, p)
+    orp, ocol = oracle.csr_bernoulli(seed, tag, n_pre, n_post, p)
+    assert np.array_equal(rp.cpu().numpy(), orp)
+    assert np.array_equal(col.cpu().numpy(), ocol)
+
+
+def test_csr_builder_bit_exact_full_size_sweep_point(gpu):
+    # 100 x 1,000,000 at p = 0.5: the largest compressed projection of the sweep
+    seed, tag = I.SEED, I.rng_tag(0, 0)
+    rp, col = gpu.csr_bernoulli(seed, tag, 100, 1_000_000, 0.5)
+    orp, ocol = oracle.csr_bernoulli(seed, tag, 100, 1_000_000, 0.5)
+    assert np.array_equal(rp.cpu().numpy(), orp)
+    assert np.array_equal(col.cpu().numpy(), ocol)
+
+
+# ---------------------------------------------------------------- events
+def _two_layer(p=0.3, n_pre=64, n_post=300, layout="csr", weight=("uniform", 0.0, 1.0)):
+    return I.net([I.source_pop(n_pre, 0.0), I.hh_pop(n_post)],
+                 [I.proj(0, 1, layout, p, weight)], dt=0.1, steps=1)
+
+
+def test_event_list_bit_exact(gpu):
+    spec = _two_layer(n_pre=120, n_post=777, p=0.2)
+    net = gpu.Network.from_spec(spec)
+    orp, ocol = oracle.csr_bernoulli(spec["seed"], I.rng_tag(0, 0), 120, 777, 0.2)
+    w = I.weights(spec, 0, len(ocol))
+    rng = np.random.default_rng(3)
+    for k in (0, 1, 7, 120):
+        spk = np.sort(rng.choice(120, k, replace=False)).astype(np.int32)
+        post, wv = net.event_list(0, spk)
+        opost, ow = oracle.event_list(orp, ocol, w.astype(np.float64), spk)
+        assert np.array_equal(post.cpu().numpy(), opost)
+        assert np.array_equal(wv.cpu().numpy(), ow.astype(np.float32))
+
+
+@pytest.mark.parametrize("layout,n_post", [("csr", 300), ("dense", 300), ("dense", 301), ("csr", 5)])
+def test_propagation_matches_oracle_delivery(gpu, layout, n_post):
+    spec = _two_layer(layout=layout, n_post=n_post)
+    net = gpu.Network.from_spec(spec)
+    ref = oracle.from_spec(spec)
+    assert net.scale(0) == pytest.approx(ref.scale(0), rel=1e-7)
+    rng = np.random.default_rng(11)
+    for k in (0, 1, 33, 64):
+        spk = np.sort(rng.choice(64, k, replace=False)).astype(np.int32)
+        net.debug_propagate(0, spk)
+        ref.deliver(0, spk)
+        assert _rel_ok(net.read_host(1, "g0"), ref.get(1, "g0"))
+
+
+def test_dense_propagation_many_spiking_rows(gpu):
+    # more than one 32-row dense item and more than one 128-post block
+    spec = I.net([I.source_pop(200, 0.0), I.hh_pop(260)],
+                 [I.proj(0, 1, "dense", 1.0, ("lognormal", -3.0, 0.5))], dt=0.1, steps=1)
+    net = gpu.Network.from_spec(spec)
+    ref = oracle.from_spec(spec)
+    spk = np.arange(0, 200, 2, dtype=np.int32)
+    net.debug_propagate(0, spk)
+    ref.deliver(0, spk)
+    assert _rel_ok(net.read_host(1, "g0"), ref.get(1, "g0"))
+
+
+# ---------------------------------------------------------------- time steps
+def test_source_spikes_and_counts_bit_exact(gpu):
+    spec = I.net([I.source_pop(1000, 200.0), I.source_pop(37, 5000.0)], [], dt=0.1, steps=1)
+    net = gpu.Network.from_spec(spec)
+    ref = oracle.from_spec(spec)
+    for t in range(100):
+        net.step()
+        ref.step()
+        for pop in (0, 1):
+            assert np.array_equal(net.read_host(pop, "spikes"), ref.spikes(pop)), (t, pop)
+    for pop in (0, 1):
+        assert net.counters(pop) == ref.counters(pop)
+
+
+def _compare_run(net, ref, steps, pops, record_isyn=True):
+    """Steps both sides one step at a time; returns max |dV| per population."""
+    if record_isyn:
+        net.set_option("record_isyn", 1)
+    worst = {p: 0.0 for p in pops}
+    for t in range(steps):
+        net.step()
+        ref.step()
+        for p in pops:
+            v, vo = net.read_host(p, "V").astype(np.float64), ref.get(p, "V")
+            worst[p] = max(worst[p], float(np.abs(v - vo).max()))
+            if record_isyn:
+                assert _rel_ok(net.read_host(p, "isyn"), ref.get(p, "isyn")), (t, p)
+            assert np.array_equal(net.read_host(p, "spikes"), ref.spikes(p)), (t, p)
+    return worst
+
+
+def test_small_workload_200_steps(gpu):
+    spec = I.config_small(steps=200)
+    net = gpu.Network.from_spec(spec)
+    ref = oracle.from_spec(spec)
+    worst = _compare_run(net, ref, 200, [1])
+    assert worst[1] <= 1e-3
+    for f in ("m", "h", "n"):
+        assert np.abs(net.read_host(1, f) - ref.get(1, f)).max() < 1e-5
+    assert net.counters(0) == ref.counters(0)
+
+
+def test_ragged_population_sizes(gpu):
+    # populations of 1, 255, 257 and 513 neurons span tile edges
+    pops = [I.source_pop(257, 500.0), I.hh_pop(1), I.hh_pop(255), I.hh_pop(513)]
+    projs = [I.proj(0, 1, "csr", 0.5, ("uniform", 0, 30.0)), I.proj(0, 2, "dense", 1.0, ("uniform", 0, 3.0)),
+             I.proj(0, 3, "csr", 0.1, ("uniform", 0, 30.0), channel=1)]
+    spec = I.net(pops, projs, dt=0.1, steps=1)
+    net = gpu.Network.from_spec(spec)
+    ref = oracle.from_spec(spec)
+    worst = _compare_run(net, ref, 60, [1, 2, 3])
+    assert max(worst.values()) <= 1e-3
+
+
+def _first_spike_steps(run_spikes, n):
+    first = np.full(n, -1)
+    for t, s in enumerate(run_spikes):
+        for i in s:
+            if first[i] < 0:
+                first[i] = t
+    return first
+
+
+def test_four_population_workload_full_size_first_200_steps(gpu):
+    spec = I.config_four_pop(steps=200)
+    net = gpu.Network.from_spec(spec)
+    ref = oracle.from_spec(spec)
+    net.set_option("record_isyn", 1)
+    n_in = spec["pops"][0]["n"]
+    vg, vo, sg, so = [], [], [], []
+    for t in range(200):
+        net.step()
+        ref.step()
+        for p in (1, 2, 3):
+            assert np.abs(net.read_host(p, "V") - ref.get(p, "V")).max() <= 1e-3, (t, p)
+            assert _rel_ok(net.read_host(p, "isyn"), ref.get(p, "isyn")), (t, p)
+        vg.append(net.read_host(0, "V").astype(np.float64))
+        vo.append(ref.get(0, "V"))
+        sg.append(net.read_host(0, "spikes"))
+        so.append(ref.spikes(0))
+    fg, fo = _first_spike_steps(sg, n_in), _first_spike_steps(so, n_in)
+    assert np.all(np.abs(fg - fo) <= 1)                     # first spikes within one step
+    vg, vo = np.array(vg), np.array(vo)
+    for i in range(n_in):                                    # V before the upstroke
+        end = (fo[i] - 10) if fo[i] >= 0 else 200
+        if end > 0:
+            assert np.abs(vg[:end, i] - vo[:end, i]).max() <= 1e-3, i
+
+
+def test_population_rates_within_2_percent(gpu):
+    # forced activity: strong weights make the HH population fire
+    spec = I.config_small(steps=3000, n_hh=400, n_src=100, p=0.2, weight_hi=60.0)
+    net = gpu.Network.from_spec(spec)
+    ref = oracle.from_spec(spec)
+    net.step(spec["steps"])
+    ref.step(spec["steps"])
+    cg, _ = net.counters(1)
+    co, _ = ref.counters(1)
+    assert co > 200
+    assert abs(cg - co) <= 0.02 * co + 1
+
+
+def test_graph_and_eager_steps_agree(gpu):
+    spec = I.config_four_pop(steps=250, n_mid=2000)
+    a = gpu.Network.from_spec(spec)
+    b = gpu.Network.from_spec(spec)
+    b.set_option("graph_steps", 0)
+    a.step(250)
+    b.step(250)
+    for p in range(4):
+        assert np.abs(a.read_host(p, "V") - b.read_host(p, "V")).max() < 1e-4
+        assert a.counters(p) == b.counters(p)
+    assert a.t == 250 and b.t == 250
+
+
+def test_reset_restarts_the_same_trajectory(gpu):
+    spec = I.config_four_pop(steps=150, n_mid=1500)
+    net = gpu.Network.from_spec(spec)
+    net.step(150)
+    v1 = [net.read_host(p, "V") for p in range(4)]
+    c1 = [net.counters(p) for p in range(4)]
+    net.reset()
+    assert net.t == 0
+    net.step(150)
+    for p in range(4):
+        assert np.abs(net.read_host(p, "V") - v1[p]).max() < 1e-4
+        assert net.counters(p) == c1[p]
+
+
+def test_nan_states_are_counted(gpu):
+    spec = I.net([I.hh_pop(300)], [], dt=0.1, steps=1)
+    net = gpu.Network.from_spec(spec)
+    v = net.read_host(0, "V")
+    v[[0, 17, 299]] = np.nan
+    net.write(0, "V", torch.from_numpy(v))
+    net.step(5)
+    assert net.counters(0)[1] == 15
+
+
+def test_malformed_rows_are_rejected(gpu):
+    import paper_1412_0595_gb300 as snn
+    spec = _two_layer()
+    pops = [dict(spec["pops"][0]), dict(spec["pops"][1])]
+    rp = np.array([0, 2, 1, 3] + [3] * 61, dtype=np.int64)     # not monotone
+    col = np.array([0, 1, 2], dtype=np.int32)
+    bad = dict(spec["projs"][0], row_ptr=rp, col=col, w=np.ones(3, np.float32))
+    with pytest.raises(snn.SNNError) as e:
+        snn.Network(pops, [bad], 0.1, 4, 1)
+    assert e.value.name == "SNN_ERR_CSR"
+    rp = np.array([0, 2] + [2] * 63, dtype=np.int64)
+    bad = dict(spec["projs"][0], row_ptr=rp, col=np.array([5, 5], np.int32), w=np.ones(2, np.float32))
+    with pytest.raises(snn.SNNError) as e:                      # not strictly ascending
+        snn.Network(pops, [bad], 0.1, 4, 1)
+    assert e.value.name == "SNN_ERR_CSR"
+    bad = dict(spec["projs"][0], row_ptr=rp, col=np.array([5, 300], np.int32), w=np.ones(2, np.float32))
+    with pytest.raises(snn.SNNError) as e:                      # post index out of range
+        snn.Network(pops, [bad], 0.1, 4, 1)
+    assert e.value.name == "SNN_ERR_CSR"
