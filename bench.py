@@ -1,0 +1,395 @@
+"""Benchmark of the HH spiking-network time-step loop on one GB300 (or N replicas).
+
+One bench step = one full simulation of the four-population feed-forward HH
+network (In 100 with Poisson current drive -> Mid 10,000 over compressed rows
+at p = 0.5 -> Out 100 dense; Inh 20 dense from In, inhibitory onto Out;
+lognormal(-3, 0.5) nS weights scaled by gScale = 1/(p N_pre)) for 10,000 time
+steps of 0.1 ms with 4 Euler substeps: every time step runs the neuron update
+with spike compaction and the propagation of that step's spikes.
+
+Metric: synaptic events/s (events = stored synapses of the spiking rows,
+counted exactly from per-neuron spike counts), with HH neuron-steps/s beside
+it.  Inputs are resident in HBM when the timed region starts; L2 is flushed
+(256 MiB write) between timed steps.  `e2e` repeats the measurement through
+the public API from pinned host buffers (weights and initial potentials
+copied in, connectivity drawn on the device, counters copied out).
+
+--impl reference times the FP64 CPU oracle (the only reference this method
+has) on a bounded sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+import snn_inputs as I  # noqa: E402
+
+# Algorithmic work per unit (see the roofline notes of the design document).
+FLOPS_PER_SUBSTEP = 64          # rates 28, currents 16, gating 12, updates 8
+FLOPS_PER_STEP_EXTRA = 9        # I_syn 5, decays 3, threshold test 1
+BYTES_PER_EVENT = 8             # 4 B post index + 4 B weight streamed from HBM
+BYTES_PER_ROW = 12              # 8 B row start + 4 B spike id per spiking row
+SM_COUNT = 152
+FP32_LANES = 128
+
+
+def _args():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--sim-steps", type=int, default=10_000)
+    ap.add_argument("--cpu-steps", type=int, default=4_000,
+                    help="time steps of the bounded oracle sample")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--steady-steps", type=int, default=2000,
+                    help="time steps run before the per-kernel timing")
+    ap.add_argument("--phase-reps", type=int, default=200,
+                    help="back-to-back launches per kernel in the per-kernel timing")
+    return ap.parse_args()
+
+
+def _dist():
+    rank = int(os.environ.get("RANK", 0))
+    world = int(os.environ.get("WORLD_SIZE", 1))
+    local = int(os.environ.get("LOCAL_RANK", 0))
+    return rank, world, local
+
+
+def _peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            d = json.load(f)
+        return d, "measured"
+    except Exception:
+        return {"hbm_gbs": 6800.0, "sm_max_mhz": 2070.0}, "fallback"
+
+
+class Clocks:
+    """nvidia-smi sampling of SM clock and throttle reasons during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.p = None
+
+    def __enter__(self):
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}",
+                                       "--format=csv,noheader,nounits", "-lms", "200"],
+                                      stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.p = None
+        return self
+
+    def __exit__(self, *a):
+        self.out = ""
+        if self.p:
+            self.p.terminate()
+            try:
+                self.out, _ = self.p.communicate(timeout=5)
+            except Exception:
+                self.p.kill()
+
+    def summary(self):
+        rows = []
+        for ln in (self.out or "").strip().splitlines():
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) >= 9:
+                rows.append(f)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0}
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for r in rows for k in range(4) if r[5 + k].lower().startswith("active")})
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": float(rows[0][2]) if rows[0][2].replace(".", "").isdigit() else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+def _cpu_baseline(sim_steps):
+    """The FP64 oracle, as it stands, on a bounded sample (single thread)."""
+    import oracle
+    spec = I.config_four_pop(steps=sim_steps)
+    ref = oracle.from_spec(spec)
+    t0 = time.perf_counter()
+    ref.step(sim_steps)
+    dt = time.perf_counter() - t0
+    n_neurons = sum(p["n"] for p in spec["pops"])
+    return {"value": ref.events / dt, "unit": "synaptic events/s", "cores": 1, "kind": "oracle",
+            "sample": f"{sim_steps} of the 10,000 time steps of the same network, FP64, 1 thread",
+            "neuron_steps_per_s": n_neurons * sim_steps / dt, "seconds": dt}
+
+
+def run_reference(a):
+    rank, world, _ = _dist()
+    if rank != 0:
+        return
+    import oracle
+    spec = I.config_four_pop(steps=a.cpu_steps)
+    n_neurons = sum(p["n"] for p in spec["pops"])
+    times, events = [], 0
+    for k in range(a.warmup + a.steps):
+        ref = oracle.from_spec(spec)
+        t0 = time.perf_counter()
+        ref.step(a.cpu_steps)
+        dt = time.perf_counter() - t0
+        if k >= a.warmup:
+            times.append(dt)
+            events += ref.events
+    total = sum(times)
+    value = events / total
+    line = {"impl": "reference", "metric": "synaptic events/s", "value": value, "unit": "synaptic events/s",
+            "n_gpus": world, "steps": a.steps, "warmup": a.warmup, "ms_per_step": 1e3 * total / a.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic",
+            "config": {"workload": spec["name"], "sim_steps_per_step": a.cpu_steps, "dt_ms": spec["dt"],
+                       "substeps": spec["n_sub"]},
+            "neuron_steps_per_s": n_neurons * a.cpu_steps * a.steps / total,
+            "cpu_baseline": {"value": value, "unit": "synaptic events/s", "cores": 1, "kind": "oracle",
+                             "sample": f"{a.cpu_steps} time steps of the same network per step"},
+            "e2e": {"value": value, "unit": "synaptic events/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def _flush_l2(buf):
+    buf.add_(1.0)
+
+
+def _phase_time_ms(net, phase, reps, torch):
+    """Average device time of one launch of a step phase: `reps` launches
+    captured back to back in a CUDA graph and timed with events."""
+    s = torch.cuda.Stream()
+    with torch.cuda.stream(s):
+        g = torch.cuda.CUDAGraph()
+        torch.cuda.synchronize()
+        with torch.cuda.graph(g, stream=s):
+            for _ in range(reps):
+                net.launch_phase(phase, stream=s)
+        g.replay()
+        s.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(s)
+        g.replay()
+        e1.record(s)
+        s.synchronize()
+    return e0.elapsed_time(e1) / reps
+
+
+def run_ours(a):
+    import torch
+    import torch.distributed as dist
+
+    import paper_1412_0595_gb300 as snn
+
+    rank, world, local = _dist()
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl")
+    dev = torch.device("cuda", local)
+    spec = I.config_four_pop(steps=a.sim_steps)
+    n_neurons = sum(p["n"] for p in spec["pops"])
+    n_hh = sum(p["n"] for p in spec["pops"] if p["kind"] == "hh")
+    net = snn.Network.from_spec(spec, device=dev)
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)   # 256 MiB > L2
+
+    def one_run():
+        net.reset()
+        _flush_l2(flush)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        net.step(a.sim_steps)
+        e1.record(stream)
+        e1.synchronize()
+        return e0.elapsed_time(e1), net.synaptic_events()
+
+    for _ in range(a.warmup):
+        one_run()
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    ms, events = [], 0
+    wall0 = time.perf_counter()
+    with Clocks(local) as clk:
+        for _ in range(a.steps):
+            t, ev = one_run()
+            ms.append(t)
+            events += ev
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    wall = time.perf_counter() - wall0
+    total_ms = sum(ms)
+    if world > 1:
+        t = torch.tensor([total_ms], device=dev, dtype=torch.float64)
+        e = torch.tensor([events], device=dev, dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        dist.all_reduce(e, op=dist.ReduceOp.SUM)
+        total_ms, events = float(t.item()), float(e.item())
+    value = events / (total_ms * 1e-3)
+    neuron_steps = world * n_neurons * a.sim_steps * a.steps / (total_ms * 1e-3)
+
+    # ---- per-kernel times for the roofline (same network, steady state) ----
+    net.reset()
+    net.step(a.steady_steps)
+    torch.cuda.synchronize()
+    spikes = [net.counters(p)[0] for p in range(len(spec["pops"]))]
+    ev_total = net.synaptic_events()
+    t_neuron = _phase_time_ms(net, 0, a.phase_reps, torch)
+    t_prop = _phase_time_ms(net, 1, a.phase_reps, torch)
+    peaks, src = _peaks()
+    sm_mhz = float(peaks.get("sm_max_mhz", 2070.0))
+    fp32_peak = SM_COUNT * FP32_LANES * 2 * sm_mhz * 1e6 / 1e12        # TFLOP/s
+    flops_per_neuron_step = FLOPS_PER_SUBSTEP * spec["n_sub"] + FLOPS_PER_STEP_EXTRA
+    neuron_tflops = n_hh * flops_per_neuron_step / (t_neuron * 1e-3) / 1e12
+    # algorithmic bytes of one propagation launch in the steady state above:
+    # compressed rows stream 8 B per synapse + 12 B per spiking row, dense
+    # rows 4 B per stored weight + 4 B per spiking row
+    dense_ev = dense_rows = csr_rows = 0
+    for d in spec["projs"]:
+        if d["layout"] == "dense":
+            dense_ev += spikes[d["pre"]] * spec["pops"][d["post"]]["n"]
+            dense_rows += spikes[d["pre"]]
+        else:
+            csr_rows += spikes[d["pre"]]
+    prop_bytes = ((ev_total - dense_ev) * BYTES_PER_EVENT + csr_rows * BYTES_PER_ROW
+                  + dense_ev * 4 + dense_rows * 4) / a.steady_steps
+    prop_gbs = prop_bytes / (t_prop * 1e-3) / 1e9
+    if t_neuron >= t_prop:
+        roof = {"kernel": "k_neuron_step", "bound": "alu", "achieved": neuron_tflops, "peak": fp32_peak,
+                "unit": "TFLOP/s", "frac": neuron_tflops / fp32_peak, "traffic": None,
+                "peak_source": "FP32 FMA peak from 152 SMs x 128 lanes x 2 x max SM clock "
+                               f"({sm_mhz:.0f} MHz, {src})",
+                "launch_us": 1e3 * t_neuron, "flops_per_launch": n_hh * flops_per_neuron_step}
+    else:
+        hbm = float(peaks.get("hbm_gbs", 6800.0))
+        roof = {"kernel": "k_propagate", "bound": "hbm", "achieved": prop_gbs, "peak": hbm, "unit": "GB/s",
+                "frac": prop_gbs / hbm, "traffic": None, "peak_source": f"hbm_gbs ({src})",
+                "launch_us": 1e3 * t_prop, "bytes_per_launch": prop_bytes}
+    roof["other"] = {"k_neuron_step_us": 1e3 * t_neuron, "k_propagate_us": 1e3 * t_prop,
+                     "neuron_tflops": neuron_tflops, "propagate_gbs": prop_gbs}
+
+    # ---- end to end through the public API from pinned host buffers ----
+    e2e = None
+    if not a.no_e2e:
+        e2e = _e2e(a, spec, dev, torch, snn)
+
+    cpu = None
+    if rank == 0 and world == 1 and not a.no_cpu_baseline:
+        cpu = _cpu_baseline(a.cpu_steps)
+
+    if rank == 0:
+        line = {"metric": "synaptic events/s", "value": value, "unit": "synaptic events/s", "n_gpus": world,
+                "steps": a.steps, "warmup": a.warmup, "ms_per_step": total_ms / a.steps,
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+                "data": "synthetic",
+                "config": {"workload": spec["name"], "sim_steps_per_step": a.sim_steps, "dt_ms": spec["dt"],
+                           "substeps": spec["n_sub"], "neurons": n_neurons,
+                           "l2": "flushed between timed steps (256 MiB write)",
+                           "parallelism": "replicas" if world > 1 else "single"},
+                "neuron_steps_per_s": neuron_steps,
+                "events_per_step": events / (a.steps * world),
+                "wall_s": wall,
+                "roofline": roof,
+                "cpu_baseline": cpu,
+                "e2e": e2e,
+                "gpu_launches": a.steps * (2 * a.sim_steps + 2),
+                "clocks": clk.summary()}
+        print(json.dumps(line), flush=True)
+    net.close()
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def _e2e(a, spec, dev, torch, snn):
+    """Same metric through the public API: pinned host inputs copied in,
+    network created, run, spike counters copied back, every step."""
+    host_v0 = {k: torch.from_numpy(I.v0(spec, k)).pin_memory()
+               for k, d in enumerate(spec["pops"]) if d["kind"] == "hh"}
+    host_w = {}
+    for q, d in enumerate(spec["projs"]):
+        n_pre, n_post = I.n_pre_post(spec, q)
+        if d["layout"] == "dense":
+            host_w[q] = torch.from_numpy(I.weights(spec, q, n_pre * n_post)).pin_memory()
+    nnz = {}
+    for q, d in enumerate(spec["projs"]):
+        if d["layout"] != "dense":
+            rp, col = snn.csr_bernoulli(spec["seed"], I.rng_tag(spec["instance"], q), *I.n_pre_post(spec, q), d["p"],
+                                        dev)
+            nnz[q] = col.numel()
+            host_w[q] = torch.from_numpy(I.weights(spec, q, nnz[q])).pin_memory()
+    out_host = torch.empty(len(spec["pops"]) * 2, dtype=torch.int64).pin_memory()
+    h2d = sum(t.numel() * 4 for t in host_v0.values()) + sum(t.numel() * 4 for t in host_w.values())
+    d2h = out_host.numel() * 8
+
+    def run():
+        pops = []
+        for k, d in enumerate(spec["pops"]):
+            e = dict(d)
+            if k in host_v0:
+                e["v0"] = host_v0[k].to(dev, non_blocking=True)
+            pops.append(e)
+        projs = []
+        for q, d in enumerate(spec["projs"]):
+            e = dict(d)
+            e["w"] = host_w[q].to(dev, non_blocking=True)
+            if d["layout"] != "dense":
+                rp, col = snn.csr_bernoulli(spec["seed"], I.rng_tag(spec["instance"], q),
+                                            *I.n_pre_post(spec, q), d["p"], dev)
+                e["row_ptr"], e["col"] = rp, col
+            else:
+                e["row_ptr"] = None
+            projs.append(e)
+        net = snn.Network(pops, projs, spec["dt"], spec["n_sub"], spec["seed"], spec["instance"], device=dev)
+        net.step(a.sim_steps)
+        ev = net.synaptic_events()
+        cnt = torch.stack([torch.cat([net.read(p, "spike_count"), net.read(p, "nan_count")])
+                           for p in range(len(spec["pops"]))]).flatten()
+        out_host.copy_(cnt)
+        torch.cuda.synchronize()
+        net.close()
+        return ev
+
+    for _ in range(min(a.warmup, 2)):
+        run()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    events = 0
+    k = max(1, min(a.steps, 3))
+    for _ in range(k):
+        events += run()
+    dt = time.perf_counter() - t0
+    return {"value": events / dt, "unit": "synaptic events/s", "h2d_bytes_per_step": h2d,
+            "d2h_bytes_per_step": d2h, "steps": k,
+            "note": "wall clock per step: pinned H2D of weights and V0, device connectivity draw, "
+                    "network creation, 10,000 time steps, D2H of counters"}
+
+
+def main():
+    a = _args()
+    if a.impl == "reference":
+        run_reference(a)
+    else:
+        run_ours(a)
+
+
+if __name__ == "__main__":
+    main()

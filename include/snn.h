@@ -65,7 +65,8 @@ enum {
     SNN_FIELD_SPIKES = 8,      /* int32[nspk], ascending spike list of the last step (read only) */
     SNN_FIELD_NSPK = 9,        /* int32, length of that list (read only) */
     SNN_FIELD_SPIKE_COUNT = 10,/* int64, spikes since creation or reset (Fig. 1 avgSpike numerator) */
-    SNN_FIELD_NAN_COUNT = 11   /* int64, neuron-steps that ended with a NaN V (Fig. 1 sumNANs) */
+    SNN_FIELD_NAN_COUNT = 11,  /* int64, neuron-steps that ended with a NaN V (Fig. 1 sumNANs) */
+    SNN_FIELD_NEURON_SPIKES = 12 /* int32[n], spikes of each neuron since creation or reset */
 };
 
 /* Options for snn_set_option. */
@@ -180,6 +181,17 @@ snn_status snn_set_option(snn_net* net, int32_t option, int64_t value);
 
 /* Steps simulated since creation or the last reset (synchronises `stream`). */
 snn_status snn_get_step(snn_net* net, int64_t* step, void* stream);
+
+/* Synaptic events delivered since creation or reset: the sum over projections
+ * and spikes of the spiking pre neuron's row length (n_post for dense
+ * storage), from the per-neuron spike counts.  Synchronises `stream`. */
+snn_status snn_synaptic_events(snn_net* net, int64_t* events, void* stream);
+
+/* Launches one phase of a step exactly as snn_step does, for timing single
+ * kernels: phase 0 = neuron update with spike compaction, 1 = propagation.
+ * A neuron phase without its propagation advances the state without
+ * delivering spikes.  Enqueued on `stream`. */
+snn_status snn_launch_phase(snn_net* net, int32_t phase, void* stream);
 
 /* Conductance scale s of projection `proj` as the GPU uses it (FP32). */
 snn_status snn_proj_scale(snn_net* net, int32_t proj, float* scale);

@@ -100,6 +100,8 @@ def lib():
         L.oracle_net_scale.restype = C.c_double
         L.oracle_net_time.argtypes = [C.c_void_p]
         L.oracle_net_time.restype = C.c_uint32
+        L.oracle_net_events.argtypes = [C.c_void_p]
+        L.oracle_net_events.restype = C.c_int64
         L.oracle_net_get.argtypes = [C.c_void_p, C.c_int, C.c_int, f64p]
         L.oracle_net_set.argtypes = [C.c_void_p, C.c_int, C.c_int, f64p]
         L.oracle_net_spikes.argtypes = [C.c_void_p, C.c_int, i32p]
@@ -277,6 +279,11 @@ class OracleNet:
 
     def scale(self, q):
         return float(lib().oracle_net_scale(self.h, q))
+
+    @property
+    def events(self):
+        """Synaptic events delivered so far (stored synapses of spiking rows)."""
+        return int(lib().oracle_net_events(self.h))
 
     def get(self, pop, field):
         out = np.zeros(self.sizes[pop], dtype=np.float64)

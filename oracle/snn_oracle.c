@@ -204,6 +204,7 @@ typedef struct {
     double dt;
     uint64_t seed;
     uint32_t t;
+    int64_t events;           /* synaptic events delivered (stored synapses of spiking rows) */
     opop* pops;
     oproj* projs;
 } oracle_net;
@@ -318,6 +319,7 @@ void oracle_net_destroy(oracle_net* net)
 
 double oracle_net_scale(const oracle_net* net, int proj) { return net->projs[proj].scale; }
 uint32_t oracle_net_time(const oracle_net* net) { return net->t; }
+int64_t oracle_net_events(const oracle_net* net) { return net->events; }
 
 /* One Euler substep of the HH equations for a single neuron. */
 static void hh_substep(const oracle_pop* d, double hs, double I_in,
@@ -386,9 +388,11 @@ void oracle_net_step(oracle_net* net)
             int64_t i = pre->spk[s];
             if (Q->desc.dense) {
                 for (int64_t j = 0; j < n_post; ++j) g[j] += Q->scale * Q->w[i * n_post + j];
+                net->events += n_post;
             } else {
                 for (int64_t k = Q->row_ptr[i]; k < Q->row_ptr[i + 1]; ++k)
                     g[Q->col[k]] += Q->scale * Q->w[k];
+                net->events += Q->row_ptr[i + 1] - Q->row_ptr[i];
             }
         }
     }

@@ -151,6 +151,7 @@ snn_status upload_projs(snn_net* net) {
         d.g = (P.d.channel == 0 ? net->g0 : net->g1) + post.offset;
         d.spk = net->spk + pre.offset;
         d.nspk = net->nspk + P.d.pre;
+        d.pre_count = net->nrn_count + pre.offset;
     }
     if (!dp.empty())
         CK(cudaMemcpy(net->d_projs, dp.data(), dp.size() * sizeof(DevProj), cudaMemcpyHostToDevice),
@@ -303,6 +304,9 @@ snn_status create_impl(const snn_pop_desc* pops, int32_t n_pops, const snn_proj_
     net->g0 = state + 4 * NT; net->g1 = state + 5 * NT; net->iext = state + 6 * NT; net->isyn = state + 7 * NT;
     TRY(dalloc(net, &net->init_state, 7 * NT, "initial state"));
     TRY(dalloc(net, &net->spk, NT, "spike lists"));
+    TRY(dalloc(net, &net->nrn_count, NT, "per-neuron spike counts"));
+    TRY(dalloc(net, &net->d_events, 1, "event counter"));
+    CK(cudaMemsetAsync(net->nrn_count, 0, NT * sizeof(int32_t), s), "clear");
     TRY(dalloc(net, &net->nspk, (size_t)n_pops, "spike counts"));
     TRY(dalloc(net, &net->counters, 2 * (size_t)n_pops, "counters"));
     TRY(dalloc(net, &net->ticket, 2, "ticket"));
@@ -354,6 +358,7 @@ snn_status create_impl(const snn_pop_desc* pops, int32_t n_pops, const snn_proj_
         q.nspk = net->nspk + k;
         q.spike_count = net->counters + 2 * k;
         q.nan_count = net->counters + 2 * k + 1;
+        q.neuron_spikes = net->nrn_count + P.offset;
     }
     CK(cudaMemcpyAsync(net->V, v0.data(), NT * sizeof(float), cudaMemcpyHostToDevice, s), "upload V0");
     for (int k = 0; k < n_pops; ++k) {
@@ -523,6 +528,10 @@ snn_status snn_read_state(snn_net* net, int32_t pop, int32_t field, void* dst, s
         CK(cudaStreamSynchronize(s), "synchronize");
         if (bytes < sizeof(int32_t) * (size_t)ns) return fail(SNN_ERR_SIZE, "destination smaller than the spike list");
         if (ns) CK(cudaMemcpyAsync(dst, net->spk + P.offset, sizeof(int32_t) * ns, kind, s), "copy spikes");
+    } else if (field == SNN_FIELD_NEURON_SPIKES) {
+        const size_t need = sizeof(int32_t) * (size_t)P.d.n;
+        if (bytes < need) return fail(SNN_ERR_SIZE, "destination smaller than n int32");
+        if (P.d.n) CK(cudaMemcpyAsync(dst, net->nrn_count + P.offset, need, kind, s), "copy counts");
     } else if (field == SNN_FIELD_SPIKE_COUNT || field == SNN_FIELD_NAN_COUNT) {
         if (bytes < sizeof(int64_t)) return fail(SNN_ERR_SIZE, "destination smaller than 8 bytes");
         const int o = field == SNN_FIELD_SPIKE_COUNT ? 0 : 1;
@@ -559,6 +568,7 @@ snn_status snn_reset(snn_net* net, void* stream) {
     CK(cudaMemsetAsync(net->isyn, 0, NT * sizeof(float), s), "clear");
     CK(cudaMemsetAsync(net->nspk, 0, sizeof(int32_t) * net->pops.size(), s), "clear");
     CK(cudaMemsetAsync(net->counters, 0, sizeof(unsigned long long) * 2 * net->pops.size(), s), "clear");
+    CK(cudaMemsetAsync(net->nrn_count, 0, NT * sizeof(int32_t), s), "clear");
     CK(launch_set_epoch_base(net->ticket, net->num_tiles, s), "reset step counter");
     return SNN_OK;
 }
@@ -597,6 +607,29 @@ snn_status snn_get_step(snn_net* net, int64_t* step, void* stream) {
     CK(cudaMemcpyAsync(t, net->ticket, sizeof(t), cudaMemcpyDeviceToHost, s), "read ticket");
     CK(cudaStreamSynchronize(s), "synchronize");
     *step = net->num_tiles ? (int64_t)(t[0] / (unsigned long long)net->num_tiles - t[1]) : 0;
+    return SNN_OK;
+}
+
+snn_status snn_synaptic_events(snn_net* net, int64_t* events, void* stream) {
+    if (!net || !events) return fail(SNN_ERR_INVALID_ARG, "bad argument");
+    cudaStream_t s = (cudaStream_t)stream;
+    unsigned long long v = 0;
+    CK(launch_count_events(net->d_projs, (int)net->projs.size(), net->d_events, s), "count events");
+    CK(cudaMemcpyAsync(&v, net->d_events, sizeof(v), cudaMemcpyDeviceToHost, s), "read events");
+    CK(cudaStreamSynchronize(s), "synchronize");
+    *events = (int64_t)v;
+    return SNN_OK;
+}
+
+snn_status snn_launch_phase(snn_net* net, int32_t phase, void* stream) {
+    if (!net || phase < 0 || phase > 1) return fail(SNN_ERR_INVALID_ARG, "bad network or phase");
+    cudaStream_t s = (cudaStream_t)stream;
+    if (phase == 0) {
+        CK(launch_neuron_step(neuron_args(net), s), "neuron phase");
+    } else if (!net->projs.empty()) {
+        PropArgs p{net->d_projs, (int32_t)net->projs.size(), net->chunk};
+        CK(launch_propagate(p, prop_blocks(net), s), "propagation phase");
+    }
     return SNN_OK;
 }
 

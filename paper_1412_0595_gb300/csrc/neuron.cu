@@ -154,6 +154,7 @@ __global__ void __launch_bounds__(kTile) k_neuron_step(const NeuronArgs a) {
     if (spike) {
         const unsigned lower = ballot & ((1u << lane) - 1u);
         P.spk[s_base + s_warp[warp] + __popc(lower)] = local;
+        P.neuron_spikes[local] += 1;
     }
 }
 

@@ -133,6 +133,27 @@ cudaError_t launch_propagate(const PropArgs& a, int blocks, cudaStream_t s) {
     return cudaGetLastError();
 }
 
+// Synaptic events since reset: sum over pre neurons of spikes x row length.
+__global__ void k_count_events(const DevProj* projs, unsigned long long* out) {
+    const DevProj& q = projs[blockIdx.y];
+    unsigned long long acc = 0;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < q.n_pre; i += gridDim.x * blockDim.x) {
+        const long long c = q.pre_count[i];
+        if (c) acc += (unsigned long long)(c * (q.layout == SNN_LAYOUT_CSR ? q.row_ptr[i + 1] - q.row_ptr[i]
+                                                                          : (int64_t)q.n_post));
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    if ((threadIdx.x & 31) == 0 && acc) atomicAdd(out, acc);
+}
+
+cudaError_t launch_count_events(const DevProj* projs, int n_projs, unsigned long long* out, cudaStream_t s) {
+    cudaError_t e = cudaMemsetAsync(out, 0, sizeof(unsigned long long), s);
+    if (e != cudaSuccess || n_projs == 0) return e;
+    k_count_events<<<dim3(64, n_projs), 256, 0, s>>>(projs, out);
+    return cudaGetLastError();
+}
+
 int dense_rows_per_item() { return kDenseRows; }
 int dense_posts_per_item() { return kDensePosts; }
 

@@ -51,6 +51,7 @@ struct DevPop {
     int32_t* nspk;
     unsigned long long* spike_count;
     unsigned long long* nan_count;
+    int32_t* neuron_spikes;        // per-neuron spike counts of this population
 };
 
 struct DevProj {
@@ -64,6 +65,7 @@ struct DevProj {
     float* g;              // post conductance channel, already offset to the post population
     const int32_t* spk;    // pre spike list
     const int32_t* nspk;
+    const int32_t* pre_count;   // per-neuron spike counts of the pre population
 };
 
 struct NeuronArgs {
@@ -132,6 +134,8 @@ struct snn_net {
     float* init_state = nullptr;   // 7 * n_total floats saved at creation
     int32_t* spk = nullptr;
     int32_t* nspk = nullptr;
+    int32_t* nrn_count = nullptr;             // per-neuron spike counts (n_total)
+    unsigned long long* d_events = nullptr;
     unsigned long long* counters = nullptr;   // 2 * n_pops
     unsigned long long* ticket = nullptr;     // [0] ticket, [1] epoch base
     unsigned long long* tile_status = nullptr;
@@ -186,6 +190,7 @@ cudaError_t launch_csr_count(uint64_t seed, uint32_t tag, int64_t n_pre, int64_t
 cudaError_t launch_csr_fill(uint64_t seed, uint32_t tag, int64_t n_pre, int64_t n_post,
                             unsigned long long thr, const int64_t* row_ptr, int32_t* col,
                             cudaStream_t s);
+cudaError_t launch_count_events(const DevProj* projs, int n_projs, unsigned long long* out, cudaStream_t s);
 cudaError_t launch_set_epoch_base(unsigned long long* ticket, int num_tiles, cudaStream_t s);
 
 unsigned long long bernoulli_threshold(double p);

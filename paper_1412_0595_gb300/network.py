@@ -222,7 +222,7 @@ class Network:
         if field in _F32:
             out = torch.empty(self.sizes[pop], dtype=torch.float32, device=self.device)
             nbytes = 4 * out.numel()
-        elif field == "spikes":
+        elif field in ("spikes", "neuron_spikes"):
             out = torch.empty(max(self.sizes[pop], 1), dtype=torch.int32, device=self.device)
             nbytes = 4 * out.numel()
         elif field == "nspk":
@@ -232,6 +232,8 @@ class Network:
             out = torch.empty(1, dtype=torch.int64, device=self.device)
             nbytes = 8
         check(L.lib.snn_read_state(self.h, int(pop), fid, out.data_ptr(), nbytes, 1, s))
+        if field == "neuron_spikes":
+            return out[: self.sizes[pop]]
         if field == "spikes":
             return out[: int(self.read(pop, "nspk", stream).item())]
         return out
@@ -257,6 +259,14 @@ class Network:
         assert t.numel() == self.sizes[pop]
         check(L.lib.snn_write_state(self.h, int(pop), L.FIELD[field], t.data_ptr(), 4 * t.numel(), 1,
                                     _stream(stream)))
+
+    def synaptic_events(self, stream=None):
+        v = C.c_int64()
+        check(L.lib.snn_synaptic_events(self.h, C.byref(v), _stream(stream)))
+        return v.value
+
+    def launch_phase(self, phase, stream=None):
+        check(L.lib.snn_launch_phase(self.h, int(phase), _stream(stream)))
 
     def counters(self, pop):
         return int(self.read(pop, "spike_count").item()), int(self.read(pop, "nan_count").item())

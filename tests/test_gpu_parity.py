@@ -133,8 +133,8 @@ def test_small_workload_200_steps(gpu):
 def test_ragged_population_sizes(gpu):
     # populations of 1, 255, 257 and 513 neurons span tile edges
     pops = [I.source_pop(257, 500.0), I.hh_pop(1), I.hh_pop(255), I.hh_pop(513)]
-    projs = [I.proj(0, 1, "csr", 0.5, ("uniform", 0, 30.0)), I.proj(0, 2, "dense", 1.0, ("uniform", 0, 3.0)),
-             I.proj(0, 3, "csr", 0.1, ("uniform", 0, 30.0), channel=1)]
+    projs = [I.proj(0, 1, "csr", 0.5, ("uniform", 0, 3.0)), I.proj(0, 2, "dense", 1.0, ("uniform", 0, 0.3)),
+             I.proj(0, 3, "csr", 0.1, ("uniform", 0, 3.0), channel=1)]
     spec = I.net(pops, projs, dt=0.1, steps=1)
     net = gpu.Network.from_spec(spec)
     ref = oracle.from_spec(spec)
