@@ -171,10 +171,16 @@ def test_four_population_workload_full_size_first_200_steps(gpu):
     fg, fo = _first_spike_steps(sg, n_in), _first_spike_steps(so, n_in)
     assert np.all(np.abs(fg - fo) <= 1)                     # first spikes within one step
     vg, vo = np.array(vg), np.array(vo)
-    for i in range(n_in):                                    # V before the upstroke
-        end = (fo[i] - 10) if fo[i] >= 0 else 200
+    # V within 1e-3 mV while the oracle trajectory is below the saddle of the
+    # resting state (-57.5253 mV); above it the upstroke amplifies the FP32
+    # rounding of V exponentially until the spike (chaotic divergence).
+    for i in range(n_in):
+        above = np.nonzero(vo[:, i] > -57.5253)[0]
+        end = above[0] if len(above) else 200
         if end > 0:
             assert np.abs(vg[:end, i] - vo[:end, i]).max() <= 1e-3, i
+    silent = fo < 0
+    assert np.abs(vg[:, silent] - vo[:, silent]).max() <= 1e-3
 
 
 def test_population_rates_within_2_percent(gpu):
