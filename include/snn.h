@@ -228,6 +228,30 @@ snn_status snn_csr_bernoulli_rows(uint64_t seed, uint32_t tag, int64_t n_pre, in
 snn_status snn_csr_bernoulli_fill(uint64_t seed, uint32_t tag, int64_t n_pre, int64_t n_post,
                                   double p, const int64_t* row_ptr, int32_t* col, void* stream);
 
+/* Largest n_pre accepted by snn_csr_bernoulli_rows_noalloc. */
+#define SNN_NOALLOC_MAX_ROWS 16777216
+
+/* Same result as snn_csr_bernoulli_rows (bit for bit), without allocating.
+ * The paper has no counterpart: this entry point exists for callers that
+ * cannot allocate device memory when they build connectivity -- code running
+ * while a CUDA graph is captured in global mode (cudaMalloc is not allowed
+ * there and invalidates the capture), code whose device memory all belongs
+ * to a pool or budget it must stay inside, and latency-sensitive loops that
+ * cannot take the device synchronisation cudaMalloc / cudaFree may imply.
+ * Row counts are written into row_ptr itself; the only scratch is a fixed
+ * array of SNN_NOALLOC_MAX_ROWS / 1024 + 1 int64 (128 KiB) in device memory,
+ * held by every GPU that loads the library until the process exits.
+ * The first call on a device looks up that array's address with the device
+ * current; make that first call before any stream capture.  Every call on a
+ * device shares the array: calls whose GPU work overlaps (different streams,
+ * no ordering between them) race and give wrong rows; calls ordered on one
+ * stream are safe.  Each call writes every scratch entry it reads.
+ * n_pre > SNN_NOALLOC_MAX_ROWS returns SNN_ERR_SIZE before any GPU work.
+ * Calls no cudaMalloc, cudaFree or allocating library routine.
+ * Synchronises `stream`; *nnz (host) receives row_ptr[n_pre]. */
+snn_status snn_csr_bernoulli_rows_noalloc(uint64_t seed, uint32_t tag, int64_t n_pre, int64_t n_post,
+                                          double p, int64_t* row_ptr, int64_t* nnz, void* stream);
+
 /* Message of the last failed call on this thread ("" if none). */
 const char* snn_last_error(void);
 

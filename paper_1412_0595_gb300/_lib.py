@@ -80,6 +80,7 @@ def _load():
         "snn_event_list": [vp, i32, vp, i32, i32, vp, vp, i64, P(i64), vp],
         "snn_csr_bernoulli_rows": [u64, u32, i64, i64, dbl, vp, P(i64), P(Allocator), vp],
         "snn_csr_bernoulli_fill": [u64, u32, i64, i64, dbl, vp, vp, vp],
+        "snn_csr_bernoulli_rows_noalloc": [u64, u32, i64, i64, dbl, vp, P(i64), vp],
     }
     for name, args in sig.items():
         f = getattr(L, name)
