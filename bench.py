@@ -173,6 +173,21 @@ def _flush_l2(buf):
     buf.add_(1.0)
 
 
+def _persistent_time_ms(net, reps, torch):
+    """Average device time of one persistent launch (SNN_OPT_PERSIST_STEPS
+    complete steps), timed with events on the launching stream."""
+    s = torch.cuda.current_stream()
+    net.launch_phase(2)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(s)
+    for _ in range(reps):
+        net.launch_phase(2)
+    e1.record(s)
+    e1.synchronize()
+    net.sync()
+    return e0.elapsed_time(e1) / reps
+
+
 def _phase_time_ms(net, phase, reps, torch):
     """Average device time of one launch of a step phase: `reps` launches
     captured back to back in a CUDA graph and timed with events."""
@@ -253,8 +268,12 @@ def run_ours(a):
     torch.cuda.synchronize()
     spikes = [net.counters(p)[0] for p in range(len(spec["pops"]))]
     ev_total = net.synaptic_events()
+    engine = net.engine
+    PERSIST = 1000
+    net.set_option("persist_steps", PERSIST)
     t_neuron = _phase_time_ms(net, 0, a.phase_reps, torch)
     t_prop = _phase_time_ms(net, 1, a.phase_reps, torch)
+    t_persist = _persistent_time_ms(net, 3, torch) if engine == "persistent" else None
     peaks, src = _peaks()
     sm_mhz = float(peaks.get("sm_max_mhz", 2070.0))
     fp32_peak = SM_COUNT * FP32_LANES * 2 * sm_mhz * 1e6 / 1e12        # TFLOP/s
@@ -273,7 +292,19 @@ def run_ours(a):
     prop_bytes = ((ev_total - dense_ev) * BYTES_PER_EVENT + csr_rows * BYTES_PER_ROW
                   + dense_ev * 4 + dense_rows * 4) / a.steady_steps
     prop_gbs = prop_bytes / (t_prop * 1e-3) / 1e9
-    if t_neuron >= t_prop:
+    other = {"k_neuron_step_us": 1e3 * t_neuron, "k_propagate_us": 1e3 * t_prop,
+             "neuron_tflops": neuron_tflops, "propagate_gbs": prop_gbs}
+    if engine == "persistent":
+        flops = PERSIST * n_hh * flops_per_neuron_step
+        ach = flops / (t_persist * 1e-3) / 1e12
+        roof = {"kernel": "k_step_persistent", "bound": "alu", "achieved": ach, "peak": fp32_peak,
+                "unit": "TFLOP/s", "frac": ach / fp32_peak, "traffic": None,
+                "peak_source": "FP32 FMA peak from 152 SMs x 128 lanes x 2 x max SM clock "
+                               f"({sm_mhz:.0f} MHz, {src})",
+                "launch_us": 1e3 * t_persist, "steps_per_launch": PERSIST, "flops_per_launch": flops,
+                "us_per_step": 1e3 * t_persist / PERSIST}
+        other["k_step_persistent_us_per_step"] = 1e3 * t_persist / PERSIST
+    elif t_neuron >= t_prop:
         roof = {"kernel": "k_neuron_step", "bound": "alu", "achieved": neuron_tflops, "peak": fp32_peak,
                 "unit": "TFLOP/s", "frac": neuron_tflops / fp32_peak, "traffic": None,
                 "peak_source": "FP32 FMA peak from 152 SMs x 128 lanes x 2 x max SM clock "
@@ -284,8 +315,7 @@ def run_ours(a):
         roof = {"kernel": "k_propagate", "bound": "hbm", "achieved": prop_gbs, "peak": hbm, "unit": "GB/s",
                 "frac": prop_gbs / hbm, "traffic": None, "peak_source": f"hbm_gbs ({src})",
                 "launch_us": 1e3 * t_prop, "bytes_per_launch": prop_bytes}
-    roof["other"] = {"k_neuron_step_us": 1e3 * t_neuron, "k_propagate_us": 1e3 * t_prop,
-                     "neuron_tflops": neuron_tflops, "propagate_gbs": prop_gbs}
+    roof["other"] = other
 
     # ---- end to end through the public API from pinned host buffers ----
     e2e = None
@@ -311,7 +341,9 @@ def run_ours(a):
                 "roofline": roof,
                 "cpu_baseline": cpu,
                 "e2e": e2e,
-                "gpu_launches": a.steps * (2 * a.sim_steps + 2),
+                "engine": engine,
+                "gpu_launches": a.steps * ((-(-a.sim_steps // 1000)) + 2 if engine == "persistent"
+                                           else 2 * a.sim_steps + 2),
                 "clocks": clk.summary()}
         print(json.dumps(line), flush=True)
     net.close()

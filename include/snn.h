@@ -62,7 +62,7 @@ enum {
     SNN_FIELD_G1 = 5,          /* float[n], conductance of channel 1 (nS) */
     SNN_FIELD_IEXT = 6,        /* float[n], drive current (pA) */
     SNN_FIELD_ISYN = 7,        /* float[n], synaptic current of the last step (pA); needs SNN_OPT_RECORD_ISYN */
-    SNN_FIELD_SPIKES = 8,      /* int32[nspk], ascending spike list of the last step (read only) */
+    SNN_FIELD_SPIKES = 8,      /* int32[nspk], spike list of the last step, handed out in ascending order (read only) */
     SNN_FIELD_NSPK = 9,        /* int32, length of that list (read only) */
     SNN_FIELD_SPIKE_COUNT = 10,/* int64, spikes since creation or reset (Fig. 1 avgSpike numerator) */
     SNN_FIELD_NAN_COUNT = 11,  /* int64, neuron-steps that ended with a NaN V (Fig. 1 sumNANs) */
@@ -75,7 +75,11 @@ enum {
     SNN_OPT_GRAPH_STEPS = 1,   /* steps per captured CUDA graph, 0 = no graph; default 100 */
     SNN_OPT_PROP_BLOCKS = 2,   /* CTAs of the propagation kernels; 0 = library choice */
     SNN_OPT_CHUNK = 3,         /* synapses per warp work item of the row kernel (multiple of 128) */
-    SNN_OPT_SPIN_LIMIT = 4     /* iterations of a bounded device wait before SNN_ERR_TIMEOUT */
+    SNN_OPT_SPIN_LIMIT = 4,    /* iterations of a bounded device wait before SNN_ERR_TIMEOUT */
+    SNN_OPT_ENGINE = 5,        /* 0 plain (two kernels per step, graph replay), 1 persistent
+                                  (one cooperative launch for many steps), 2 choose (default:
+                                  persistent when every tile gets its own resident CTA) */
+    SNN_OPT_PERSIST_STEPS = 6  /* steps per persistent launch; default 1000 */
 };
 
 /* A population.  kind SNN_POP_HH: Traub-Miles HH neurons with the given
@@ -172,12 +176,16 @@ snn_status snn_read_state(snn_net* net, int32_t pop, int32_t field, void* dst, s
 snn_status snn_write_state(snn_net* net, int32_t pop, int32_t field, const void* src, size_t bytes,
                            int32_t src_is_device, void* stream);
 
-/* Restores the state the network had at creation and sets the step counter
- * (and hence the random-number counters) back to 0.  Enqueued on `stream`. */
+/* Restores the state the network had at creation, sets the step counter
+ * (and hence the random-number counters) back to 0 and clears a sticky
+ * device error.  Enqueued on `stream`. */
 snn_status snn_reset(snn_net* net, void* stream);
 
 /* Sets an SNN_OPT_* option (see the enum). */
 snn_status snn_set_option(snn_net* net, int32_t option, int64_t value);
+
+/* Engine snn_step uses with the current options: 0 plain, 1 persistent. */
+snn_status snn_get_engine(snn_net* net, int32_t* engine);
 
 /* Steps simulated since creation or the last reset (synchronises `stream`). */
 snn_status snn_get_step(snn_net* net, int64_t* step, void* stream);
@@ -188,7 +196,8 @@ snn_status snn_get_step(snn_net* net, int64_t* step, void* stream);
 snn_status snn_synaptic_events(snn_net* net, int64_t* events, void* stream);
 
 /* Launches one phase of a step exactly as snn_step does, for timing single
- * kernels: phase 0 = neuron update with spike compaction, 1 = propagation.
+ * kernels: phase 0 = neuron update with spike compaction, 1 = propagation,
+ * 2 = one persistent launch of SNN_OPT_PERSIST_STEPS complete steps.
  * A neuron phase without its propagation advances the state without
  * delivering spikes.  Enqueued on `stream`. */
 snn_status snn_launch_phase(snn_net* net, int32_t phase, void* stream);

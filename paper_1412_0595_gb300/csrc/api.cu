@@ -150,8 +150,9 @@ snn_status upload_projs(snn_net* net) {
         d.w = P.w;
         d.g = (P.d.channel == 0 ? net->g0 : net->g1) + post.offset;
         d.spk = net->spk + pre.offset;
-        d.nspk = net->nspk + P.d.pre;
+        d.nspk = net->nspk + 2 * P.d.pre;
         d.pre_count = net->nrn_count + pre.offset;
+        d.acc = net->acc + (P.d.channel == 0 ? 0 : 2 * (size_t)std::max(1, net->n_total)) + post.offset;
     }
     if (!dp.empty())
         CK(cudaMemcpy(net->d_projs, dp.data(), dp.size() * sizeof(DevProj), cudaMemcpyHostToDevice),
@@ -167,7 +168,6 @@ NeuronArgs neuron_args(snn_net* net) {
     a.g0 = net->g0; a.g1 = net->g1; a.iext = net->iext;
     a.isyn_rec = net->record_isyn ? net->isyn : nullptr;
     a.ticket = net->ticket;
-    a.tile_status = net->tile_status;
     a.epoch_base = net->ticket + 1;
     a.error = net->error;
     a.num_tiles = net->num_tiles;
@@ -181,11 +181,42 @@ NeuronArgs neuron_args(snn_net* net) {
 
 int prop_blocks(snn_net* net) { return net->prop_blocks > 0 ? net->prop_blocks : net->sm_count * 4; }
 
+bool use_persistent(const snn_net* net) {
+    if (net->engine == 1) return net->persist_grid > 0;
+    if (net->engine == 0) return false;
+    return net->num_tiles > 0 && net->num_tiles <= net->persist_grid;   // one resident CTA per tile
+}
+
+PersistArgs persist_args(snn_net* net, int32_t n_steps) {
+    PersistArgs p{};
+    p.n = neuron_args(net);
+    p.projs = net->d_projs;
+    p.out_begin = net->out_begin;
+    p.out_list = net->out_list;
+    const size_t NT = std::max<size_t>(1, (size_t)net->n_total);
+    p.acc0 = net->acc;
+    p.acc1 = net->acc + 2 * NT;
+    p.acc_stride = (int32_t)NT;
+    p.n_steps = n_steps;
+    p.bar = net->bar;
+    return p;
+}
+
+cudaError_t enqueue_persistent(snn_net* net, int64_t n_steps, cudaStream_t s) {
+    while (n_steps > 0) {
+        const int32_t k = (int32_t)std::min<int64_t>(n_steps, net->persist_steps);
+        cudaError_t e = launch_persistent(persist_args(net, k), net->persist_grid, s);
+        if (e != cudaSuccess) return e;
+        n_steps -= k;
+    }
+    return cudaSuccess;
+}
+
 cudaError_t enqueue_step(snn_net* net, cudaStream_t s) {
     cudaError_t e = launch_neuron_step(neuron_args(net), s);
     if (e != cudaSuccess) return e;
     if (!net->projs.empty()) {
-        PropArgs p{net->d_projs, (int32_t)net->projs.size(), net->chunk};
+        PropArgs p{net->d_projs, (int32_t)net->projs.size(), net->chunk, net->ticket, net->num_tiles};
         e = launch_propagate(p, prop_blocks(net), s);
     }
     return e;
@@ -306,21 +337,25 @@ snn_status create_impl(const snn_pop_desc* pops, int32_t n_pops, const snn_proj_
     TRY(dalloc(net, &net->spk, NT, "spike lists"));
     TRY(dalloc(net, &net->nrn_count, NT, "per-neuron spike counts"));
     TRY(dalloc(net, &net->d_events, 1, "event counter"));
+    TRY(dalloc(net, &net->acc, 4 * NT, "event accumulators"));
+    TRY(dalloc(net, &net->bar, 1, "grid barrier"));
+    TRY(dalloc(net, &net->out_begin, (size_t)n_pops + 1, "outgoing projection offsets"));
+    TRY(dalloc(net, &net->out_list, std::max<size_t>(1, (size_t)n_projs), "outgoing projections"));
+    CK(cudaMemsetAsync(net->acc, 0, 4 * NT * sizeof(float), s), "clear");
+    CK(cudaMemsetAsync(net->bar, 0, sizeof(GridBarrier), s), "clear");
     CK(cudaMemsetAsync(net->nrn_count, 0, NT * sizeof(int32_t), s), "clear");
-    TRY(dalloc(net, &net->nspk, (size_t)n_pops, "spike counts"));
+    TRY(dalloc(net, &net->nspk, 2 * (size_t)n_pops, "spike list lengths"));
     TRY(dalloc(net, &net->counters, 2 * (size_t)n_pops, "counters"));
     TRY(dalloc(net, &net->ticket, 2, "ticket"));
-    TRY(dalloc(net, &net->tile_status, std::max<size_t>(1, (size_t)tiles), "tile status"));
     TRY(dalloc(net, &net->tile_pop, std::max<size_t>(1, (size_t)tiles), "tile map"));
     TRY(dalloc(net, &net->error, 1, "error word"));
     TRY(dalloc(net, &net->d_pops, (size_t)n_pops, "population descriptors"));
     TRY(dalloc(net, &net->d_projs, std::max<size_t>(1, (size_t)n_projs), "projection descriptors"));
     TRY(dalloc(net, &net->d_dbg_proj, 1, "debug descriptor"));
     CK(cudaMemsetAsync(state, 0, 8 * NT * sizeof(float), s), "clear state");
-    CK(cudaMemsetAsync(net->nspk, 0, sizeof(int32_t) * n_pops, s), "clear");
+    CK(cudaMemsetAsync(net->nspk, 0, sizeof(int32_t) * 2 * n_pops, s), "clear");
     CK(cudaMemsetAsync(net->counters, 0, sizeof(unsigned long long) * 2 * n_pops, s), "clear");
     CK(cudaMemsetAsync(net->ticket, 0, 2 * sizeof(unsigned long long), s), "clear");
-    CK(cudaMemsetAsync(net->tile_status, 0, sizeof(unsigned long long) * std::max<int64_t>(1, tiles), s), "clear");
     CK(cudaMemsetAsync(net->error, 0, sizeof(uint32_t), s), "clear");
 
     // ---- initial potentials, population descriptors, tile map ----
@@ -355,7 +390,7 @@ snn_status create_impl(const snn_pop_desc* pops, int32_t n_pops, const snn_proj_
         q.thr_src = d.kind == SNN_POP_SOURCE ? bernoulli_threshold(d.src_rate_hz * dt * 1e-3) : 0ull;
         q.thr_drive = d.kind == SNN_POP_HH ? bernoulli_threshold(d.drive_rate_hz * dt * 1e-3) : 0ull;
         q.spk = net->spk + P.offset;
-        q.nspk = net->nspk + k;
+        q.nspk = net->nspk + 2 * k;
         q.spike_count = net->counters + 2 * k;
         q.nan_count = net->counters + 2 * k + 1;
         q.neuron_spikes = net->nrn_count + P.offset;
@@ -438,6 +473,22 @@ snn_status create_impl(const snn_pop_desc* pops, int32_t n_pops, const snn_proj_
         CK(cudaStreamSynchronize(s), "synchronize");
         for (int q = 0; q < n_projs; ++q) net->projs[q].max_row = mx[q];
     }
+    {   // projections grouped by pre population, for the persistent engine's pushes
+        std::vector<int32_t> begin((size_t)n_pops + 1, 0), list;
+        for (int k = 0; k < n_pops; ++k) {
+            begin[k] = (int32_t)list.size();
+            for (int q = 0; q < n_projs; ++q)
+                if (net->projs[q].d.pre == k) list.push_back(q);
+        }
+        begin[n_pops] = (int32_t)list.size();
+        if (list.empty()) list.push_back(0);
+        CK(cudaMemcpyAsync(net->out_begin, begin.data(), begin.size() * sizeof(int32_t), cudaMemcpyHostToDevice, s),
+           "upload outgoing offsets");
+        CK(cudaMemcpyAsync(net->out_list, list.data(), list.size() * sizeof(int32_t), cudaMemcpyHostToDevice, s),
+           "upload outgoing projections");
+        CK(cudaStreamSynchronize(s), "synchronize");
+    }
+    CK(persistent_capacity(net->sm_count, &net->persist_grid), "persistent occupancy");
     TRY(upload_projs(net));
     // save the creation state for snn_reset
     CK(cudaMemcpyAsync(net->init_state, net->V, 7 * NT * sizeof(float), cudaMemcpyDeviceToDevice, s),
@@ -487,6 +538,10 @@ snn_status snn_step(snn_net* net, int64_t n_steps, void* stream) {
     if (!net || n_steps < 0) return fail(SNN_ERR_INVALID_ARG, "bad network or step count");
     cudaStream_t s = (cudaStream_t)stream;
     try {
+        if (use_persistent(net)) {
+            CK(enqueue_persistent(net, n_steps, s), "persistent steps");
+            return SNN_OK;
+        }
         int64_t left = n_steps;
         if (net->graph_steps > 0 && left >= net->graph_steps) {
             TRY(ensure_graph(net));
@@ -519,15 +574,31 @@ snn_status snn_read_state(snn_net* net, int32_t pop, int32_t field, void* dst, s
         const size_t need = sizeof(float) * (size_t)P.d.n;
         if (bytes < need) return fail(SNN_ERR_SIZE, "destination smaller than n floats");
         if (P.d.n) CK(cudaMemcpyAsync(dst, field_base(net, field) + P.offset, need, kind, s), "copy field");
-    } else if (field == SNN_FIELD_NSPK) {
-        if (bytes < sizeof(int32_t)) return fail(SNN_ERR_SIZE, "destination smaller than 4 bytes");
-        CK(cudaMemcpyAsync(dst, net->nspk + pop, sizeof(int32_t), kind, s), "copy count");
-    } else if (field == SNN_FIELD_SPIKES) {
-        int32_t ns = 0;
-        CK(cudaMemcpyAsync(&ns, net->nspk + pop, sizeof(int32_t), cudaMemcpyDeviceToHost, s), "read count");
+    } else if (field == SNN_FIELD_NSPK || field == SNN_FIELD_SPIKES) {
+        // the list of the last completed step: parity slot of epoch ticket / num_tiles - 1
+        unsigned long long tk = 0;
+        int32_t cnt[2] = {0, 0};
+        CK(cudaMemcpyAsync(&tk, net->ticket, sizeof(tk), cudaMemcpyDeviceToHost, s), "read ticket");
+        CK(cudaMemcpyAsync(cnt, net->nspk + 2 * pop, sizeof(cnt), cudaMemcpyDeviceToHost, s), "read counts");
         CK(cudaStreamSynchronize(s), "synchronize");
-        if (bytes < sizeof(int32_t) * (size_t)ns) return fail(SNN_ERR_SIZE, "destination smaller than the spike list");
-        if (ns) CK(cudaMemcpyAsync(dst, net->spk + P.offset, sizeof(int32_t) * ns, kind, s), "copy spikes");
+        const unsigned long long done = net->num_tiles ? tk / (unsigned long long)net->num_tiles : 0;
+        const int32_t ns = done ? cnt[(done - 1) & 1] : 0;
+        if (field == SNN_FIELD_NSPK) {
+            if (bytes < sizeof(int32_t)) return fail(SNN_ERR_SIZE, "destination smaller than 4 bytes");
+            CK(cudaMemcpyAsync(dst, &ns, sizeof(int32_t), dst_is_device ? cudaMemcpyHostToDevice
+                                                                           : cudaMemcpyHostToHost, s), "copy count");
+        } else {
+            if (bytes < sizeof(int32_t) * (size_t)ns) return fail(SNN_ERR_SIZE, "destination smaller than the spike list");
+            std::vector<int32_t> list((size_t)ns);
+            if (ns) {
+                CK(cudaMemcpyAsync(list.data(), net->spk + P.offset, sizeof(int32_t) * ns, cudaMemcpyDeviceToHost, s),
+                   "copy spikes");
+                CK(cudaStreamSynchronize(s), "synchronize");
+                std::sort(list.begin(), list.end());      // ascending neuron index
+                CK(cudaMemcpyAsync(dst, list.data(), sizeof(int32_t) * ns,
+                                   dst_is_device ? cudaMemcpyHostToDevice : cudaMemcpyHostToHost, s), "copy spikes");
+            }
+        }
     } else if (field == SNN_FIELD_NEURON_SPIKES) {
         const size_t need = sizeof(int32_t) * (size_t)P.d.n;
         if (bytes < need) return fail(SNN_ERR_SIZE, "destination smaller than n int32");
@@ -566,9 +637,12 @@ snn_status snn_reset(snn_net* net, void* stream) {
     const size_t NT = std::max<size_t>(1, (size_t)net->n_total);
     CK(cudaMemcpyAsync(net->V, net->init_state, 7 * NT * sizeof(float), cudaMemcpyDeviceToDevice, s), "restore");
     CK(cudaMemsetAsync(net->isyn, 0, NT * sizeof(float), s), "clear");
-    CK(cudaMemsetAsync(net->nspk, 0, sizeof(int32_t) * net->pops.size(), s), "clear");
+    CK(cudaMemsetAsync(net->nspk, 0, sizeof(int32_t) * 2 * net->pops.size(), s), "clear");
     CK(cudaMemsetAsync(net->counters, 0, sizeof(unsigned long long) * 2 * net->pops.size(), s), "clear");
     CK(cudaMemsetAsync(net->nrn_count, 0, NT * sizeof(int32_t), s), "clear");
+    CK(cudaMemsetAsync(net->acc, 0, 4 * NT * sizeof(float), s), "clear");
+    CK(cudaMemsetAsync(net->bar, 0, sizeof(GridBarrier), s), "clear");
+    CK(cudaMemsetAsync(net->error, 0, sizeof(uint32_t), s), "clear");
     CK(launch_set_epoch_base(net->ticket, net->num_tiles, s), "reset step counter");
     return SNN_OK;
 }
@@ -594,9 +668,24 @@ snn_status snn_set_option(snn_net* net, int32_t option, int64_t value) {
         if (value < 1 || value > (int64_t)1 << 31) return fail(SNN_ERR_INVALID_ARG, "spin limit in 1..2^31");
         net->spin_limit = (uint32_t)value;
         break;
+    case SNN_OPT_ENGINE:
+        if (value < 0 || value > 2) return fail(SNN_ERR_INVALID_ARG, "engine: 0 plain, 1 persistent, 2 choose");
+        if (value == 1 && net->persist_grid <= 0) return fail(SNN_ERR_STATE, "persistent kernel cannot be resident");
+        net->engine = (int32_t)value;
+        break;
+    case SNN_OPT_PERSIST_STEPS:
+        if (value < 1 || value > (1 << 24)) return fail(SNN_ERR_INVALID_ARG, "persistent steps in 1..2^24");
+        net->persist_steps = (int32_t)value;
+        break;
     default: return fail(SNN_ERR_INVALID_ARG, "unknown option");
     }
     drop_graph(net);
+    return SNN_OK;
+}
+
+snn_status snn_get_engine(snn_net* net, int32_t* engine) {
+    if (!net || !engine) return fail(SNN_ERR_INVALID_ARG, "bad argument");
+    *engine = use_persistent(net) ? 1 : 0;
     return SNN_OK;
 }
 
@@ -622,12 +711,15 @@ snn_status snn_synaptic_events(snn_net* net, int64_t* events, void* stream) {
 }
 
 snn_status snn_launch_phase(snn_net* net, int32_t phase, void* stream) {
-    if (!net || phase < 0 || phase > 1) return fail(SNN_ERR_INVALID_ARG, "bad network or phase");
+    if (!net || phase < 0 || phase > 2) return fail(SNN_ERR_INVALID_ARG, "bad network or phase");
     cudaStream_t s = (cudaStream_t)stream;
-    if (phase == 0) {
+    if (phase == 2) {
+        if (net->persist_grid <= 0) return fail(SNN_ERR_STATE, "persistent kernel cannot be resident");
+        CK(launch_persistent(persist_args(net, net->persist_steps), net->persist_grid, s), "persistent phase");
+    } else if (phase == 0) {
         CK(launch_neuron_step(neuron_args(net), s), "neuron phase");
     } else if (!net->projs.empty()) {
-        PropArgs p{net->d_projs, (int32_t)net->projs.size(), net->chunk};
+        PropArgs p{net->d_projs, (int32_t)net->projs.size(), net->chunk, net->ticket, net->num_tiles};
         CK(launch_propagate(p, prop_blocks(net), s), "propagation phase");
     }
     return SNN_OK;
@@ -662,14 +754,15 @@ static snn_status stage_spikes(snn_net* net, int32_t proj, const int32_t* spk, i
     for (int32_t k = 0; k < n; ++k)
         if (h[k] < 0 || h[k] >= n_pre || (k && h[k] <= h[k - 1]))
             return fail(SNN_ERR_INVALID_ARG, "spike list must be ascending indices of the pre population");
-    if (net->dbg_cap < n + 1) {
+    if (net->dbg_cap < n + 2) {
         int32_t* p = nullptr;
-        TRY(dalloc(net, &p, (size_t)n + 1, "debug spikes"));
+        TRY(dalloc(net, &p, (size_t)n + 2, "debug spikes"));
         net->d_dbg_spk = p;
-        net->dbg_cap = n + 1;
+        net->dbg_cap = n + 2;
     }
-    h.push_back(n);   // count stored after the list
-    CK(cudaMemcpyAsync(net->d_dbg_spk, h.data(), sizeof(int32_t) * (n + 1), cudaMemcpyHostToDevice, s), "stage");
+    h.push_back(n);   // the count, in both parity slots, after the list
+    h.push_back(n);
+    CK(cudaMemcpyAsync(net->d_dbg_spk, h.data(), sizeof(int32_t) * (n + 2), cudaMemcpyHostToDevice, s), "stage");
     CK(cudaStreamSynchronize(s), "synchronize");
     return SNN_OK;
 }
@@ -686,7 +779,7 @@ snn_status snn_debug_propagate(snn_net* net, int32_t proj, const int32_t* spk, i
         d.spk = net->d_dbg_spk;
         d.nspk = net->d_dbg_spk + n;
         CK(cudaMemcpyAsync(net->d_dbg_proj, &d, sizeof(d), cudaMemcpyHostToDevice, s), "write descriptor");
-        PropArgs p{net->d_dbg_proj, 1, net->chunk};
+        PropArgs p{net->d_dbg_proj, 1, net->chunk, net->ticket, std::max(1, net->num_tiles)};
         CK(launch_propagate(p, prop_blocks(net), s), "propagate");
         return sticky(net, s);
     } catch (...) {

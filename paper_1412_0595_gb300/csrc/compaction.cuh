@@ -1,0 +1,42 @@
+// Spike compaction shared by the step kernels.  A warp ballot and a CTA scan
+// order a tile's spikes by neuron index; the tile then claims a contiguous
+// slot range of its population's list with one atomic add.  Tiles never wait
+// for each other, so the list is ascending within each tile and the tiles'
+// ranges follow completion order (the C-ABI sorts when it hands the list out).
+// List lengths are double-buffered by step parity: step e counts into slot
+// e & 1 and clears slot (e + 1) & 1, which the previous step's consumers have
+// finished reading by then.
+#pragma once
+
+#include "snn_internal.cuh"
+
+namespace snn {
+
+// Called by every thread of the CTA (kTile threads) with its spike flag.
+// Returns the tile's spike total; s_off[warp] receives warp offsets within
+// the tile and *s_base the claimed start in the population list.
+__device__ __forceinline__ int tile_claim(bool spike, unsigned ballot, int* s_off, int* s_total, int* s_base,
+                                          int32_t* nspk_slot) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (lane == 0) s_off[warp] = __popc(ballot);
+    __syncthreads();
+    if (warp == 0) {
+        const int c = lane < kTile / 32 ? s_off[lane] : 0;
+        int incl = c;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int y = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= o) incl += y;
+        }
+        if (lane < kTile / 32) s_off[lane] = incl - c;
+        if (lane == 31) {
+            *s_total = incl;
+            *s_base = incl ? atomicAdd(nspk_slot, incl) : 0;
+        }
+    }
+    __syncthreads();
+    (void)spike;
+    return *s_total;
+}
+
+}  // namespace snn

@@ -46,25 +46,60 @@ __device__ __forceinline__ float linoid(float x) {
     return x / expm1f(x);
 }
 
+// Taylor series of x / (exp(x) - 1) about 0 to x^4 (Bernoulli numbers
+// B1 = -1/2, B2 = 1/6, B4 = -1/30): 1 - x/2 + x^2/12 - x^4/720; the first
+// omitted term is x^6/30240, below 2e-11 for |x| < 0.1.
+__device__ __forceinline__ float linoid_series(float x) {
+    const float x2 = x * x;
+    return fmaf(x2, fmaf(x2, -1.0f / 720.0f, 1.0f / 12.0f), fmaf(-0.5f, x, 1.0f));
+}
+
 struct HHCell {
     float gNa, ENa, gK, EK, gL, EL;
 };
 
+// Traub-Miles rates at V with four hardware exponentials and four
+// reciprocals.  Algebraic identities used (exact in real arithmetic):
+//   E = exp((V + 25)/5) serves beta_m = 1.4 y / (E - 1), y = (V + 25)/5,
+//   beta_h = 4 / (1/E + 1) = 4 E / (E + 1), and
+//   alpha_n = 0.16 z / (exp(z) - 1) with exp(z) = exp(-5) / E, z = (-50 - V)/5,
+//   so alpha_n = 0.16 z E / (exp(-5) - E).
+// Linoid rates switch to the series for |argument| < 0.1, where exp(x) - 1
+// would lose digits to cancellation.
+struct HHRates {
+    float am, bm, ah, bh, an, bn;
+};
+
+__device__ __forceinline__ HHRates hh_rates(float V) {
+    constexpr float kLog2e = 1.4426950408889634f;
+    constexpr float kExpM5 = 6.737946999085467e-3f;     // exp(-5)
+    const float x = (-52.0f - V) * 0.25f;                // alpha_m argument
+    const float y = (V + 25.0f) * 0.2f;                  // beta_m argument
+    const float z = (-50.0f - V) * 0.2f;                 // alpha_n argument
+    const float Em = exp2f(x * kLog2e);
+    const float E = exp2f(y * kLog2e);
+    const float Eh = exp2f((-48.0f - V) * (kLog2e / 18.0f));
+    const float En = exp2f((-55.0f - V) * (kLog2e / 40.0f));
+    HHRates r;
+    r.am = 1.28f * (fabsf(x) < 0.1f ? linoid_series(x) : __fdividef(x, Em - 1.0f));
+    r.bm = 1.4f * (fabsf(y) < 0.1f ? linoid_series(y) : __fdividef(y, E - 1.0f));
+    r.an = 0.16f * (fabsf(z) < 0.1f ? linoid_series(z) : __fdividef(z * E, kExpM5 - E));
+    r.ah = 0.128f * Eh;
+    r.bh = __fdividef(4.0f * E, E + 1.0f);
+    r.bn = 0.5f * En;
+    return r;
+}
+
 // One forward-Euler substep with every right-hand side at the substep start.
 __device__ __forceinline__ void hh_substep(const HHCell& c, float hs, float hs_over_C, float I_in,
                                            float& V, float& m, float& h, float& n) {
-    const float am = 1.28f * linoid((-52.0f - V) * 0.25f);
-    const float bm = 1.4f * linoid((V + 25.0f) * 0.2f);
-    const float ah = 0.128f * expf((-48.0f - V) * (1.0f / 18.0f));
-    const float bh = 4.0f / (expf((-25.0f - V) * 0.2f) + 1.0f);
-    const float an = 0.16f * linoid((-50.0f - V) * 0.2f);
-    const float bn = 0.5f * expf((-55.0f - V) * 0.025f);
+    const HHRates r = hh_rates(V);
     const float m3h = m * m * m * h;
     const float n2 = n * n;
     const float I = I_in - c.gNa * m3h * (V - c.ENa) - c.gK * (n2 * n2) * (V - c.EK) - c.gL * (V - c.EL);
-    const float dm = am * (1.0f - m) - bm * m;
-    const float dh = ah * (1.0f - h) - bh * h;
-    const float dn = an * (1.0f - n) - bn * n;
+    const float dm = r.am * (1.0f - m) - r.bm * m;
+    const float dh = r.ah * (1.0f - h) - r.bh * h;
+    const float dn = r.an * (1.0f - n) - r.bn * n;
     V = fmaf(hs_over_C, I, V);
     m = fmaf(hs, dm, m);
     h = fmaf(hs, dh, h);
@@ -95,6 +130,10 @@ __device__ __forceinline__ unsigned long long ld_acquire_u64(const unsigned long
 
 __device__ __forceinline__ void st_release_u64(unsigned long long* p, unsigned long long v) {
     asm volatile("st.release.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+
+__device__ __forceinline__ void st_release_u32(unsigned int* p, unsigned int v) {
+    asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
 }
 
 __device__ __forceinline__ uint32_t ld_acquire_u32(const uint32_t* p) {

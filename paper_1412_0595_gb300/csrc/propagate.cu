@@ -22,8 +22,8 @@ constexpr int kPropThreads = 256;
 constexpr int kDenseRows = 32;     // spiking rows per dense item
 constexpr int kDensePosts = 128;   // posts per dense item (32 lanes x 4)
 
-__device__ __forceinline__ int64_t items_of(const DevProj& q) {
-    const int64_t ns = *q.nspk;
+__device__ __forceinline__ int64_t items_of(const DevProj& q, int slot) {
+    const int64_t ns = q.nspk[slot];
     if (q.layout == SNN_LAYOUT_CSR) return ns * q.chunks;
     return ((ns + kDenseRows - 1) / kDenseRows) * q.chunks;
 }
@@ -50,10 +50,10 @@ __device__ __forceinline__ void csr_item(const DevProj& q, int64_t r, int chunk,
     }
 }
 
-__device__ __forceinline__ void dense_item(const DevProj& q, int64_t r, int lane) {
+__device__ __forceinline__ void dense_item(const DevProj& q, int64_t r, int lane, int slot) {
     const int64_t sb = r / q.chunks;
     const int pb = (int)(r - sb * q.chunks);
-    const int ns = *q.nspk;
+    const int ns = q.nspk[slot];
     const int s_beg = (int)sb * kDenseRows;
     const int s_end = min(ns, s_beg + kDenseRows);
     const int n_post = q.n_post;
@@ -88,13 +88,15 @@ __device__ __forceinline__ void dense_item(const DevProj& q, int64_t r, int lane
 __global__ void __launch_bounds__(kPropThreads) k_propagate(const PropArgs a) {
     extern __shared__ int64_t s_pref[];   // n_projs + 1 item offsets
     const int np = a.n_projs;
+    // list-length slot of the step whose spikes are delivered
+    const int slot = (int)((*a.ticket / (unsigned long long)a.num_tiles + 1ull) & 1ull);
     // Item offsets of every projection (warp 0 scans 32 projections at a time).
     if (threadIdx.x < 32) {
         const int lane = threadIdx.x;
         int64_t run = 0;
         for (int b = 0; b < np; b += 32) {
             const int q = b + lane;
-            const int64_t v = q < np ? items_of(a.projs[q]) : 0;
+            const int64_t v = q < np ? items_of(a.projs[q], slot) : 0;
             int64_t incl = v;
 #pragma unroll
             for (int o = 1; o < 32; o <<= 1) {
@@ -117,12 +119,12 @@ __global__ void __launch_bounds__(kPropThreads) k_propagate(const PropArgs a) {
         const DevProj& Q = a.projs[q];
         const int64_t r = item - s_pref[q];
         if (Q.layout == SNN_LAYOUT_CSR) csr_item(Q, r, a.chunk, lane);
-        else dense_item(Q, r, lane);
+        else dense_item(Q, r, lane, slot);
     }
 }
 
 cudaError_t launch_propagate(const PropArgs& a, int blocks, cudaStream_t s) {
-    if (a.n_projs == 0) return cudaSuccess;
+    if (a.n_projs == 0 || a.num_tiles == 0) return cudaSuccess;
     const size_t smem = sizeof(int64_t) * (size_t)(a.n_projs + 1);
     if (smem > 48 * 1024) {
         cudaError_t e = cudaFuncSetAttribute(k_propagate, cudaFuncAttributeMaxDynamicSharedMemorySize,

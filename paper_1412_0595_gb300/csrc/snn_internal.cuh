@@ -26,11 +26,6 @@ constexpr uint32_t kStreamSource = 1u;
 constexpr uint32_t kStreamDrive = 2u;
 constexpr uint32_t kStreamCsr = 3u;
 
-// Tile status word of the ordered spike compaction:
-// [63:32] step epoch, [31:30] flag (1 = tile total, 2 = inclusive prefix), [29:0] count.
-constexpr unsigned long long kFlagAgg = 1ull << 30;
-constexpr unsigned long long kFlagPrefix = 2ull << 30;
-constexpr unsigned long long kCountMask = (1ull << 30) - 1;
 
 struct DevPop {
     int32_t kind;          // SNN_POP_HH or SNN_POP_SOURCE
@@ -47,8 +42,8 @@ struct DevPop {
     float drive_amp, drive_dec;
     unsigned long long thr_src;    // Bernoulli thresholds round(p * 2^32)
     unsigned long long thr_drive;
-    int32_t* spk;          // spike list of the last step
-    int32_t* nspk;
+    int32_t* spk;          // spike list of the last step (ascending within each tile)
+    int32_t* nspk;         // [2] list lengths, slot e & 1 for step epoch e
     unsigned long long* spike_count;
     unsigned long long* nan_count;
     int32_t* neuron_spikes;        // per-neuron spike counts of this population
@@ -64,8 +59,17 @@ struct DevProj {
     const float* w;        // nnz (CSR) or n_pre * n_post (dense)
     float* g;              // post conductance channel, already offset to the post population
     const int32_t* spk;    // pre spike list
-    const int32_t* nspk;
+    const int32_t* nspk;   // [2] list lengths of the pre population (slot e & 1)
     const int32_t* pre_count;   // per-neuron spike counts of the pre population
+    float* acc;            // persistent engine: event accumulator (buffer 0), offset to the post population
+};
+
+// Grid barrier of the persistent engine: a monotone arrival counter.  A launch
+// reads `base` once; barrier k of that launch completes when count reaches
+// base + (k + 1) * gridDim.x; block 0 advances base when the launch ends.
+struct GridBarrier {
+    unsigned long long count;
+    unsigned long long base;
 };
 
 struct NeuronArgs {
@@ -73,8 +77,7 @@ struct NeuronArgs {
     const int32_t* tile_pop;       // compaction tile -> population
     float *V, *m, *h, *n, *g0, *g1, *iext;
     float* isyn_rec;               // nullptr unless recording
-    unsigned long long* ticket;    // monotone tile ticket
-    unsigned long long* tile_status;
+    unsigned long long* ticket;    // monotone tile ticket: step epoch = ticket / num_tiles
     const unsigned long long* epoch_base;
     uint32_t* error;
     int32_t num_tiles;
@@ -84,10 +87,24 @@ struct NeuronArgs {
     uint32_t seed_lo, seed_hi;
 };
 
+struct PersistArgs {
+    NeuronArgs n;
+    const DevProj* projs;
+    const int32_t* out_begin;      // [n_pops + 1] offsets into out_list
+    const int32_t* out_list;       // projections grouped by pre population
+    float* acc0;                   // [2][n_total] incoming events, channel 0
+    float* acc1;                   // [2][n_total] incoming events, channel 1
+    int32_t acc_stride;            // n_total
+    int32_t n_steps;
+    GridBarrier* bar;
+};
+
 struct PropArgs {
     const DevProj* projs;
     int32_t n_projs;
     int32_t chunk;                 // synapses per CSR work item
+    const unsigned long long* ticket;   // the step delivered is epoch ticket / num_tiles - 1
+    int32_t num_tiles;
 };
 
 // Memory obtained from the user allocator (or cudaMalloc).
@@ -133,12 +150,18 @@ struct snn_net {
           *iext = nullptr, *isyn = nullptr;
     float* init_state = nullptr;   // 7 * n_total floats saved at creation
     int32_t* spk = nullptr;
-    int32_t* nspk = nullptr;
+    int32_t* nspk = nullptr;                  // [2 * n_pops]
     int32_t* nrn_count = nullptr;             // per-neuron spike counts (n_total)
     unsigned long long* d_events = nullptr;
+    float* acc = nullptr;                     // persistent engine accumulators [2 channels][2 buffers][n_total]
+    int32_t* out_begin = nullptr;
+    int32_t* out_list = nullptr;
+    snn::GridBarrier* bar = nullptr;
+    int32_t engine = 2;                       // 0 plain, 1 persistent, 2 choose
+    int32_t persist_steps = 1000;             // steps per persistent launch
+    int32_t persist_grid = 0;                 // co-resident CTAs of the persistent kernel
     unsigned long long* counters = nullptr;   // 2 * n_pops
     unsigned long long* ticket = nullptr;     // [0] ticket, [1] epoch base
-    unsigned long long* tile_status = nullptr;
     int32_t* tile_pop = nullptr;
     uint32_t* error = nullptr;
     snn::DevPop* d_pops = nullptr;
@@ -191,6 +214,8 @@ cudaError_t launch_csr_fill(uint64_t seed, uint32_t tag, int64_t n_pre, int64_t 
                             unsigned long long thr, const int64_t* row_ptr, int32_t* col,
                             cudaStream_t s);
 cudaError_t launch_count_events(const DevProj* projs, int n_projs, unsigned long long* out, cudaStream_t s);
+cudaError_t persistent_capacity(int sm_count, int* blocks);
+cudaError_t launch_persistent(const PersistArgs& a, int grid, cudaStream_t s);
 cudaError_t launch_set_epoch_base(unsigned long long* ticket, int num_tiles, cudaStream_t s);
 
 unsigned long long bernoulli_threshold(double p);

@@ -199,6 +199,13 @@ class Network:
         check(L.lib.snn_set_option(self.h, L.OPT[name], int(value)))
 
     @property
+    def engine(self):
+        """Engine snn_step uses: 'plain' or 'persistent'."""
+        v = C.c_int32()
+        check(L.lib.snn_get_engine(self.h, C.byref(v)))
+        return "persistent" if v.value == 1 else "plain"
+
+    @property
     def t(self):
         v = C.c_int64()
         check(L.lib.snn_get_step(self.h, C.byref(v), _stream(None)))

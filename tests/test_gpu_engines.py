@@ -1,0 +1,91 @@
+"""The persistent engine (one cooperative launch for many steps, one grid
+barrier per step) against the oracle and against the plain two-kernel engine."""
+import numpy as np
+import pytest
+
+import oracle
+import snn_inputs as I
+
+pytestmark = pytest.mark.gpu
+
+
+def _rel_ok(got, want, rel=1e-5):
+    got = np.asarray(got, np.float64)
+    want = np.asarray(want, np.float64)
+    floor = 1e-5 * np.abs(want).max() if want.size else 0.0
+    return np.all(np.abs(got - want) <= rel * np.maximum(np.abs(want), floor) + 1e-30)
+
+
+def test_small_networks_choose_the_persistent_engine(gpu):
+    net = gpu.Network.from_spec(I.config_four_pop(steps=1))
+    assert net.engine == "persistent"
+    net.set_option("engine", 0)
+    assert net.engine == "plain"
+
+
+def test_persistent_engine_matches_oracle_step_by_step(gpu):
+    pops = [I.source_pop(257, 500.0), I.hh_pop(1), I.hh_pop(255), I.hh_pop(513)]
+    projs = [I.proj(0, 1, "csr", 0.5, ("uniform", 0, 3.0)), I.proj(0, 2, "dense", 1.0, ("uniform", 0, 0.3)),
+             I.proj(0, 3, "csr", 0.1, ("uniform", 0, 3.0), channel=1)]
+    spec = I.net(pops, projs, dt=0.1, steps=1)
+    net = gpu.Network.from_spec(spec)
+    net.set_option("engine", 1)
+    net.set_option("record_isyn", 1)
+    ref = oracle.from_spec(spec)
+    for t in range(60):
+        net.step()
+        ref.step()
+        assert np.array_equal(net.read_host(0, "spikes"), ref.spikes(0)), t
+        for p in (1, 2, 3):
+            assert np.abs(net.read_host(p, "V") - ref.get(p, "V")).max() <= 1e-3, (t, p)
+            assert _rel_ok(net.read_host(p, "isyn"), ref.get(p, "isyn")), (t, p)
+            assert _rel_ok(net.read_host(p, "g0"), ref.get(p, "g0")), (t, p)
+            assert _rel_ok(net.read_host(p, "g1"), ref.get(p, "g1")), (t, p)
+    for p in range(4):
+        assert net.counters(p) == ref.counters(p)
+
+
+def test_persistent_engine_long_launch_matches_oracle(gpu):
+    # forced activity: the HH population spikes, rows are pushed by their owners
+    spec = I.config_small(steps=3000, n_hh=400, n_src=100, p=0.2, weight_hi=60.0)
+    net = gpu.Network.from_spec(spec)
+    assert net.engine == "persistent"
+    net.set_option("persist_steps", 700)        # several launches, ragged last one
+    ref = oracle.from_spec(spec)
+    net.step(spec["steps"])
+    ref.step(spec["steps"])
+    cg, co = net.counters(1)[0], ref.counters(1)[0]
+    assert co > 200 and abs(cg - co) <= 0.02 * co + 1
+    assert net.counters(0) == ref.counters(0)
+    assert net.t == spec["steps"]
+    assert net.synaptic_events() == ref.events or abs(net.synaptic_events() - ref.events) <= 0.02 * ref.events
+
+
+def test_engines_alternate_on_one_trajectory(gpu):
+    spec = I.config_four_pop(steps=300, n_mid=3000)
+    a = gpu.Network.from_spec(spec)
+    b = gpu.Network.from_spec(spec)
+    a.set_option("engine", 0)
+    a.step(300)
+    for eng in (1, 0, 1):
+        b.set_option("engine", eng)
+        b.step(100)
+    for p in range(4):
+        assert np.abs(a.read_host(p, "V") - b.read_host(p, "V")).max() < 1e-4
+        assert np.abs(a.read_host(p, "g0") - b.read_host(p, "g0")).max() <= 1e-6 * (1 + np.abs(a.read_host(p, "g0")).max())
+        assert a.counters(p) == b.counters(p)
+    assert a.t == b.t == 300
+    assert np.array_equal(a.read_host(0, "spikes"), b.read_host(0, "spikes"))
+
+
+def test_persistent_engine_with_more_tiles_than_resident_ctas(gpu):
+    # 400,000 HH neurons = 1563 tiles: CTAs loop over tiles, state goes through HBM
+    spec = I.config_small(steps=40, n_hh=400_000, n_src=100, p=0.001)
+    net = gpu.Network.from_spec(spec)
+    net.set_option("engine", 1)
+    ref = oracle.from_spec(spec)
+    net.step(40)
+    ref.step(40)
+    assert np.abs(net.read_host(1, "V") - ref.get(1, "V")).max() <= 1e-3
+    assert _rel_ok(net.read_host(1, "g0"), ref.get(1, "g0"))
+    assert net.counters(0) == ref.counters(0)
