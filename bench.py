@@ -58,6 +58,10 @@ def _args():
                     help="time steps run before the per-kernel timing")
     ap.add_argument("--phase-reps", type=int, default=200,
                     help="back-to-back launches per kernel in the per-kernel timing")
+    ap.add_argument("--sweep", action="store_true",
+                    help="print one JSON line per point of the scaling sweep instead of the headline line")
+    ap.add_argument("--no-scale-point", action="store_true",
+                    help="skip the forced-activity propagation measurement at 100 x 1,000,000, p = 0.5")
     return ap.parse_args()
 
 
@@ -121,6 +125,68 @@ class Clocks:
         return {"sm_mhz": statistics.median(sm) if sm else None,
                 "sm_max_mhz": float(rows[0][2]) if rows[0][2].replace(".", "").isdigit() else None,
                 "reasons": reasons, "samples": len(rows)}
+
+
+def _forced_propagation(snn, torch, dev, n_mid, p, layout, reps=7, flush=None):
+    """Forced activity: all 100 input rows spike; times the production
+    propagation kernel alone (L2 flushed before each launch) and returns
+    algorithmic bytes / time."""
+    spec = I.net([I.source_pop(100, 0.0), I.hh_pop(n_mid)],
+                 [I.proj(0, 1, layout, p, ("lognormal", -3.0, 0.5))], dt=0.1, steps=1)
+    net = snn.Network.from_spec(spec, device=dev)
+    rows = 100
+    net.debug_propagate(0, np.arange(rows, dtype=np.int32))
+    nnz = net.nnz(0)
+    if layout == "dense":
+        events, nbytes = rows * n_mid, rows * n_mid * 4 + rows * 4
+    else:
+        events, nbytes = nnz, nnz * BYTES_PER_EVENT + rows * BYTES_PER_ROW
+    s = torch.cuda.current_stream()
+    times = []
+    for _ in range(reps):
+        if flush is not None:
+            flush.add_(1.0)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(s)
+        net.launch_phase(3)
+        e1.record(s)
+        e1.synchronize()
+        times.append(e0.elapsed_time(e1))
+    net.sync()
+    net.close()
+    t = statistics.median(times) * 1e-3
+    return {"n_mid": n_mid, "p": p, "layout": layout, "events": events, "bytes": nbytes,
+            "us": t * 1e6, "gbs": nbytes / t / 1e9, "events_per_s": events / t}
+
+
+def _neuron_rate(snn, torch, dev, n, reps=50):
+    spec = I.net([I.hh_pop(n)], [], dt=0.1, steps=1)
+    net = snn.Network.from_spec(spec, device=dev)
+    net.set_option("engine", 0)
+    t = _phase_time_ms(net, 0, reps, torch)
+    net.close()
+    flops = n * (FLOPS_PER_SUBSTEP * 4 + FLOPS_PER_STEP_EXTRA)
+    return {"n": n, "us": t * 1e3, "neuron_steps_per_s": n / (t * 1e-3), "tflops": flops / (t * 1e-3) / 1e12}
+
+
+def run_sweep(a):
+    import torch
+
+    import paper_1412_0595_gb300 as snn
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    peaks, src = _peaks()
+    hbm = float(peaks.get("hbm_gbs", 6800.0))
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)
+    for n in I.SWEEP_N_MID:
+        r = _neuron_rate(snn, torch, dev, n)
+        r["kind"] = "neuron_update"
+        print(json.dumps(r), flush=True)
+        for p in I.SWEEP_P:
+            for layout in ("csr", "dense"):
+                r = _forced_propagation(snn, torch, dev, n, p, layout, flush=flush)
+                r.update(kind="propagation", frac_hbm=r["gbs"] / hbm, hbm_peak=hbm, peak_source=src)
+                print(json.dumps(r), flush=True)
 
 
 def _cpu_baseline(sim_steps):
@@ -317,6 +383,16 @@ def run_ours(a):
                 "launch_us": 1e3 * t_prop, "bytes_per_launch": prop_bytes}
     roof["other"] = other
 
+    # ---- forced-activity propagation at the sweep's largest point ----
+    scale = None
+    if not a.no_scale_point:
+        hbm = float(peaks.get("hbm_gbs", 6800.0))
+        scale = []
+        for layout in ("csr", "dense"):
+            r = _forced_propagation(snn, torch, dev, 1_000_000, 0.5, layout, flush=flush)
+            r["frac_hbm"] = r["gbs"] / hbm
+            scale.append(r)
+
     # ---- end to end through the public API from pinned host buffers ----
     e2e = None
     if not a.no_e2e:
@@ -339,6 +415,7 @@ def run_ours(a):
                 "events_per_step": events / (a.steps * world),
                 "wall_s": wall,
                 "roofline": roof,
+                "propagation_at_scale": scale,
                 "cpu_baseline": cpu,
                 "e2e": e2e,
                 "engine": engine,
@@ -417,7 +494,9 @@ def _e2e(a, spec, dev, torch, snn):
 
 def main():
     a = _args()
-    if a.impl == "reference":
+    if a.sweep:
+        run_sweep(a)
+    elif a.impl == "reference":
         run_reference(a)
     else:
         run_ours(a)

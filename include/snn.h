@@ -79,7 +79,11 @@ enum {
     SNN_OPT_ENGINE = 5,        /* 0 plain (two kernels per step, graph replay), 1 persistent
                                   (one cooperative launch for many steps), 2 choose (default:
                                   persistent when every tile gets its own resident CTA) */
-    SNN_OPT_PERSIST_STEPS = 6  /* steps per persistent launch; default 1000 */
+    SNN_OPT_PERSIST_STEPS = 6, /* steps per persistent launch; default 1000 */
+    SNN_OPT_TILED = 7          /* compressed-row propagation of the plain engine: 0 one warp per
+                                  row chunk with global atomics, 1 post-tiled through shared
+                                  memory, 2 choose (default: post-tiled when a row has
+                                  >= 1024 synapses per 8192-post tile, over > 16384 posts) */
 };
 
 /* A population.  kind SNN_POP_HH: Traub-Miles HH neurons with the given
@@ -197,7 +201,9 @@ snn_status snn_synaptic_events(snn_net* net, int64_t* events, void* stream);
 
 /* Launches one phase of a step exactly as snn_step does, for timing single
  * kernels: phase 0 = neuron update with spike compaction, 1 = propagation,
- * 2 = one persistent launch of SNN_OPT_PERSIST_STEPS complete steps.
+ * 2 = one persistent launch of SNN_OPT_PERSIST_STEPS complete steps,
+ * 3 = the propagation kernel again on the list last staged by
+ * snn_debug_propagate (SNN_ERR_STATE if none).
  * A neuron phase without its propagation advances the state without
  * delivering spikes.  Enqueued on `stream`. */
 snn_status snn_launch_phase(snn_net* net, int32_t phase, void* stream);

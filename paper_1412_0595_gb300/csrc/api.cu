@@ -153,6 +153,10 @@ snn_status upload_projs(snn_net* net) {
         d.nspk = net->nspk + 2 * P.d.pre;
         d.pre_count = net->nrn_count + pre.offset;
         d.acc = net->acc + (P.d.channel == 0 ? 0 : 2 * (size_t)std::max(1, net->n_total)) + post.offset;
+        d.mode = P.mode;
+        d.ptile = kPostTile;
+        d.n_ptiles = (post.d.n + kPostTile - 1) / kPostTile;
+        d.split = P.split;
     }
     if (!dp.empty())
         CK(cudaMemcpy(net->d_projs, dp.data(), dp.size() * sizeof(DevProj), cudaMemcpyHostToDevice),
@@ -180,6 +184,48 @@ NeuronArgs neuron_args(snn_net* net) {
 }
 
 int prop_blocks(snn_net* net) { return net->prop_blocks > 0 ? net->prop_blocks : net->sm_count * 4; }
+
+// Post-tiled propagation pays off when a row has many synapses in each post
+// tile (at least ~1024: density x tile >= 1024) and there are several tiles.
+bool want_tiled(const snn_net* net, const ProjHost& P) {
+    if (P.d.layout != SNN_LAYOUT_CSR || net->tiled == 0) return false;
+    if (net->tiled == 1) return true;
+    const int32_t n_pre = net->pops[P.d.pre].d.n, n_post = net->pops[P.d.post].d.n;
+    if (n_post <= 2 * kPostTile || n_pre == 0) return false;
+    const double per_tile = (double)P.nnz / n_pre * kPostTile / n_post;
+    return per_tile >= 1024.0;
+}
+
+snn_status setup_tiled(snn_net* net, cudaStream_t s) {
+    for (auto& P : net->projs) {
+        P.mode = want_tiled(net, P) ? 1 : 0;
+        if (P.mode == 1 && !P.split) {
+            const int32_t n_pre = net->pops[P.d.pre].d.n, n_post = net->pops[P.d.post].d.n;
+            const int32_t nt = (n_post + kPostTile - 1) / kPostTile;
+            TRY(dalloc(net, &P.split, (size_t)n_pre * (nt + 1) + 1, "row splits"));
+            CK(launch_row_splits(P.row_ptr, P.col, n_pre, nt, kPostTile, P.split, s), "row splits");
+        }
+    }
+    CK(cudaStreamSynchronize(s), "synchronize");
+    return upload_projs(net);
+}
+
+// Propagation of the projections in `dev` (n of them, host copies in `host`).
+cudaError_t launch_projections(snn_net* net, const DevProj* dev, const ProjHost* const* host, int n, cudaStream_t s) {
+    PropArgs p{dev, n, net->chunk, net->ticket, std::max(1, net->num_tiles)};
+    cudaError_t e = launch_propagate(p, prop_blocks(net), s);
+    for (int q = 0; q < n && e == cudaSuccess; ++q)
+        if (host[q]->mode == 1)
+            e = launch_propagate_tiled(dev + q, kPostTile, net->ticket, std::max(1, net->num_tiles), net->sm_count * 4, s);
+    return e;
+}
+
+cudaError_t launch_all_projections(snn_net* net, cudaStream_t s) {
+    if (net->projs.empty()) return cudaSuccess;
+    std::vector<const ProjHost*> host;
+    for (const auto& P : net->projs) host.push_back(&P);
+    return launch_projections(net, net->d_projs, host.data(), (int)host.size(), s);
+}
 
 bool use_persistent(const snn_net* net) {
     if (net->engine == 1) return net->persist_grid > 0;
@@ -215,11 +261,7 @@ cudaError_t enqueue_persistent(snn_net* net, int64_t n_steps, cudaStream_t s) {
 cudaError_t enqueue_step(snn_net* net, cudaStream_t s) {
     cudaError_t e = launch_neuron_step(neuron_args(net), s);
     if (e != cudaSuccess) return e;
-    if (!net->projs.empty()) {
-        PropArgs p{net->d_projs, (int32_t)net->projs.size(), net->chunk, net->ticket, net->num_tiles};
-        e = launch_propagate(p, prop_blocks(net), s);
-    }
-    return e;
+    return launch_all_projections(net, s);
 }
 
 void drop_graph(snn_net* net) {
@@ -489,7 +531,7 @@ snn_status create_impl(const snn_pop_desc* pops, int32_t n_pops, const snn_proj_
         CK(cudaStreamSynchronize(s), "synchronize");
     }
     CK(persistent_capacity(net->sm_count, &net->persist_grid), "persistent occupancy");
-    TRY(upload_projs(net));
+    TRY(setup_tiled(net, s));
     // save the creation state for snn_reset
     CK(cudaMemcpyAsync(net->init_state, net->V, 7 * NT * sizeof(float), cudaMemcpyDeviceToDevice, s),
        "save initial state");
@@ -673,6 +715,11 @@ snn_status snn_set_option(snn_net* net, int32_t option, int64_t value) {
         if (value == 1 && net->persist_grid <= 0) return fail(SNN_ERR_STATE, "persistent kernel cannot be resident");
         net->engine = (int32_t)value;
         break;
+    case SNN_OPT_TILED:
+        if (value < 0 || value > 2) return fail(SNN_ERR_INVALID_ARG, "tiled: 0 off, 1 on, 2 choose");
+        net->tiled = (int32_t)value;
+        TRY(setup_tiled(net, nullptr));
+        break;
     case SNN_OPT_PERSIST_STEPS:
         if (value < 1 || value > (1 << 24)) return fail(SNN_ERR_INVALID_ARG, "persistent steps in 1..2^24");
         net->persist_steps = (int32_t)value;
@@ -711,16 +758,19 @@ snn_status snn_synaptic_events(snn_net* net, int64_t* events, void* stream) {
 }
 
 snn_status snn_launch_phase(snn_net* net, int32_t phase, void* stream) {
-    if (!net || phase < 0 || phase > 2) return fail(SNN_ERR_INVALID_ARG, "bad network or phase");
+    if (!net || phase < 0 || phase > 3) return fail(SNN_ERR_INVALID_ARG, "bad network or phase");
     cudaStream_t s = (cudaStream_t)stream;
-    if (phase == 2) {
+    if (phase == 3) {
+        if (!net->dbg_staged) return fail(SNN_ERR_STATE, "no spike list staged by snn_debug_propagate");
+        const ProjHost* h = &net->projs[net->dbg_proj];
+        CK(launch_projections(net, net->d_dbg_proj, &h, 1, s), "staged propagation");
+    } else if (phase == 2) {
         if (net->persist_grid <= 0) return fail(SNN_ERR_STATE, "persistent kernel cannot be resident");
         CK(launch_persistent(persist_args(net, net->persist_steps), net->persist_grid, s), "persistent phase");
     } else if (phase == 0) {
         CK(launch_neuron_step(neuron_args(net), s), "neuron phase");
-    } else if (!net->projs.empty()) {
-        PropArgs p{net->d_projs, (int32_t)net->projs.size(), net->chunk, net->ticket, net->num_tiles};
-        CK(launch_propagate(p, prop_blocks(net), s), "propagation phase");
+    } else {
+        CK(launch_all_projections(net, s), "propagation phase");
     }
     return SNN_OK;
 }
@@ -779,8 +829,10 @@ snn_status snn_debug_propagate(snn_net* net, int32_t proj, const int32_t* spk, i
         d.spk = net->d_dbg_spk;
         d.nspk = net->d_dbg_spk + n;
         CK(cudaMemcpyAsync(net->d_dbg_proj, &d, sizeof(d), cudaMemcpyHostToDevice, s), "write descriptor");
-        PropArgs p{net->d_dbg_proj, 1, net->chunk, net->ticket, std::max(1, net->num_tiles)};
-        CK(launch_propagate(p, prop_blocks(net), s), "propagate");
+        net->dbg_staged = true;
+        net->dbg_proj = proj;
+        const ProjHost* h = &net->projs[proj];
+        CK(launch_projections(net, net->d_dbg_proj, &h, 1, s), "propagate");
         return sticky(net, s);
     } catch (...) {
         return fail(SNN_ERR_OOM, "host allocation failed");

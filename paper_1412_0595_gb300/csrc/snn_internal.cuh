@@ -62,6 +62,10 @@ struct DevProj {
     const int32_t* nspk;   // [2] list lengths of the pre population (slot e & 1)
     const int32_t* pre_count;   // per-neuron spike counts of the pre population
     float* acc;            // persistent engine: event accumulator (buffer 0), offset to the post population
+    int32_t mode;          // compressed rows: 0 warp per row chunk, 1 post-tiled (own kernel)
+    int32_t n_ptiles;      // post tiles of the post-tiled mode
+    int32_t ptile;         // posts per tile
+    const int64_t* split;  // [n_pre][n_ptiles + 1] first synapse of each row in each post tile
 };
 
 // Grid barrier of the persistent engine: a monotone arrival counter.  A launch
@@ -126,6 +130,8 @@ struct ProjHost {
     float scale;
     int64_t nnz;
     int32_t max_row;
+    int32_t mode = 0;          // 1: post-tiled propagation
+    int64_t* split = nullptr;
     int64_t* row_ptr = nullptr;
     int32_t* col = nullptr;
     float* w = nullptr;
@@ -160,6 +166,7 @@ struct snn_net {
     int32_t engine = 2;                       // 0 plain, 1 persistent, 2 choose
     int32_t persist_steps = 1000;             // steps per persistent launch
     int32_t persist_grid = 0;                 // co-resident CTAs of the persistent kernel
+    int32_t tiled = 2;                        // post-tiled rows: 0 off, 1 all compressed projections, 2 choose
     unsigned long long* counters = nullptr;   // 2 * n_pops
     unsigned long long* ticket = nullptr;     // [0] ticket, [1] epoch base
     int32_t* tile_pop = nullptr;
@@ -169,6 +176,8 @@ struct snn_net {
     snn::DevProj* d_dbg_proj = nullptr;       // one-projection scratch descriptor
     int32_t* d_dbg_spk = nullptr;
     int32_t dbg_cap = 0;
+    bool dbg_staged = false;
+    int32_t dbg_proj = 0;
     // options
     bool record_isyn = false;
     int64_t graph_steps = 100;
@@ -214,6 +223,11 @@ cudaError_t launch_csr_fill(uint64_t seed, uint32_t tag, int64_t n_pre, int64_t 
                             unsigned long long thr, const int64_t* row_ptr, int32_t* col,
                             cudaStream_t s);
 cudaError_t launch_count_events(const DevProj* projs, int n_projs, unsigned long long* out, cudaStream_t s);
+cudaError_t launch_row_splits(const int64_t* row_ptr, const int32_t* col, int32_t n_pre, int32_t n_tiles, int32_t P,
+                              int64_t* split, cudaStream_t s);
+cudaError_t launch_propagate_tiled(const DevProj* q, int32_t P, const unsigned long long* ticket, int32_t num_tiles,
+                                   int blocks, cudaStream_t s);
+constexpr int32_t kPostTile = 8192;          // posts per tile of the post-tiled propagation (32 KiB)
 cudaError_t persistent_capacity(int sm_count, int* blocks);
 cudaError_t launch_persistent(const PersistArgs& a, int grid, cudaStream_t s);
 cudaError_t launch_set_epoch_base(unsigned long long* ticket, int num_tiles, cudaStream_t s);
