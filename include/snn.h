@@ -153,6 +153,29 @@ snn_status snn_create_network(const snn_pop_desc* pops, int32_t n_pops,
                               double dt, int32_t n_substeps, uint64_t seed, uint32_t rng_instance,
                               const snn_allocator* alloc, void* stream, snn_net** out);
 
+/* One network instance of a batch. */
+typedef struct snn_net_desc {
+    const snn_pop_desc* pops;
+    int32_t n_pops;
+    const snn_proj_desc* projs;
+    int32_t n_projs;
+    uint32_t rng_instance;     /* folded into the instance's random-number counters (< 2^24) */
+    int32_t reserved;
+} snn_net_desc;
+
+/* Creates one network object that holds n_instances independent networks of
+ * any sizes (the batched form: many instances with their own conductance
+ * scale factors, as in the paper's sweep over scaling factors, Sec. 2 and
+ * Fig. 1).  Their populations and projections are packed one after another:
+ * instance b's population k becomes population (sum of n_pops of instances
+ * < b) + k of the batch, and likewise for projections, so every other call
+ * (snn_step, snn_read_state, counters) addresses them by those indices.  No
+ * projection crosses instances.  Each instance draws the same random numbers
+ * as a stand-alone network created with its rng_instance.  Up to 4096
+ * populations and 4096 projections in total; errors as snn_create_network. */
+snn_status snn_create_batch(const snn_net_desc* nets, int32_t n_instances, double dt, int32_t n_substeps,
+                            uint64_t seed, const snn_allocator* alloc, void* stream, snn_net** out);
+
 /* Releases the network and all its device memory (synchronises its streams). */
 snn_status snn_destroy(snn_net* net);
 
@@ -266,6 +289,40 @@ snn_status snn_csr_bernoulli_fill(uint64_t seed, uint32_t tag, int64_t n_pre, in
  * Synchronises `stream`; *nnz (host) receives row_ptr[n_pre]. */
 snn_status snn_csr_bernoulli_rows_noalloc(uint64_t seed, uint32_t tag, int64_t n_pre, int64_t n_post,
                                           double p, int64_t* row_ptr, int64_t* nnz, void* stream);
+
+/* ---- checkpoint / resume --------------------------------------------------
+ * A snapshot holds the whole dynamic state: V, m, h, n, conductances, drive
+ * currents, spike lists and lengths, all counters, the persistent engine's
+ * accumulators and the step counter (so random numbers continue where they
+ * left off).  Loading it into the same network (or one created from the same
+ * description) and stepping reproduces the uninterrupted run up to the order
+ * of floating-point atomic adds.  Buffers are host or device; the caller
+ * owns them.  snn_save_state synchronises `stream` and returns a sticky error
+ * first; snn_load_state returns SNN_ERR_STATE for a snapshot of another shape
+ * and SNN_ERR_SIZE for a short buffer. */
+snn_status snn_state_size(snn_net* net, size_t* bytes);
+snn_status snn_save_state(snn_net* net, void* dst, size_t bytes, int32_t dst_is_device, void* stream);
+snn_status snn_load_state(snn_net* net, const void* src, size_t bytes, int32_t src_is_device, void* stream);
+
+/* ---- autotuning ----------------------------------------------------------- */
+typedef struct snn_tuning {
+    int32_t engine;            /* SNN_OPT_ENGINE chosen (0 plain, 1 persistent) */
+    int32_t prop_blocks;       /* SNN_OPT_PROP_BLOCKS */
+    int32_t chunk;             /* SNN_OPT_CHUNK */
+    int32_t tiled;             /* SNN_OPT_TILED */
+    double us_per_step;        /* trial time of the chosen configuration */
+    int32_t cached;            /* 1 if taken from the in-process cache */
+    int32_t reserved;
+} snn_tuning;
+
+/* Times candidate launch configurations (engine, propagation CTAs, row chunk,
+ * post-tiled rows) on trial runs of `trial_steps` steps started from a
+ * snapshot of the current state, applies the fastest, and restores the
+ * snapshot so the simulation continues unchanged.  Results are cached per
+ * device and network shape for the life of the process.  `result` may be
+ * NULL.  Synchronises `stream`.  The paper's own block-size rule is
+ * occupancy-based (Sec. 3); this replaces it with measurement. */
+snn_status snn_autotune(snn_net* net, int32_t trial_steps, snn_tuning* result, void* stream);
 
 /* Message of the last failed call on this thread ("" if none). */
 const char* snn_last_error(void);

@@ -47,6 +47,16 @@ class ProjDesc(C.Structure):
     ]
 
 
+class NetDesc(C.Structure):
+    _fields_ = [("pops", C.POINTER(PopDesc)), ("n_pops", C.c_int32), ("projs", C.POINTER(ProjDesc)),
+                ("n_projs", C.c_int32), ("rng_instance", C.c_uint32), ("reserved", C.c_int32)]
+
+
+class Tuning(C.Structure):
+    _fields_ = [("engine", C.c_int32), ("prop_blocks", C.c_int32), ("chunk", C.c_int32), ("tiled", C.c_int32),
+                ("us_per_step", C.c_double), ("cached", C.c_int32), ("reserved", C.c_int32)]
+
+
 ALLOC_FN = C.CFUNCTYPE(C.c_void_p, C.c_size_t, C.c_void_p, C.c_void_p)
 FREE_FN = C.CFUNCTYPE(None, C.c_void_p, C.c_void_p, C.c_void_p)
 
@@ -65,6 +75,7 @@ def _load():
     P = C.POINTER
     sig = {
         "snn_create_network": ([P(PopDesc), i32, P(ProjDesc), i32, dbl, i32, u64, u32, P(Allocator), vp, P(vp)]),
+        "snn_create_batch": [P(NetDesc), i32, dbl, i32, u64, P(Allocator), vp, P(vp)],
         "snn_destroy": [vp],
         "snn_step": [vp, i64, vp],
         "snn_sync": [vp, vp],
@@ -83,6 +94,10 @@ def _load():
         "snn_csr_bernoulli_rows": [u64, u32, i64, i64, dbl, vp, P(i64), P(Allocator), vp],
         "snn_csr_bernoulli_fill": [u64, u32, i64, i64, dbl, vp, vp, vp],
         "snn_csr_bernoulli_rows_noalloc": [u64, u32, i64, i64, dbl, vp, P(i64), vp],
+        "snn_state_size": [vp, P(sz)],
+        "snn_save_state": [vp, vp, sz, i32, vp],
+        "snn_load_state": [vp, vp, sz, i32, vp],
+        "snn_autotune": [vp, i32, P(Tuning), vp],
     }
     for name, args in sig.items():
         f = getattr(L, name)

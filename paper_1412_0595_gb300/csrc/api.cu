@@ -568,6 +568,43 @@ snn_status snn_create_network(const snn_pop_desc* pops, int32_t n_pops, const sn
     }
 }
 
+snn_status snn_create_batch(const snn_net_desc* nets, int32_t n_instances, double dt, int32_t n_substeps,
+                            uint64_t seed, const snn_allocator* alloc, void* stream, snn_net** out) {
+    try {
+        if (!nets || n_instances < 1) return fail(SNN_ERR_INVALID_ARG, "need at least one instance");
+        std::vector<snn_pop_desc> pops;
+        std::vector<snn_proj_desc> projs;
+        std::vector<uint32_t> tags;
+        for (int b = 0; b < n_instances; ++b) {
+            const snn_net_desc& d = nets[b];
+            if (d.n_pops < 1 || d.n_pops > 256 || !d.pops || d.n_projs < 0 || (d.n_projs > 0 && !d.projs))
+                return fail(SNN_ERR_INVALID_ARG, "instance " + std::to_string(b) + ": bad populations or projections");
+            if (d.rng_instance >= (1u << 24)) return fail(SNN_ERR_INVALID_ARG, "rng_instance must be < 2^24");
+            const int32_t base = (int32_t)pops.size();
+            if (base + d.n_pops > kMaxPops || (int64_t)projs.size() + d.n_projs > kMaxProjs)
+                return fail(SNN_ERR_INVALID_ARG, "at most 4096 populations and 4096 projections in a batch");
+            for (int k = 0; k < d.n_pops; ++k) {
+                pops.push_back(d.pops[k]);
+                tags.push_back((d.rng_instance << 8) | (uint32_t)k);
+            }
+            for (int q = 0; q < d.n_projs; ++q) {
+                snn_proj_desc p = d.projs[q];
+                if (p.pre < 0 || p.pre >= d.n_pops || p.post < 0 || p.post >= d.n_pops)
+                    return fail(SNN_ERR_INVALID_ARG, "instance " + std::to_string(b) + ": projection outside the instance");
+                p.pre += base;
+                p.post += base;
+                projs.push_back(p);
+            }
+        }
+        return create_impl(pops.data(), (int32_t)pops.size(), projs.empty() ? nullptr : projs.data(),
+                           (int32_t)projs.size(), dt, n_substeps, seed, tags, alloc, (cudaStream_t)stream, out);
+    } catch (const std::bad_alloc&) {
+        return fail(SNN_ERR_OOM, "host allocation failed");
+    } catch (...) {
+        return fail(SNN_ERR_INVALID_ARG, "unexpected host exception");
+    }
+}
+
 snn_status snn_destroy(snn_net* net) {
     if (!net) return SNN_OK;
     cudaDeviceSynchronize();

@@ -69,6 +69,86 @@ def csr_bernoulli(seed, tag, n_pre, n_post, p, device=None, stream=None):
     return row_ptr, col[:nnz.value]
 
 
+def _descs(pops, projs, device, keep):
+    """ctypes descriptor arrays for populations and projections (device copies
+    of the arrays are appended to `keep` until the library has copied them)."""
+    P = (L.PopDesc * len(pops))()
+    for k, d in enumerate(pops):
+        p = P[k]
+        p.kind = L.POP_SOURCE if d["kind"] == "source" else L.POP_HH
+        p.n = int(d["n"])
+        for f, v in (d.get("hh") or {}).items():
+            setattr(p, f, float(v))
+        E = d.get("E_syn", (0.0, -92.0))
+        tau = d.get("tau_syn", (1.0, 1.0))
+        p.E_syn[0], p.E_syn[1] = float(E[0]), float(E[1])
+        p.tau_syn[0], p.tau_syn[1] = float(tau[0]), float(tau[1])
+        p.v_thresh = float(d.get("v_thresh", 0.0))
+        p.src_rate_hz = float(d.get("rate_hz", 0.0))
+        drv = d.get("drive") or {}
+        p.drive_rate_hz = float(drv.get("rate_hz", 0.0))
+        p.drive_amp = float(drv.get("amp", 0.0))
+        p.drive_tau = float(drv.get("tau", 0.0))
+        v0 = d.get("v0")
+        if v0 is not None and p.kind == L.POP_HH:
+            t = _dev(v0, torch.float32, device)
+            assert t.numel() == p.n
+            keep.append(t)
+            p.v0, p.v0_on_device = t.data_ptr(), 1
+    Q = (L.ProjDesc * max(len(projs), 1))()
+    for k, d in enumerate(projs):
+        q = Q[k]
+        q.pre, q.post = int(d["pre"]), int(d["post"])
+        q.layout = L.LAYOUT_DENSE if d["layout"] == "dense" else L.LAYOUT_CSR
+        q.channel = int(d.get("channel", 0))
+        q.synapse = L.SYN_GRADED if d.get("synapse") == "graded" else L.SYN_EXP
+        q.on_device = 1
+        w = _dev(d["w"], torch.float32, device)
+        keep.append(w)
+        q.w = w.data_ptr()
+        if d.get("row_ptr") is None:
+            q.input_dense = 1
+            q.nnz = w.numel()
+        else:
+            rp = _dev(d["row_ptr"], torch.int64, device)
+            col = _dev(d["col"], torch.int32, device)
+            keep += [rp, col]
+            q.row_ptr, q.col, q.nnz = rp.data_ptr(), col.data_ptr(), col.numel()
+        q.k1, q.k2, q.k3 = float(d.get("k1", 1.0)), float(d.get("k2", 0.0)), float(d.get("k3", 0.0))
+        q.density = float(d.get("p", d.get("density", 1.0)))
+        q.n_conn = float(d.get("n_conn", 0.0) or 0.0)
+        q.user_scale = float(d.get("user_scale", 1.0))
+        q.v_thr = float(d.get("v_thr", -20.0))
+        q.v_slope = float(d.get("v_slope", 2.0))
+    return P, Q
+
+
+def _spec_arrays(spec, device, stream, inst):
+    """Population and projection dicts of a ``snn_inputs`` description with
+    device arrays: connectivity drawn on the GPU, seeded weights and V0."""
+    import snn_inputs as I
+    pops = []
+    for k, d in enumerate(spec["pops"]):
+        e = dict(d)
+        v0 = I.v0(spec, k)
+        if v0 is not None:
+            e["v0"] = torch.from_numpy(v0).to(device)
+        pops.append(e)
+    projs = []
+    for q, d in enumerate(spec["projs"]):
+        n_pre, n_post = I.n_pre_post(spec, q)
+        e = dict(d)
+        if d["layout"] == "dense" and d["p"] >= 1.0:
+            e["w"] = torch.from_numpy(I.weights(spec, q, n_pre * n_post)).to(device)
+            e["row_ptr"] = None
+        else:
+            rp, col = csr_bernoulli(spec["seed"], I.rng_tag(inst, q), n_pre, n_post, d["p"], device, stream)
+            e["row_ptr"], e["col"] = rp, col
+            e["w"] = torch.from_numpy(I.weights(spec, q, col.numel())).to(device)
+        projs.append(e)
+    return pops, projs
+
+
 class Network:
     """An HH spiking network living on one GPU.
 
@@ -81,61 +161,11 @@ class Network:
 
     def __init__(self, pops, projs, dt, n_sub=4, seed=0, instance=0, device=None, stream=None,
                  torch_alloc=True):
-        self.device = torch.device("cuda") if device is None else torch.device(device)
-        if self.device.index is None:
-            self.device = torch.device("cuda", torch.cuda.current_device())
+        self._setup(device, torch_alloc)
         self.sizes = [int(d["n"]) for d in pops]
         self.n_projs = len(projs)
-        self._alloc = TorchAllocator(self.device.index) if torch_alloc else None
         keep = []
-        P = (L.PopDesc * len(pops))()
-        for k, d in enumerate(pops):
-            p = P[k]
-            p.kind = L.POP_SOURCE if d["kind"] == "source" else L.POP_HH
-            p.n = int(d["n"])
-            for f, v in (d.get("hh") or {}).items():
-                setattr(p, f, float(v))
-            E = d.get("E_syn", (0.0, -92.0))
-            tau = d.get("tau_syn", (1.0, 1.0))
-            p.E_syn[0], p.E_syn[1] = float(E[0]), float(E[1])
-            p.tau_syn[0], p.tau_syn[1] = float(tau[0]), float(tau[1])
-            p.v_thresh = float(d.get("v_thresh", 0.0))
-            p.src_rate_hz = float(d.get("rate_hz", 0.0))
-            drv = d.get("drive") or {}
-            p.drive_rate_hz = float(drv.get("rate_hz", 0.0))
-            p.drive_amp = float(drv.get("amp", 0.0))
-            p.drive_tau = float(drv.get("tau", 0.0))
-            v0 = d.get("v0")
-            if v0 is not None and p.kind == L.POP_HH:
-                t = _dev(v0, torch.float32, self.device)
-                assert t.numel() == p.n
-                keep.append(t)
-                p.v0, p.v0_on_device = t.data_ptr(), 1
-        Q = (L.ProjDesc * max(len(projs), 1))()
-        for k, d in enumerate(projs):
-            q = Q[k]
-            q.pre, q.post = int(d["pre"]), int(d["post"])
-            q.layout = L.LAYOUT_DENSE if d["layout"] == "dense" else L.LAYOUT_CSR
-            q.channel = int(d.get("channel", 0))
-            q.synapse = L.SYN_GRADED if d.get("synapse") == "graded" else L.SYN_EXP
-            q.on_device = 1
-            w = _dev(d["w"], torch.float32, self.device)
-            keep.append(w)
-            q.w = w.data_ptr()
-            if d.get("row_ptr") is None:
-                q.input_dense = 1
-                q.nnz = w.numel()
-            else:
-                rp = _dev(d["row_ptr"], torch.int64, self.device)
-                col = _dev(d["col"], torch.int32, self.device)
-                keep += [rp, col]
-                q.row_ptr, q.col, q.nnz = rp.data_ptr(), col.data_ptr(), col.numel()
-            q.k1, q.k2, q.k3 = float(d.get("k1", 1.0)), float(d.get("k2", 0.0)), float(d.get("k3", 0.0))
-            q.density = float(d.get("p", d.get("density", 1.0)))
-            q.n_conn = float(d.get("n_conn", 0.0) or 0.0)
-            q.user_scale = float(d.get("user_scale", 1.0))
-            q.v_thr = float(d.get("v_thr", -20.0))
-            q.v_slope = float(d.get("v_slope", 2.0))
+        P, Q = _descs(pops, projs, self.device, keep)
         h = C.c_void_p()
         torch.cuda.synchronize(self.device)
         check(L.lib.snn_create_network(P, len(pops), Q, len(projs), float(dt), int(n_sub), int(seed),
@@ -143,6 +173,54 @@ class Network:
                                        _stream(stream), C.byref(h)))
         self.h = h.value
         self.dt = float(dt)
+        self.pop_offsets = [0]
+
+    def _setup(self, device, torch_alloc):
+        self.device = torch.device("cuda") if device is None else torch.device(device)
+        if self.device.index is None:
+            self.device = torch.device("cuda", torch.cuda.current_device())
+        self._alloc = TorchAllocator(self.device.index) if torch_alloc else None
+
+    @classmethod
+    def batch(cls, instances, dt, n_sub=4, seed=0, device=None, stream=None, torch_alloc=True):
+        """Many independent networks in one object (snn_create_batch).
+        ``instances``: list of (pops, projs, rng_instance).  Population k of
+        instance b is population ``pop_offsets[b] + k`` of the batch."""
+        self = cls.__new__(cls)
+        self._setup(device, torch_alloc)
+        keep, descs, self.sizes, self.pop_offsets = [], [], [], []
+        D = (L.NetDesc * len(instances))()
+        n_projs = 0
+        for b, (pops, projs, inst) in enumerate(instances):
+            P, Q = _descs(pops, projs, self.device, keep)
+            keep += [P, Q]
+            self.pop_offsets.append(len(self.sizes))
+            self.sizes += [int(d["n"]) for d in pops]
+            D[b].pops, D[b].n_pops = C.cast(P, C.POINTER(L.PopDesc)), len(pops)
+            D[b].projs, D[b].n_projs = C.cast(Q, C.POINTER(L.ProjDesc)), len(projs)
+            D[b].rng_instance = int(inst)
+            n_projs += len(projs)
+        self.n_projs = n_projs
+        h = C.c_void_p()
+        torch.cuda.synchronize(self.device)
+        check(L.lib.snn_create_batch(D, len(instances), float(dt), int(n_sub), int(seed),
+                                     self._alloc.ref() if self._alloc else None, _stream(stream), C.byref(h)))
+        self.h = h.value
+        self.dt = float(dt)
+        return self
+
+    @classmethod
+    def from_specs(cls, specs, device=None, stream=None, **kw):
+        """Batch of ``snn_inputs`` descriptions (same dt, substeps and seed),
+        each with its own instance number."""
+        device = torch.device("cuda") if device is None else torch.device(device)
+        s0 = specs[0]
+        inst = []
+        for spec in specs:
+            assert spec["dt"] == s0["dt"] and spec["n_sub"] == s0["n_sub"] and spec["seed"] == s0["seed"]
+            pops, projs = _spec_arrays(spec, device, stream, spec["instance"])
+            inst.append((pops, projs, spec["instance"]))
+        return cls.batch(inst, s0["dt"], s0["n_sub"], s0["seed"], device=device, stream=stream, **kw)
 
     # ------------------------------------------------------------------ build
     @classmethod
@@ -150,28 +228,9 @@ class Network:
         """Builds the network of a ``snn_inputs`` description: connectivity is
         drawn on the GPU from the seed, weights and initial potentials are the
         shared seeded arrays, nConn = p * N_pre inside the library."""
-        import snn_inputs as I
         inst = spec["instance"] if instance is None else instance
         device = torch.device("cuda") if device is None else torch.device(device)
-        pops = []
-        for k, d in enumerate(spec["pops"]):
-            e = dict(d)
-            v0 = I.v0(spec, k)
-            if v0 is not None:
-                e["v0"] = torch.from_numpy(v0).to(device)
-            pops.append(e)
-        projs = []
-        for q, d in enumerate(spec["projs"]):
-            n_pre, n_post = I.n_pre_post(spec, q)
-            e = dict(d)
-            if d["layout"] == "dense" and d["p"] >= 1.0:
-                e["w"] = torch.from_numpy(I.weights(spec, q, n_pre * n_post)).to(device)
-                e["row_ptr"] = None
-            else:
-                rp, col = csr_bernoulli(spec["seed"], I.rng_tag(inst, q), n_pre, n_post, d["p"], device, stream)
-                e["row_ptr"], e["col"] = rp, col
-                e["w"] = torch.from_numpy(I.weights(spec, q, col.numel())).to(device)
-            projs.append(e)
+        pops, projs = _spec_arrays(spec, device, stream, inst)
         return cls(pops, projs, spec["dt"], spec["n_sub"], spec["seed"], inst, device=device, stream=stream, **kw)
 
     # ------------------------------------------------------------------ run
@@ -277,6 +336,28 @@ class Network:
 
     def counters(self, pop):
         return int(self.read(pop, "spike_count").item()), int(self.read(pop, "nan_count").item())
+
+    # ------------------------------------------------------------------ checkpoints, tuning
+    def save_state(self, stream=None) -> torch.Tensor:
+        """Snapshot of the whole dynamic state as a device byte tensor."""
+        n = C.c_size_t()
+        check(L.lib.snn_state_size(self.h, C.byref(n)))
+        buf = torch.empty(n.value, dtype=torch.uint8, device=self.device)
+        check(L.lib.snn_save_state(self.h, buf.data_ptr(), n.value, 1, _stream(stream)))
+        return buf
+
+    def load_state(self, buf, stream=None):
+        if buf.is_cuda:
+            check(L.lib.snn_load_state(self.h, buf.data_ptr(), buf.numel(), 1, _stream(stream)))
+        else:
+            b = buf.contiguous()
+            check(L.lib.snn_load_state(self.h, b.data_ptr(), b.numel(), 0, _stream(stream)))
+
+    def autotune(self, trial_steps=200, stream=None):
+        r = L.Tuning()
+        check(L.lib.snn_autotune(self.h, int(trial_steps), C.byref(r), _stream(stream)))
+        return {"engine": "persistent" if r.engine == 1 else "plain", "prop_blocks": r.prop_blocks,
+                "chunk": r.chunk, "tiled": r.tiled, "us_per_step": r.us_per_step, "cached": bool(r.cached)}
 
     # ------------------------------------------------------------------ checks
     def debug_propagate(self, q, spk, stream=None):
