@@ -60,6 +60,9 @@ def _args():
                     help="back-to-back launches per kernel in the per-kernel timing")
     ap.add_argument("--sweep", action="store_true",
                     help="print one JSON line per point of the scaling sweep instead of the headline line")
+    ap.add_argument("--no-batched", action="store_true", help="skip the batched-vs-sequential comparison")
+    ap.add_argument("--batch-instances", type=int, default=512)
+    ap.add_argument("--batch-steps", type=int, default=5000)
     ap.add_argument("--no-scale-point", action="store_true",
                     help="skip the forced-activity propagation measurement at 100 x 1,000,000, p = 0.5")
     return ap.parse_args()
@@ -189,6 +192,54 @@ def run_sweep(a):
                 print(json.dumps(r), flush=True)
 
 
+def _batched(snn, torch, dev, n_inst, steps):
+    """The batched form (n_inst instances of the small workload, middle sizes
+    and conductance factors log-uniform, one network object) against the same
+    instances run one after another as stand-alone networks."""
+    specs = I.config_batched(n_inst, steps=steps)
+    batch = snn.Network.from_specs(specs, device=dev)
+    tune = batch.autotune(trial_steps=100)
+    batch.reset()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    batch.step(steps)
+    e1.record()
+    e1.synchronize()
+    t_batch = e0.elapsed_time(e1) * 1e-3
+    n_hh = [s["pops"][1]["n"] for s in specs]
+    rate_b = np.array([batch.counters(batch.pop_offsets[b] + 1)[0] / n_hh[b] / (steps * specs[0]["dt"] * 1e-3)
+                       for b in range(n_inst)])
+    nan_b = np.array([batch.counters(batch.pop_offsets[b] + 1)[1] for b in range(n_inst)])
+    ev_b = batch.synaptic_events()
+    batch.close()
+    solos = [snn.Network.from_spec(s, device=dev) for s in specs]
+    for net in solos:
+        net.step(1)
+        net.reset()
+    torch.cuda.synchronize()
+    e0.record()
+    for net in solos:
+        net.step(steps)
+    e1.record()
+    e1.synchronize()
+    t_seq = e0.elapsed_time(e1) * 1e-3
+    rate_s = np.array([solos[b].counters(1)[0] / n_hh[b] / (steps * specs[0]["dt"] * 1e-3) for b in range(n_inst)])
+    nan_s = np.array([solos[b].counters(1)[1] for b in range(n_inst)])
+    for net in solos:
+        net.close()
+    neuron_steps = (sum(n_hh) + 100 * n_inst) * steps
+    return {"workload": f"{n_inst} instances of 100 Poisson sources -> N HH (p = 0.1), N log-uniform 1k-50k, "
+                        f"conductance factor log-uniform 0.1-10, {steps} steps",
+            "neurons": sum(n_hh) + 100 * n_inst, "autotune": tune,
+            "batched_s": t_batch, "sequential_s": t_seq, "speedup": t_seq / t_batch,
+            "batched_neuron_steps_per_s": neuron_steps / t_batch,
+            "sequential_neuron_steps_per_s": neuron_steps / t_seq,
+            "batched_events": ev_b,
+            "mean_rate_hz": float(rate_b.mean()), "max_rate_diff_hz": float(np.abs(rate_b - rate_s).max()),
+            "instances_with_nan": int((nan_b > 0).sum()), "nan_counts_equal": bool(np.array_equal(nan_b, nan_s))}
+
+
 def _cpu_baseline(sim_steps):
     """The FP64 oracle, as it stands, on a bounded sample (single thread)."""
     import oracle
@@ -289,6 +340,7 @@ def run_ours(a):
     n_neurons = sum(p["n"] for p in spec["pops"])
     n_hh = sum(p["n"] for p in spec["pops"] if p["kind"] == "hh")
     net = snn.Network.from_spec(spec, device=dev)
+    tune = net.autotune(trial_steps=500)
     stream = torch.cuda.current_stream()
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)   # 256 MiB > L2
 
@@ -398,6 +450,10 @@ def run_ours(a):
     if not a.no_e2e:
         e2e = _e2e(a, spec, dev, torch, snn)
 
+    batched = None
+    if not a.no_batched and rank == 0:
+        batched = _batched(snn, torch, dev, a.batch_instances, a.batch_steps)
+
     cpu = None
     if rank == 0 and world == 1 and not a.no_cpu_baseline:
         cpu = _cpu_baseline(a.cpu_steps)
@@ -419,6 +475,8 @@ def run_ours(a):
                 "cpu_baseline": cpu,
                 "e2e": e2e,
                 "engine": engine,
+                "autotune": tune,
+                "batched": batched,
                 "gpu_launches": a.steps * ((-(-a.sim_steps // 1000)) + 2 if engine == "persistent"
                                            else 2 * a.sim_steps + 2),
                 "clocks": clk.summary()}
@@ -468,6 +526,7 @@ def _e2e(a, spec, dev, torch, snn):
                 e["row_ptr"] = None
             projs.append(e)
         net = snn.Network(pops, projs, spec["dt"], spec["n_sub"], spec["seed"], spec["instance"], device=dev)
+        net.autotune(trial_steps=500)          # cached after the first network of this shape
         net.step(a.sim_steps)
         ev = net.synaptic_events()
         cnt = torch.stack([torch.cat([net.read(p, "spike_count"), net.read(p, "nan_count")])
