@@ -41,7 +41,7 @@ def build(force: bool = False) -> Path:
     if not force and _LIB_PATH.exists() and _LIB_PATH.stat().st_mtime >= newest:
         return _LIB_PATH
     tmp = _LIB_PATH.with_suffix(f".so.tmp{os.getpid()}")
-    cmd = ["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fno-fast-math", "-fPIC", "-shared",
+    cmd = ["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fno-fast-math", "-fPIC", "-shared", f"-I{_HERE}",
            *map(str, srcs), "-o", str(tmp), "-lm"]
     subprocess.run(cmd, check=True)
     os.replace(tmp, _LIB_PATH)

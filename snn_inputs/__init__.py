@@ -118,15 +118,26 @@ def config_batched(n_instances=512, steps=5000, seed=SEED, n_lo=1_000, n_hi=50_0
 GRADED = dict(v_thr=-20.0, v_slope=2.0, tau_filter=5.0, target_jitter=0.1)
 
 
+# Graded weights (nS, uniform [0, max]) per projection In -> Mid, recurrent,
+# Mid -> Out; calibrated once on the FP64 oracle (200-neuron copy, 2000 steps)
+# so that the middle and output populations respond to the input spikes
+# (filtered output range about -63 to -58 mV) while central finite
+# differences still agree with the adjoint.
+GRADED_WEIGHTS = (60.0, 5.0, 60.0)
+
+
 def config_graded(n_in=100, n_mid=20000, n_out=100, p=0.05, p_in=None, steps=2000, dt=0.05,
-                  recurrent=True, weight=("uniform", 0.0, 2.0), seed=SEED):
+                  recurrent=True, weights=GRADED_WEIGHTS, seed=SEED):
     """Graded sigmoidal synapses, release 1/(1 + exp((V_thr - V_pre)/2 mV)),
     V_thr = -20 mV.  In (Poisson-current drive) -> Mid, Mid -> Mid, Mid -> Out,
-    all compressed rows at density p, excitatory.  Weights in nS."""
+    all compressed rows at density p, excitatory; weights uniform in nS."""
     pops = [hh_pop(n_in, drive=dict(INPUT_DRIVE)), hh_pop(n_mid), hh_pop(n_out)]
-    projs = [proj(0, 1, "csr", p if p_in is None else p_in, weight),
-             proj(1, 1, "csr", p, weight) if recurrent else proj(2, 2, "csr", p, weight),
-             proj(1, 2, "csr", p, weight)]
+    w = [("uniform", 0.0, float(x)) for x in weights]
+    projs = [proj(0, 1, "csr", p if p_in is None else p_in, w[0]),
+             proj(1, 1, "csr", p, w[1]) if recurrent else proj(2, 2, "csr", p, w[1]),
+             proj(1, 2, "csr", p, w[2])]
+    for d in projs:
+        d.update(synapse="graded", v_thr=GRADED["v_thr"], v_slope=GRADED["v_slope"])
     return net(pops, projs, dt=dt, steps=steps, seed=seed,
                name=f"graded_in{n_in}_mid{n_mid}_out{n_out}_p{p}")
 
