@@ -290,6 +290,44 @@ snn_status snn_csr_bernoulli_fill(uint64_t seed, uint32_t tag, int64_t n_pre, in
 snn_status snn_csr_bernoulli_rows_noalloc(uint64_t seed, uint32_t tag, int64_t n_pre, int64_t n_post,
                                           double p, int64_t* row_ptr, int64_t* nnz, void* stream);
 
+/* ---- parameters ----------------------------------------------------------- */
+/* Replaces the conductance scale s of projection `proj` (rounded to FP32). */
+snn_status snn_set_scale(snn_net* net, int32_t proj, double scale);
+
+/* Replaces the nnz weights (nS, compressed-row order) of projection `proj`
+ * (compressed-row storage only), host or device.  Synchronises `stream`. */
+snn_status snn_set_weights(snn_net* net, int32_t proj, const float* w, int32_t on_device, void* stream);
+
+/* ---- differentiable form (graded synapses) ---------------------------------
+ * A network whose projections all have synapse = SNN_SYN_GRADED uses graded
+ * release r = 1 / (1 + exp((v_thr - V_pre) / v_slope)) instead of spikes:
+ * each step, G_q[k] = sum_i w_ik r_i and I_syn_k = sum_q s_q (E_q - V_k) G_q[k]
+ * (E_q: the post population's reversal potential of the projection's
+ * channel), then the Euler substeps; spike counts are still kept.  The paper
+ * fixes no synapse model (Sec. 2); this graded one makes the loss below a
+ * smooth function of the scales s_q (Sec. 5.1) and the weights. */
+
+/* Runs n_steps steps from the creation state (it resets the network first)
+ * and evaluates L = mean over steps t and output neurons k of
+ * (y_k(t+1) - target[t][k])^2, where y follows the output population's V
+ * with y += (dt / tau_f)(V - y), starting at V(0).  target (device,
+ * n_steps x n_out floats) is copied; y_out (device, n_steps x n_out) may be
+ * NULL; *loss (host) receives L.  Stores the state every checkpoint_every
+ * steps (1..512) for snn_backward.  Synchronises `stream`.  SNN_ERR_STATE for
+ * a spiking network. */
+snn_status snn_forward_record(snn_net* net, int64_t n_steps, int32_t checkpoint_every, int32_t out_pop,
+                              double tau_f, const float* target, float* y_out, double* loss, void* stream);
+
+/* Gradient of the last recorded L with respect to every projection's scale
+ * (grad_scale: device, n_projs floats) and weights (grad_w: host array of
+ * n_projs device pointers, each nnz floats in compressed-row order), by the
+ * discrete adjoint of the recorded steps: each checkpoint segment is
+ * recomputed, then swept in reverse (substeps, synaptic current,
+ * pre-synaptic gather), and the weight gradients of the segment are summed
+ * over its steps in one pass.  Overwrites the outputs.  SNN_ERR_STATE
+ * without a recorded forward.  Synchronises `stream`. */
+snn_status snn_backward(snn_net* net, float* grad_scale, float* const* grad_w, void* stream);
+
 /* ---- checkpoint / resume --------------------------------------------------
  * A snapshot holds the whole dynamic state: V, m, h, n, conductances, drive
  * currents, spike lists and lengths, all counters, the persistent engine's

@@ -327,7 +327,9 @@ snn_status create_impl(const snn_pop_desc* pops, int32_t n_pops, const snn_proj_
         if (d.channel != 0 && d.channel != 1) return fail(SNN_ERR_INVALID_ARG, at + "channel must be 0 or 1");
         if (d.layout != SNN_LAYOUT_CSR && d.layout != SNN_LAYOUT_DENSE)
             return fail(SNN_ERR_INVALID_ARG, at + "bad layout");
-        if (d.synapse != SNN_SYN_EXP) return fail(SNN_ERR_INVALID_ARG, at + "spiking networks take exponential synapses");
+        if (d.synapse != SNN_SYN_EXP && d.synapse != SNN_SYN_GRADED) return fail(SNN_ERR_INVALID_ARG, at + "bad synapse kind");
+        if ((d.synapse == SNN_SYN_GRADED) != graded_requested(projs, n_projs))
+            return fail(SNN_ERR_INVALID_ARG, at + "a network is either spiking (exponential) or graded throughout");
         if (d.input_dense) {
             if (d.layout != SNN_LAYOUT_DENSE) return fail(SNN_ERR_INVALID_ARG, at + "dense input needs dense layout");
             if (!d.w && (int64_t)pops[d.pre].n * pops[d.post].n > 0) return fail(SNN_ERR_INVALID_ARG, at + "w is NULL");
@@ -532,6 +534,7 @@ snn_status create_impl(const snn_pop_desc* pops, int32_t n_pops, const snn_proj_
     }
     CK(persistent_capacity(net->sm_count, &net->persist_grid), "persistent occupancy");
     TRY(setup_tiled(net, s));
+    if (graded_requested(projs, n_projs)) TRY(graded_setup(net, s));
     // save the creation state for snn_reset
     CK(cudaMemcpyAsync(net->init_state, net->V, 7 * NT * sizeof(float), cudaMemcpyDeviceToDevice, s),
        "save initial state");
@@ -617,6 +620,7 @@ snn_status snn_step(snn_net* net, int64_t n_steps, void* stream) {
     if (!net || n_steps < 0) return fail(SNN_ERR_INVALID_ARG, "bad network or step count");
     cudaStream_t s = (cudaStream_t)stream;
     try {
+        if (net->graded) return graded_step(net, n_steps, s);
         if (use_persistent(net)) {
             CK(enqueue_persistent(net, n_steps, s), "persistent steps");
             return SNN_OK;
@@ -723,6 +727,7 @@ snn_status snn_reset(snn_net* net, void* stream) {
     CK(cudaMemsetAsync(net->bar, 0, sizeof(GridBarrier), s), "clear");
     CK(cudaMemsetAsync(net->error, 0, sizeof(uint32_t), s), "clear");
     CK(launch_set_epoch_base(net->ticket, net->num_tiles, s), "reset step counter");
+    if (net->graded) return graded_reset(net, s);
     return SNN_OK;
 }
 
@@ -779,7 +784,7 @@ snn_status snn_get_step(snn_net* net, int64_t* step, void* stream) {
     cudaStream_t s = (cudaStream_t)stream;
     CK(cudaMemcpyAsync(t, net->ticket, sizeof(t), cudaMemcpyDeviceToHost, s), "read ticket");
     CK(cudaStreamSynchronize(s), "synchronize");
-    *step = net->num_tiles ? (int64_t)(t[0] / (unsigned long long)net->num_tiles - t[1]) : 0;
+    *step = net->graded ? net->g_t : net->num_tiles ? (int64_t)(t[0] / (unsigned long long)net->num_tiles - t[1]) : 0;
     return SNN_OK;
 }
 

@@ -1,0 +1,374 @@
+// Differentiable form: graded-synapse HH network, forward and discrete adjoint.
+//
+// Forward step (one per time step, two launches):
+//   k_graded_spmv    G_q[j] = sum_i w_ij r_i for every graded projection q,
+//                    pulled over the transposed (post-major) copy of the
+//                    compressed rows: no atomics, a fixed summation order, so
+//                    a recomputed step is bit-identical to the first pass;
+//   k_graded_neuron  I_syn = sum_q s_q (E_q - V) G_q, drive events, Euler
+//                    substeps, drive decay, output filter y += a (V - y) and
+//                    squared error against the target, and the next release
+//                    r = 1 / (1 + exp((v_thr - V) / slope)).
+// Adjoint (per checkpoint segment of K steps, in reverse):
+//   the segment is recomputed from its checkpoint with the same two kernels,
+//   storing step-start states, releases and G;
+//   k_graded_reverse back through the filter, the substeps (recomputed in
+//                    registers, analytic rate derivatives) and the synaptic
+//                    current: state adjoints, dL/dG_q = mu s_q (E_q - V), and
+//                    dL/ds_q partial sums;
+//   k_graded_gather  dL/dV_i += r'_i sum_q sum_k w_ik dL/dG_q[k] over the
+//                    compressed row of i (pre-synaptic path);
+//   k_graded_sddmm   after the segment: dL/dw_ik += sum_t r_i(t) dL/dG_q[k](t),
+//                    with dL/dG stored post-major and time-contiguous so each
+//                    synapse reads K consecutive floats.
+#include "device_math.cuh"
+#include "snn_internal.cuh"
+
+namespace snn {
+
+namespace {
+
+constexpr int kThreads = 256;
+
+__device__ __forceinline__ float release(float V, float thr, float inv_slope) {
+    return 1.0f / (1.0f + __expf((thr - V) * inv_slope));
+}
+
+// d/dx [x / (exp(x) - 1)]: series (Bernoulli numbers) for |x| < 0.5, else the
+// closed form (e - 1 - x e) / (e - 1)^2 with e = exp(x).
+__device__ __forceinline__ float dlinoid(float x, float e) {
+    if (fabsf(x) < 0.5f) {
+        const float x2 = x * x;
+        return fmaf(x, fmaf(x2, fmaf(x2, fmaf(x2, -1.0f / 151200.0f, 1.0f / 5040.0f), -1.0f / 180.0f),
+                            1.0f / 6.0f), -0.5f);
+    }
+    const float em = e - 1.0f;
+    return __fdividef(em - x * e, em * em);
+}
+
+struct HHDerivs {
+    float am, bm, ah, bh, an, bn;
+};
+
+// Derivatives in V of the rates of hh_rates (same identities).
+__device__ __forceinline__ HHDerivs hh_rate_derivs(float V, const HHRates& r) {
+    constexpr float kLog2e = 1.4426950408889634f;
+    constexpr float kExpM5 = 6.737946999085467e-3f;
+    const float x = (-52.0f - V) * 0.25f;
+    const float y = (V + 25.0f) * 0.2f;
+    const float z = (-50.0f - V) * 0.2f;
+    const float Em = exp2f(x * kLog2e);
+    const float E = exp2f(y * kLog2e);
+    const float Ez = __fdividef(kExpM5, E);
+    HHDerivs d;
+    d.am = 1.28f * dlinoid(x, Em) * -0.25f;
+    d.bm = 1.4f * dlinoid(y, E) * 0.2f;
+    d.an = 0.16f * dlinoid(z, Ez) * -0.2f;
+    d.ah = -r.ah * (1.0f / 18.0f);
+    const float e1 = E + 1.0f;
+    d.bh = __fdividef(0.8f * E, e1 * e1);
+    d.bn = -r.bn * 0.025f;
+    return d;
+}
+
+// Synaptic current of neuron `local` of population p from the G vector.
+__device__ __forceinline__ float graded_isyn(const GradedArgs& a, int pop, int local, float V, float* dI_dV) {
+    float isyn = 0.0f, d = 0.0f;
+    const int b = a.in_begin[pop], e = a.in_begin[pop + 1];
+    for (int k = b; k < e; ++k) {
+        const GradProj& q = a.gprojs[a.in_list[k]];
+        const float G = a.G[q.g_off + local];
+        isyn += q.scale * (q.E - V) * G;
+        d -= q.scale * G;
+    }
+    *dI_dV = d;
+    return isyn;
+}
+
+}  // namespace
+
+__global__ void __launch_bounds__(kThreads) k_graded_spmv(const GradedArgs a) {
+    const int lane = threadIdx.x & 31;
+    const int64_t warp = (int64_t)blockIdx.x * (kThreads / 32) + (threadIdx.x >> 5);
+    const int64_t warps = (int64_t)gridDim.x * (kThreads / 32);
+    for (int64_t w = warp; w < a.total_posts; w += warps) {
+        int q = 0;
+        while (a.gprojs[q].g_off + a.gprojs[q].n_post <= w) ++q;
+        const GradProj& Q = a.gprojs[q];
+        const int j = (int)(w - Q.g_off);
+        const int64_t b = Q.csc_ptr[j], e = Q.csc_ptr[j + 1];
+        float acc = 0.0f;
+        for (int64_t k = b + lane; k < e; k += 32) acc = fmaf(Q.csc_w[k], a.r[Q.pre_off + Q.csc_pre[k]], acc);
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+        if (lane == 0) a.G[w] = acc;
+    }
+}
+
+__global__ void __launch_bounds__(kThreads) k_graded_neuron(const GradedArgs a) {
+    const int idx_t = blockIdx.x * kThreads + threadIdx.x;     // tile-major over the SoA
+    if (idx_t >= a.n_total) return;
+    const int tile = idx_t / kTile;
+    const int pop = a.tile_pop[tile];
+    const DevPop& P = a.pops[pop];
+    const int local = (tile - P.first_tile) * kTile + (idx_t % kTile);
+    if (local >= P.n) return;
+    const int idx = P.offset + local;
+    float V = a.V[idx], m = a.m[idx], h = a.h[idx], n = a.n[idx], ie = a.iext[idx];
+    if (P.thr_drive) {
+        const uint4 r = philox_4x32_10(make_uint4((uint32_t)local, a.t_rng, P.tag, kStreamDrive),
+                                       PhiloxKey{a.seed_lo, a.seed_hi});
+        if (below(r.x, P.thr_drive)) ie += P.drive_amp;
+    }
+    if (a.rec_state) {                     // step-start state for the adjoint
+        a.rec_state[idx] = V;
+        a.rec_state[a.n_total + idx] = m;
+        a.rec_state[2 * (size_t)a.n_total + idx] = h;
+        a.rec_state[3 * (size_t)a.n_total + idx] = n;
+        a.rec_state[4 * (size_t)a.n_total + idx] = ie;
+        a.rec_r[idx] = a.r[idx];
+    }
+    float dI;
+    const float isyn = graded_isyn(a, pop, local, V, &dI);
+    const float I_in = isyn + ie;
+    const HHCell cell{P.gNa, P.ENa, P.gK, P.EK, P.gL, P.EL};
+    const float V0 = V;
+    for (int s = 0; s < a.n_sub; ++s) hh_substep(cell, a.hs, P.hs_over_C, I_in, V, m, h, n);
+    a.V[idx] = V; a.m[idx] = m; a.h[idx] = h; a.n[idx] = n;
+    a.iext[idx] = ie * P.drive_dec;
+    a.r[idx] = release(V, P.rel_thr, P.rel_inv_slope);
+    if (V0 < P.v_thresh && V >= P.v_thresh) {
+        atomicAdd(P.spike_count, 1ull);
+        P.neuron_spikes[local] += 1;
+    }
+    if (isnan(V)) atomicAdd(P.nan_count, 1ull);
+    if (pop == a.out_pop) {
+        const float y = a.y[local] + a.a_filter * (V - a.y[local]);
+        a.y[local] = y;
+        if (a.y_out) a.y_out[(size_t)a.t_rec * a.n_out + local] = y;
+        if (a.rec_y) a.rec_y[local] = y;
+        if (a.target) {
+            const float d = y - a.target[(size_t)a.t_rec * a.n_out + local];
+            atomicAdd(a.loss, (double)d * (double)d);
+        }
+    }
+}
+
+__global__ void k_graded_release_init(const GradedArgs a) {
+    const int idx_t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx_t >= a.n_total) return;
+    const int tile = idx_t / kTile;
+    const DevPop& P = a.pops[a.tile_pop[tile]];
+    const int local = (tile - P.first_tile) * kTile + (idx_t % kTile);
+    if (local >= P.n) return;
+    a.r[P.offset + local] = release(a.V[P.offset + local], P.rel_thr, P.rel_inv_slope);
+    if (a.tile_pop[tile] == a.out_pop) a.y[local] = a.V[P.offset + local];
+}
+
+// Reverse of one step for every neuron.  Reads the adjoint of the state after
+// the step (lV includes the pre-synaptic gather of the later step), writes the
+// local part of the adjoint of the state before it, dL/dG per incoming
+// projection (per-step slice and time-contiguous copy) and dL/ds partials.
+__global__ void __launch_bounds__(kThreads) k_graded_reverse(const GradedArgs a, const AdjArgs b) {
+    __shared__ double s_gs[kMaxGradedProjs];
+    for (int k = threadIdx.x; k < a.n_gprojs; k += kThreads) s_gs[k] = 0.0;
+    __syncthreads();
+    const int idx_t = blockIdx.x * kThreads + threadIdx.x;
+    bool active = idx_t < a.n_total;
+    int pop = 0, local = 0, idx = 0;
+    const DevPop* Pp = nullptr;
+    if (active) {
+        const int tile = idx_t / kTile;
+        pop = a.tile_pop[tile];
+        Pp = &a.pops[pop];
+        local = (tile - Pp->first_tile) * kTile + (idx_t % kTile);
+        active = local < Pp->n;
+        idx = Pp->offset + local;
+    }
+    if (active) {
+        const DevPop& P = *Pp;
+        const size_t NT = (size_t)a.n_total;
+        const float V0 = b.st[idx], m0 = b.st[NT + idx], h0 = b.st[2 * NT + idx], n0 = b.st[3 * NT + idx];
+        const float ie = b.st[4 * NT + idx];
+        float dIsyn_dV;
+        const float isyn = graded_isyn(a, pop, local, V0, &dIsyn_dV);
+        const float I_in = isyn + ie;
+        const HHCell cell{P.gNa, P.ENa, P.gK, P.EK, P.gL, P.EL};
+        // recompute the substep states (identical to the forward pass)
+        float Vs[kMaxSub + 1], ms[kMaxSub + 1], hs_[kMaxSub + 1], ns[kMaxSub + 1];
+        Vs[0] = V0; ms[0] = m0; hs_[0] = h0; ns[0] = n0;
+        const int S = a.n_sub;
+#pragma unroll 4
+        for (int s = 0; s < S; ++s) {
+            float V = Vs[s], m = ms[s], h = hs_[s], n = ns[s];
+            hh_substep(cell, a.hs, P.hs_over_C, I_in, V, m, h, n);
+            Vs[s + 1] = V; ms[s + 1] = m; hs_[s + 1] = h; ns[s + 1] = n;
+        }
+        float lV = b.lV[idx], lm = b.lm[idx], lh = b.lh[idx], ln = b.ln[idx];
+        float ly_prev = 0.0f;
+        if (pop == a.out_pop) {
+            float ly = b.ly[local];
+            const float y = b.y_after[local];
+            ly += a.loss_scale * (y - a.target[(size_t)a.t_rec * a.n_out + local]);
+            lV += a.a_filter * ly;
+            ly_prev = (1.0f - a.a_filter) * ly;
+        }
+        float aI = 0.0f;
+        const float c = P.hs_over_C;
+        for (int s = S - 1; s >= 0; --s) {
+            const float V = Vs[s], m = ms[s], h = hs_[s], n = ns[s];
+            const HHRates r = hh_rates(V);
+            const HHDerivs d = hh_rate_derivs(V, r);
+            const float m2 = m * m, m3 = m2 * m, n3 = n * n * n;
+            const float dI_dV = P.gNa * m3 * h + P.gK * n3 * n + P.gL;
+            const float dI_dm = 3.0f * P.gNa * m2 * h * (V - P.ENa);
+            const float dI_dh = P.gNa * m3 * (V - P.ENa);
+            const float dI_dn = 4.0f * P.gK * n3 * (V - P.EK);
+            const float nV = lV * (1.0f - c * dI_dV) + lm * a.hs * (d.am * (1.0f - m) - d.bm * m) +
+                             lh * a.hs * (d.ah * (1.0f - h) - d.bh * h) + ln * a.hs * (d.an * (1.0f - n) - d.bn * n);
+            const float nm = lV * (-c * dI_dm) + lm * (1.0f - a.hs * (r.am + r.bm));
+            const float nh = lV * (-c * dI_dh) + lh * (1.0f - a.hs * (r.ah + r.bh));
+            const float nn = lV * (-c * dI_dn) + ln * (1.0f - a.hs * (r.an + r.bn));
+            aI = fmaf(lV, c, aI);
+            lV = nV; lm = nm; lh = nh; ln = nn;
+        }
+        b.lV_loc[idx] = fmaf(aI, dIsyn_dV, lV);
+        b.lm[idx] = lm; b.lh[idx] = lh; b.ln[idx] = ln;
+        if (pop == a.out_pop) b.ly[local] = ly_prev;
+        const int qb = a.in_begin[pop], qe = a.in_begin[pop + 1];
+        for (int k = qb; k < qe; ++k) {
+            const int qi = a.in_list[k];
+            const GradProj& q = a.gprojs[qi];
+            const float nu = aI * q.scale * (q.E - V0);
+            b.nu_step[q.g_off + local] = nu;
+            b.nu_km[(size_t)(q.g_off + local) * b.kp + b.tl] = nu;
+            atomicAdd(&s_gs[qi], (double)aI * (double)(q.E - V0) * (double)a.G[q.g_off + local]);
+        }
+    }
+    __syncthreads();
+    for (int k = threadIdx.x; k < a.n_gprojs; k += kThreads)
+        if (s_gs[k] != 0.0) atomicAdd(b.grad_scale + k, s_gs[k]);
+}
+
+// dL/dV_i = local part + r'_i sum over outgoing rows of w * dL/dG (one warp per neuron).
+__global__ void __launch_bounds__(kThreads) k_graded_gather(const GradedArgs a, const AdjArgs b) {
+    const int lane = threadIdx.x & 31;
+    const int64_t warp = (int64_t)blockIdx.x * (kThreads / 32) + (threadIdx.x >> 5);
+    const int64_t warps = (int64_t)gridDim.x * (kThreads / 32);
+    for (int64_t w = warp; w < a.n_total; w += warps) {
+        const int tile = (int)(w / kTile);
+        const int pop = a.tile_pop[tile];
+        const DevPop& P = a.pops[pop];
+        const int local = (tile - P.first_tile) * kTile + (int)(w % kTile);
+        if (local >= P.n) continue;
+        const int idx = P.offset + local;
+        float acc = 0.0f;
+        for (int k = a.out_begin[pop]; k < a.out_begin[pop + 1]; ++k) {
+            const GradProj& q = a.gprojs[a.out_list[k]];
+            const float* nu = b.nu_step + q.g_off;
+            for (int64_t e = q.row_ptr[local] + lane; e < q.row_ptr[local + 1]; e += 32)
+                acc = fmaf(q.w[e], nu[q.col[e]], acc);
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+        if (lane == 0) {
+            const float r = b.r_step[idx];
+            b.lV[idx] = fmaf(r * (1.0f - r) * P.rel_inv_slope, acc, b.lV_loc[idx]);
+        }
+    }
+}
+
+// dL/dw_ik += sum over the segment's steps of r_i(t) dL/dG_q[k](t); one warp
+// per compressed row, the row's releases staged in shared memory.
+__global__ void __launch_bounds__(kThreads) k_graded_sddmm(const GradedArgs a, const AdjArgs b, int qi,
+                                                           float* grad_w, int L) {
+    __shared__ float s_r[kThreads / 32][kMaxSeg];
+    const GradProj& q = a.gprojs[qi];
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+    const int64_t warps = (int64_t)gridDim.x * (kThreads / 32);
+    const size_t NT = (size_t)a.n_total;
+    for (int64_t i = (int64_t)blockIdx.x * (kThreads / 32) + wib; i < q.n_pre; i += warps) {
+        for (int t = lane; t < L; t += 32) s_r[wib][t] = b.r_seg[(size_t)t * NT + q.pre_off + i];
+        __syncwarp();
+        for (int64_t e = q.row_ptr[i] + lane; e < q.row_ptr[i + 1]; e += 32) {
+            const float* nu = b.nu_km + (size_t)(q.g_off + q.col[e]) * b.kp;
+            float acc = 0.0f;
+            int t = 0;
+            for (; t + 4 <= L; t += 4) {
+                const float4 v = *reinterpret_cast<const float4*>(nu + t);
+                acc = fmaf(s_r[wib][t], v.x, acc);
+                acc = fmaf(s_r[wib][t + 1], v.y, acc);
+                acc = fmaf(s_r[wib][t + 2], v.z, acc);
+                acc = fmaf(s_r[wib][t + 3], v.w, acc);
+            }
+            for (; t < L; ++t) acc = fmaf(s_r[wib][t], nu[t], acc);
+            grad_w[e] += acc;
+        }
+        __syncwarp();
+    }
+}
+
+__global__ void k_scatter_csc(const float* w_csr, const int64_t* perm, float* w_csc, int64_t nnz) {
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < nnz; e += (int64_t)gridDim.x * blockDim.x)
+        w_csc[e] = w_csr[perm[e]];
+}
+
+__global__ void k_finish_grad_scale(const double* acc, const float* scale_of, float* out, int n) {
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k < n) out[k] = (float)acc[k];
+    (void)scale_of;
+}
+
+// ---- launchers ---------------------------------------------------------------
+static int grid_warps(int64_t warps) {
+    int64_t b = (warps + (kThreads / 32) - 1) / (kThreads / 32);
+    if (b < 1) b = 1;
+    if (b > 152 * 32) b = 152 * 32;
+    return (int)b;
+}
+
+cudaError_t launch_graded_spmv(const GradedArgs& a, cudaStream_t s) {
+    if (a.total_posts == 0) return cudaSuccess;
+    k_graded_spmv<<<grid_warps(a.total_posts), kThreads, 0, s>>>(a);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_graded_neuron(const GradedArgs& a, cudaStream_t s) {
+    k_graded_neuron<<<(a.n_total + kThreads - 1) / kThreads, kThreads, 0, s>>>(a);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_graded_release_init(const GradedArgs& a, cudaStream_t s) {
+    k_graded_release_init<<<(a.n_total + kThreads - 1) / kThreads, kThreads, 0, s>>>(a);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_graded_reverse(const GradedArgs& a, const AdjArgs& b, cudaStream_t s) {
+    k_graded_reverse<<<(a.n_total + kThreads - 1) / kThreads, kThreads, 0, s>>>(a, b);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    k_graded_gather<<<grid_warps(a.n_total), kThreads, 0, s>>>(a, b);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_graded_sddmm(const GradedArgs& a, const AdjArgs& b, int q, int64_t n_pre, float* grad_w, int L,
+                                cudaStream_t s) {
+    if (n_pre == 0 || L == 0) return cudaSuccess;
+    k_graded_sddmm<<<grid_warps(n_pre), kThreads, 0, s>>>(a, b, q, grad_w, L);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_scatter_csc(const float* w_csr, const int64_t* perm, float* w_csc, int64_t nnz, cudaStream_t s) {
+    if (nnz == 0) return cudaSuccess;
+    const int blocks = (int)std::min<int64_t>((nnz + 255) / 256, 4096);
+    k_scatter_csc<<<blocks, 256, 0, s>>>(w_csr, perm, w_csc, nnz);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_finish_grad_scale(const double* acc, float* out, int n, cudaStream_t s) {
+    if (n == 0) return cudaSuccess;
+    k_finish_grad_scale<<<1, 256, 0, s>>>(acc, nullptr, out, n);
+    return cudaGetLastError();
+}
+
+}  // namespace snn

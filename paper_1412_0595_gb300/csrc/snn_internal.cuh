@@ -47,6 +47,7 @@ struct DevPop {
     unsigned long long* spike_count;
     unsigned long long* nan_count;
     int32_t* neuron_spikes;        // per-neuron spike counts of this population
+    float rel_thr, rel_inv_slope;  // graded release of this population's neurons
 };
 
 struct DevProj {
@@ -74,6 +75,66 @@ struct DevProj {
 struct GridBarrier {
     unsigned long long count;
     unsigned long long base;
+};
+
+constexpr int kMaxGradedProjs = 64;
+constexpr int kMaxSub = 16;            // substeps the adjoint recomputes in registers
+constexpr int kMaxSeg = 512;           // steps per checkpoint segment
+
+struct GradProj {
+    int32_t pre, post;
+    int32_t pre_off, post_off;         // SoA offsets of the pre / post populations
+    int32_t n_pre, n_post;
+    float scale;                       // s_q
+    float E;                           // reversal potential of the post channel
+    int64_t g_off;                     // block of this projection in a step's G vector
+    const int64_t* row_ptr;            // compressed rows (pre-major)
+    const int32_t* col;
+    const float* w;
+    const int64_t* csc_ptr;            // transposed copy (post-major)
+    const int32_t* csc_pre;
+    const float* csc_w;
+};
+
+struct GradedArgs {
+    const DevPop* pops;
+    const int32_t* tile_pop;
+    const GradProj* gprojs;
+    int32_t n_gprojs;
+    int64_t total_posts;               // sum of n_post over projections (length of G)
+    const int32_t* in_begin;           // [n_pops + 1] incoming projections per population
+    const int32_t* in_list;
+    const int32_t* out_begin;          // [n_pops + 1] outgoing projections per population
+    const int32_t* out_list;
+    int32_t n_total;
+    float *V, *m, *h, *n, *iext;
+    float* r;                          // release of every neuron (next step's input)
+    float* G;                          // G vector of the current step
+    float* y;                          // output filter state [n_out]
+    float* y_out;                      // optional [T][n_out] record of y
+    const float* target;               // [T][n_out] or nullptr (no loss)
+    double* loss;
+    int32_t out_pop, n_out;
+    int32_t t_rec;                     // step index within the recorded forward
+    uint32_t t_rng;                    // step counter of the drive random numbers
+    int32_t n_sub;
+    float hs, a_filter, loss_scale;
+    uint32_t seed_lo, seed_hi;
+    float* rec_state;                  // [5][n_total] step-start V, m, h, n, I_ext (after drive) or nullptr
+    float* rec_r;                      // [n_total] releases used by the step
+    float* rec_y;                      // [n_out] y after the step
+};
+
+struct AdjArgs {
+    const float* st;                   // [5][n_total] step-start state of the step being reversed
+    const float* r_step;               // [n_total] releases of that step
+    const float* r_seg;                // [K][n_total] releases of the segment
+    const float* y_after;              // [n_out] y after that step
+    float *lV, *lV_loc, *lm, *lh, *ln, *ly;
+    float* nu_step;                    // [G] dL/dG of the step
+    float* nu_km;                      // [G][kp] dL/dG of the segment, time-contiguous
+    int32_t kp, tl;
+    double* grad_scale;
 };
 
 struct NeuronArgs {
@@ -127,6 +188,11 @@ struct PopHost {
 
 struct ProjHost {
     snn_proj_desc d;
+    int64_t* csc_ptr = nullptr;    // graded: transposed copy
+    int32_t* csc_pre = nullptr;
+    float* csc_w = nullptr;
+    int64_t* csc_perm = nullptr;   // transposed position -> compressed-row position
+    int64_t g_off = 0;
     float scale;
     int64_t nnz;
     int32_t max_row;
@@ -167,6 +233,28 @@ struct snn_net {
     int32_t persist_steps = 1000;             // steps per persistent launch
     int32_t persist_grid = 0;                 // co-resident CTAs of the persistent kernel
     int32_t tiled = 2;                        // post-tiled rows: 0 off, 1 all compressed projections, 2 choose
+    // graded (differentiable) networks
+    bool graded = false;
+    snn::GradProj* d_gprojs = nullptr;
+    int32_t* in_begin = nullptr;
+    int32_t* in_list = nullptr;
+    int64_t total_posts = 0;
+    float *r = nullptr, *G = nullptr, *y = nullptr;
+    double* d_loss = nullptr;
+    double* d_grad_scale = nullptr;
+    int64_t g_t = 0;                          // graded step counter
+    // recorded forward
+    int64_t rec_T = 0;
+    int32_t rec_K = 0, rec_out_pop = -1, rec_n_out = 0;
+    double rec_tau = 0.0, rec_loss = 0.0;
+    float* rec_ckpt = nullptr;                // [n_ckpt][6][n_total]
+    float* rec_target = nullptr;              // [T][n_out]
+    size_t rec_ckpt_cap = 0, rec_target_cap = 0;
+    // segment buffers of the adjoint
+    float *seg_state = nullptr, *seg_r = nullptr, *seg_G = nullptr, *seg_y = nullptr;
+    float *nu_step = nullptr, *nu_km = nullptr;
+    float *adj = nullptr;                     // lV, lV_loc, lm, lh, ln (5 * n_total) + ly (n_total)
+    int32_t seg_cap_K = 0;
     unsigned long long* counters = nullptr;   // 2 * n_pops
     unsigned long long* ticket = nullptr;     // [0] ticket, [1] epoch base
     int32_t* tile_pop = nullptr;
@@ -195,6 +283,18 @@ namespace snn {
 // Thread-local error message helpers (api.cu).
 snn_status fail(snn_status s, const std::string& msg);
 snn_status cuda_fail(cudaError_t e, const char* what);
+
+#define SNN_CK(call, what)                                       \
+    do {                                                         \
+        cudaError_t e_ = (call);                                 \
+        if (e_ != cudaSuccess) return snn::cuda_fail(e_, what);  \
+    } while (0)
+
+#define SNN_TRY(x)                    \
+    do {                              \
+        snn_status s_ = (x);          \
+        if (s_ != SNN_OK) return s_;  \
+    } while (0)
 
 // Kernel launchers (neuron.cu, propagate.cu, csr.cu).
 cudaError_t launch_neuron_step(const NeuronArgs& a, cudaStream_t s);
@@ -229,9 +329,33 @@ cudaError_t launch_propagate_tiled(const DevProj* q, int32_t P, const unsigned l
                                    int blocks, cudaStream_t s);
 constexpr int32_t kPostTile = 8192;          // posts per tile of the post-tiled propagation (32 KiB)
 cudaError_t persistent_capacity(int sm_count, int* blocks);
+cudaError_t launch_graded_spmv(const GradedArgs& a, cudaStream_t s);
+cudaError_t launch_graded_neuron(const GradedArgs& a, cudaStream_t s);
+cudaError_t launch_graded_release_init(const GradedArgs& a, cudaStream_t s);
+cudaError_t launch_graded_reverse(const GradedArgs& a, const AdjArgs& b, cudaStream_t s);
+cudaError_t launch_graded_sddmm(const GradedArgs& a, const AdjArgs& b, int q, int64_t n_pre, float* grad_w, int L,
+                                cudaStream_t s);
+cudaError_t launch_scatter_csc(const float* w_csr, const int64_t* perm, float* w_csc, int64_t nnz, cudaStream_t s);
+cudaError_t launch_finish_grad_scale(const double* acc, float* out, int n, cudaStream_t s);
 cudaError_t launch_persistent(const PersistArgs& a, int grid, cudaStream_t s);
 cudaError_t launch_set_epoch_base(unsigned long long* ticket, int num_tiles, cudaStream_t s);
 
 unsigned long long bernoulli_threshold(double p);
+
+// Device allocation owned by the network (released by snn_destroy).
+template <typename T>
+snn_status net_alloc(snn_net* net, T** out, size_t count, const char* what) {
+    void* p = net->mem.get(count * sizeof(T));
+    if (!p) return fail(SNN_ERR_OOM, std::string("device allocation failed: ") + what);
+    net->owned.push_back(p);
+    *out = static_cast<T*>(p);
+    return SNN_OK;
+}
+
+// graded_api.cu
+snn_status graded_setup(snn_net* net, cudaStream_t s);
+snn_status graded_reset(snn_net* net, cudaStream_t s);
+snn_status graded_step(snn_net* net, int64_t n_steps, cudaStream_t s);
+bool graded_requested(const snn_proj_desc* projs, int n_projs);
 
 }  // namespace snn

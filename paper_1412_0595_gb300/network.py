@@ -378,3 +378,61 @@ class Network:
         check(L.lib.snn_event_list(self.h, int(q), t.data_ptr() if t.numel() else None, t.numel(), 1,
                                    post.data_ptr(), w.data_ptr(), n.value, C.byref(n), s))
         return post[: n.value], w[: n.value]
+
+
+class GradedNetwork(Network):
+    """A network whose projections are all graded (the differentiable form):
+    recorded forward with checkpoints and the discrete adjoint."""
+
+    def set_scale(self, q, scale):
+        check(L.lib.snn_set_scale(self.h, int(q), float(scale)))
+
+    def set_weights(self, q, w, stream=None):
+        t = _dev(w, torch.float32, self.device)
+        assert t.numel() == self.nnz(q)
+        check(L.lib.snn_set_weights(self.h, int(q), t.data_ptr(), 1, _stream(stream)))
+
+    def forward_record(self, target, out_pop=None, tau_f=5.0, checkpoint_every=100, return_y=False, stream=None):
+        """Loss L of the recorded run; `target` is a (T, n_out) tensor."""
+        out_pop = len(self.sizes) - 1 if out_pop is None else int(out_pop)
+        tgt = _dev(target, torch.float32, self.device)
+        T, n_out = tgt.shape
+        assert n_out == self.sizes[out_pop]
+        y = torch.empty((T, n_out), dtype=torch.float32, device=self.device) if return_y else None
+        loss = C.c_double()
+        check(L.lib.snn_forward_record(self.h, int(T), int(checkpoint_every), out_pop, float(tau_f), tgt.data_ptr(),
+                                       y.data_ptr() if y is not None else None, C.byref(loss), _stream(stream)))
+        return (loss.value, y) if return_y else loss.value
+
+    def backward(self, stream=None):
+        """(dL/ds per projection, [dL/dw per projection, compressed-row order])."""
+        gs = torch.empty(self.n_projs, dtype=torch.float32, device=self.device)
+        gw = [torch.empty(max(self.nnz(q), 1), dtype=torch.float32, device=self.device) for q in range(self.n_projs)]
+        ptrs = (C.c_void_p * max(1, self.n_projs))(*[t.data_ptr() for t in gw])
+        check(L.lib.snn_backward(self.h, gs.data_ptr(), ptrs, _stream(stream)))
+        return gs, [g[: self.nnz(q)] for q, g in enumerate(gw)]
+
+
+class SNNFunction(torch.autograd.Function):
+    """L(scales, weights) of a graded network as an autograd node.
+
+    forward(net, target, out_pop, tau_f, checkpoint_every, scales, *weights):
+    sets every projection's scale s_q and weights, runs the recorded forward
+    and returns L as a 0-d tensor; backward returns dL/ds and dL/dw from the
+    network's discrete adjoint."""
+
+    @staticmethod
+    def forward(ctx, net, target, out_pop, tau_f, checkpoint_every, scales, *weights):
+        for q in range(net.n_projs):
+            net.set_scale(q, float(scales[q]))
+            net.set_weights(q, weights[q].detach())
+        loss = net.forward_record(target, out_pop, tau_f, checkpoint_every)
+        ctx.net = net
+        return torch.tensor(loss, dtype=torch.float64, device=scales.device)
+
+    @staticmethod
+    def backward(ctx, grad_out):
+        gs, gw = ctx.net.backward()
+        g = grad_out.to(torch.float32)
+        return (None, None, None, None, None, (g * gs).to(torch.float64) if gs.dtype != torch.float64 else g * gs,
+                *[g * x for x in gw])

@@ -1,0 +1,151 @@
+"""Differentiable form on the GPU against the FP64 oracle: recorded forward
+(loss, filtered output) and the discrete adjoint (dL/ds, dL/dw)."""
+import numpy as np
+import pytest
+import torch
+
+import snn_inputs as I  # noqa: E402
+from oracle.graded import GradedOracle
+
+pytestmark = pytest.mark.gpu
+
+
+def _rel_l2(a, b):
+    a, b = np.asarray(a, np.float64), np.asarray(b, np.float64)
+    return np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300)
+
+
+def _cos(a, b):
+    a, b = np.asarray(a, np.float64).ravel(), np.asarray(b, np.float64).ravel()
+    return float(a @ b / (np.linalg.norm(a) * np.linalg.norm(b)))
+
+
+def _pair(gpu, spec, T):
+    net = gpu.GradedNetwork.from_spec(spec)
+    ref = GradedOracle(spec)
+    target = I.target_trace(spec, T, ref.n_out)
+    return net, ref, target
+
+
+def test_graded_forward_matches_oracle_200_neuron_copy(gpu):
+    T = 2000
+    spec = I.config_graded_small(steps=T)
+    net, ref, target = _pair(gpu, spec, T)
+    loss, y = net.forward_record(torch.from_numpy(target), checkpoint_every=100, return_y=True)
+    rloss, ry = ref.forward(target.astype(np.float64))
+    assert loss == pytest.approx(rloss, rel=1e-3)
+    assert np.abs(y.cpu().numpy() - ry).max() < 0.05
+    assert net.t == T
+
+
+def test_graded_gradients_match_oracle_adjoint_before_divergence(gpu):
+    # 200 steps (10 ms): the FP32 trajectory still follows the FP64 one
+    T = 200
+    spec = I.config_graded_small(steps=T)
+    net, ref, target = _pair(gpu, spec, T)
+    net.forward_record(torch.from_numpy(target), checkpoint_every=64)
+    gs, gw = net.backward()
+    ref.forward(target.astype(np.float64))
+    rgs, rgw = ref.backward()
+    assert _rel_l2(gs.cpu().numpy(), rgs) < 1e-3
+    for q in range(3):
+        assert _rel_l2(gw[q].cpu().numpy(), rgw[q]) < 2e-3, q
+        assert _cos(gw[q].cpu().numpy(), rgw[q]) > 0.99999, q
+
+
+def test_graded_gradients_match_oracle_adjoint_smooth_network(gpu):
+    # no spikes: clamped pre cells near threshold drive passive cells
+    import test_oracle_graded as TG
+    pops = [I.hh_pop(20, v0_range=(-26.0, -14.0)), TG._passive(30), TG._passive(10)]
+    pops[0]["hh"]["C"] = 1e300
+    for d in pops[1:]:
+        d["v0_range"] = (-64.0, -60.0)
+    projs = [TG._graded_proj(0, 1, 0.0, p=0.5), TG._graded_proj(1, 1, 0.0, p=0.3), TG._graded_proj(1, 2, 0.0, p=0.5)]
+    for d, wmax in zip(projs, (5.0, 1.0, 5.0)):
+        d["weight"] = ("uniform", 0.0, wmax)
+    projs[1]["v_thr"] = projs[2]["v_thr"] = -62.0
+    spec = I.net(pops, projs, dt=0.05, steps=1)
+    T = 600
+    net, ref, target = _pair(gpu, spec, T)
+    loss = net.forward_record(torch.from_numpy(target), checkpoint_every=100)
+    gs, gw = net.backward()
+    rloss, _ = ref.forward(target.astype(np.float64))
+    rgs, rgw = ref.backward()
+    assert loss == pytest.approx(rloss, rel=1e-5)
+    assert _rel_l2(gs.cpu().numpy(), rgs) < 1e-4
+    for q in range(3):
+        assert _rel_l2(gw[q].cpu().numpy(), rgw[q]) < 1e-4, q
+
+
+def test_graded_gradients_2000_steps_output_projection(gpu):
+    # over the full 2000 steps the spiking middle population amplifies FP32
+    # rounding; the output projection's gradient stays well conditioned
+    T = 2000
+    spec = I.config_graded_small(steps=T)
+    net, ref, target = _pair(gpu, spec, T)
+    net.forward_record(torch.from_numpy(target), checkpoint_every=100)
+    gs, gw = net.backward()
+    ref.forward(target.astype(np.float64))
+    rgs, rgw = ref.backward()
+    assert gs[2].item() == pytest.approx(rgs[2], rel=1e-2)
+    assert _rel_l2(gw[2].cpu().numpy(), rgw[2]) < 2e-2
+    assert _cos(gw[2].cpu().numpy(), rgw[2]) > 0.999
+    assert torch.isfinite(gs).all() and all(torch.isfinite(g).all() for g in gw)
+
+
+def test_checkpoint_interval_does_not_change_the_gradient(gpu):
+    T = 600
+    spec = I.config_graded_small(steps=T)
+    net, ref, target = _pair(gpu, spec, T)
+    out = []
+    for K in (100, 37, 512):
+        l = net.forward_record(torch.from_numpy(target), checkpoint_every=K)
+        gs, gw = net.backward()
+        out.append((l, gs.cpu().numpy(), [g.cpu().numpy() for g in gw]))
+    for l, gs, gw in out[1:]:
+        assert l == out[0][0]                                   # the forward is deterministic
+        assert np.allclose(gs, out[0][1], rtol=1e-5, atol=0)
+        for q in range(3):
+            assert _rel_l2(gw[q], out[0][2][q]) < 1e-5
+
+
+def test_autograd_function_and_a_descent_step(gpu):
+    T = 400
+    spec = I.config_graded_small(steps=T)
+    net, ref, target = _pair(gpu, spec, T)
+    tgt = torch.from_numpy(target).cuda()
+    scales = torch.tensor([ref.scale(q) for q in range(3)], dtype=torch.float64, device="cuda", requires_grad=True)
+    ws = [torch.from_numpy(ref.rows[q][2].astype(np.float32)).cuda().requires_grad_(True) for q in range(3)]
+    loss = gpu.SNNFunction.apply(net, tgt, 2, 5.0, 100, scales, *ws)
+    loss.backward()
+    gs, gw = net.backward()
+    assert torch.allclose(scales.grad.float(), gs, rtol=1e-6, atol=0)
+    assert torch.equal(ws[0].grad, gw[0])
+    with torch.no_grad():                                      # a small step downhill on the scales
+        new_scales = scales * (1.0 - 1e-5 * torch.sign(scales.grad))
+    loss2 = gpu.SNNFunction.apply(net, tgt, 2, 5.0, 100, new_scales, *[w.detach() for w in ws])
+    assert loss2.item() < loss.item()
+
+
+def test_full_size_differentiable_workload_first_100_steps(gpu):
+    # 20,000 middle neurons, three projections at p = 0.05 (2e7 recurrent synapses)
+    T = 100
+    spec = I.config_graded(steps=T)
+    net, ref, target = _pair(gpu, spec, T)
+    loss = net.forward_record(torch.from_numpy(target), checkpoint_every=50)
+    rloss, _ = ref.forward(target.astype(np.float64))
+    assert loss == pytest.approx(rloss, rel=1e-4)
+    gs, gw = net.backward()
+    rgs, rgw = ref.backward()
+    assert _rel_l2(gs.cpu().numpy(), rgs) < 1e-3
+    for q in range(3):
+        assert _cos(gw[q].cpu().numpy(), rgw[q]) > 0.9999, q
+    assert all(torch.isfinite(g).all() for g in gw)
+
+
+def test_backward_without_forward_is_rejected(gpu):
+    import paper_1412_0595_gb300 as snn
+    net = gpu.GradedNetwork.from_spec(I.config_graded_small(steps=10))
+    with pytest.raises(snn.SNNError) as e:
+        net.backward()
+    assert e.value.name == "SNN_ERR_STATE"
