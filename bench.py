@@ -63,6 +63,7 @@ def _args():
     ap.add_argument("--no-batched", action="store_true", help="skip the batched-vs-sequential comparison")
     ap.add_argument("--batch-instances", type=int, default=512)
     ap.add_argument("--batch-steps", type=int, default=5000)
+    ap.add_argument("--no-graded", action="store_true", help="skip the differentiable-form measurement")
     ap.add_argument("--no-scale-point", action="store_true",
                     help="skip the forced-activity propagation measurement at 100 x 1,000,000, p = 0.5")
     return ap.parse_args()
@@ -238,6 +239,43 @@ def _batched(snn, torch, dev, n_inst, steps):
             "batched_events": ev_b,
             "mean_rate_hz": float(rate_b.mean()), "max_rate_diff_hz": float(np.abs(rate_b - rate_s).max()),
             "instances_with_nan": int((nan_b > 0).sum()), "nan_counts_equal": bool(np.array_equal(nan_b, nan_s))}
+
+
+def _differentiable(snn, torch, dev, steps=2000, K=100):
+    """Differentiable form (graded synapses, 20,000 middle neurons, p = 0.05):
+    recorded forward + adjoint backward against the 6 plain forward runs a
+    central finite difference over the 3 projection scales needs."""
+    spec = I.config_graded(steps=steps)
+    net = snn.GradedNetwork.from_spec(spec, device=dev)
+    n_out = spec["pops"][-1]["n"]
+    target = torch.from_numpy(I.target_trace(spec, steps, n_out)).to(dev)
+    nnz = sum(net.nnz(q) for q in range(net.n_projs))
+    net.forward_record(target, checkpoint_every=K)
+    net.backward()
+    torch.cuda.synchronize()
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+    ev[0].record()
+    loss = net.forward_record(target, checkpoint_every=K)
+    ev[1].record()
+    gs, gw = net.backward()
+    ev[2].record()
+    for _ in range(6):
+        net.forward_record(target, checkpoint_every=K)
+    ev[3].record()
+    ev[3].synchronize()
+    t_f, t_b, t_fd = ev[0].elapsed_time(ev[1]), ev[1].elapsed_time(ev[2]), ev[2].elapsed_time(ev[3])
+    peaks, src = _peaks()
+    hbm = float(peaks.get("hbm_gbs", 6800.0))
+    fwd_gbs = nnz * 8 * steps / (t_f * 1e-3) / 1e9
+    out = {"workload": f"graded HH: In 100 -> Mid 20,000 (+ recurrent) -> Out 100, p = 0.05, {steps} steps of 0.05 ms",
+           "synapses": nnz, "checkpoint_every": K, "loss": loss,
+           "forward_ms": t_f, "backward_ms": t_b, "adjoint_total_ms": t_f + t_b,
+           "six_forward_runs_ms": t_fd, "adjoint_vs_fd_speedup": t_fd / (t_f + t_b),
+           "gradients": 3 + nnz, "grad_scale": gs.cpu().tolist(),
+           "forward_synapse_stream_gbs": fwd_gbs, "forward_frac_hbm": fwd_gbs / hbm,
+           "finite": bool(torch.isfinite(gs).all() and all(torch.isfinite(g).all() for g in gw))}
+    net.close()
+    return out
 
 
 def _cpu_baseline(sim_steps):
@@ -453,6 +491,9 @@ def run_ours(a):
     batched = None
     if not a.no_batched and rank == 0:
         batched = _batched(snn, torch, dev, a.batch_instances, a.batch_steps)
+    differentiable = None
+    if not a.no_graded and rank == 0:
+        differentiable = _differentiable(snn, torch, dev)
 
     cpu = None
     if rank == 0 and world == 1 and not a.no_cpu_baseline:
@@ -477,6 +518,7 @@ def run_ours(a):
                 "engine": engine,
                 "autotune": tune,
                 "batched": batched,
+                "differentiable": differentiable,
                 "gpu_launches": a.steps * ((-(-a.sim_steps // 1000)) + 2 if engine == "persistent"
                                            else 2 * a.sim_steps + 2),
                 "clocks": clk.summary()}
