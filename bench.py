@@ -64,6 +64,7 @@ def _args():
     ap.add_argument("--batch-instances", type=int, default=512)
     ap.add_argument("--batch-steps", type=int, default=5000)
     ap.add_argument("--no-graded", action="store_true", help="skip the differentiable-form measurement")
+    ap.add_argument("--no-gscale", action="store_true", help="skip the gScale sweep and fit")
     ap.add_argument("--no-scale-point", action="store_true",
                     help="skip the forced-activity propagation measurement at 100 x 1,000,000, p = 0.5")
     return ap.parse_args()
@@ -276,6 +277,27 @@ def _differentiable(snn, torch, dev, steps=2000, K=100):
            "finite": bool(torch.isfinite(gs).all() and all(torch.isfinite(g).all() for g in gw))}
     net.close()
     return out
+
+
+def _gscale_procedure(dev, steps=5000):
+    """The paper's Fig. 1 procedure on the batched form: nConn 100..1000 step
+    50 x gScale 2^(k/4), k = -8..16, reference (1000, 1.0); selection by
+    closest avgSpike among NaN-free runs; fit of k1 / (k2 + nConn) + k3."""
+    from paper_1412_0595_gb300 import gscale as G
+    import torch
+    n_conn = list(range(100, 1001, 50))
+    grid = [2.0 ** (k / 4.0) for k in range(-8, 17)]
+    specs, keys = G.sweep_specs(n_conn, grid, steps=steps)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    recs = G.run_sweep(specs, keys, device=dev)
+    t_run = time.perf_counter() - t0
+    x, y, target = G.select(recs, 1000.0, 1.0)
+    (k1, k2, k3), mape = G.fit(x, y)
+    return {"runs": len(recs), "steps": steps, "seconds_incl_build": t_run, "reference_avg_spike": target,
+            "k1": k1, "k2": k2, "k3": k3, "mape_percent": mape,
+            "selected": {str(int(a)): float(b) for a, b in zip(x, y)},
+            "nan_runs": int(sum(r["sum_nans"] > 0 for r in recs))}
 
 
 def _cpu_baseline(sim_steps):
@@ -494,6 +516,9 @@ def run_ours(a):
     differentiable = None
     if not a.no_graded and rank == 0:
         differentiable = _differentiable(snn, torch, dev)
+    gscale_fit = None
+    if not a.no_gscale and rank == 0:
+        gscale_fit = _gscale_procedure(dev)
 
     cpu = None
     if rank == 0 and world == 1 and not a.no_cpu_baseline:
@@ -519,6 +544,7 @@ def run_ours(a):
                 "autotune": tune,
                 "batched": batched,
                 "differentiable": differentiable,
+                "gscale_fit": gscale_fit,
                 "gpu_launches": a.steps * ((-(-a.sim_steps // 1000)) + 2 if engine == "persistent"
                                            else 2 * a.sim_steps + 2),
                 "clocks": clk.summary()}

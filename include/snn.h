@@ -80,6 +80,11 @@ enum {
                                   (one cooperative launch for many steps), 2 choose (default:
                                   persistent when every tile gets its own resident CTA) */
     SNN_OPT_PERSIST_STEPS = 6, /* steps per persistent launch; default 1000 */
+    SNN_OPT_TEST_BARRIER_EXTRA = 8, /* test hook, 0 (default) or 1: with 1 the persistent
+                                  engine's grid barrier waits for one arrival that never
+                                  comes, so every CTA runs out of SNN_OPT_SPIN_LIMIT and the
+                                  next synchronising call returns SNN_ERR_TIMEOUT; snn_reset
+                                  recovers the network */
     SNN_OPT_TILED = 7          /* compressed-row propagation of the plain engine: 0 one warp per
                                   row chunk with global atomics, 1 post-tiled through shared
                                   memory, 2 choose (default: post-tiled when a row has

@@ -244,6 +244,7 @@ PersistArgs persist_args(snn_net* net, int32_t n_steps) {
     p.acc1 = net->acc + 2 * NT;
     p.acc_stride = (int32_t)NT;
     p.n_steps = n_steps;
+    p.barrier_extra = net->barrier_extra;
     p.bar = net->bar;
     return p;
 }
@@ -756,6 +757,10 @@ snn_status snn_set_option(snn_net* net, int32_t option, int64_t value) {
         if (value < 0 || value > 2) return fail(SNN_ERR_INVALID_ARG, "engine: 0 plain, 1 persistent, 2 choose");
         if (value == 1 && net->persist_grid <= 0) return fail(SNN_ERR_STATE, "persistent kernel cannot be resident");
         net->engine = (int32_t)value;
+        break;
+    case SNN_OPT_TEST_BARRIER_EXTRA:
+        if (value < 0 || value > 1) return fail(SNN_ERR_INVALID_ARG, "test barrier hook: 0 or 1");
+        net->barrier_extra = (int32_t)value;
         break;
     case SNN_OPT_TILED:
         if (value < 0 || value > 2) return fail(SNN_ERR_INVALID_ARG, "tiled: 0 off, 1 on, 2 choose");

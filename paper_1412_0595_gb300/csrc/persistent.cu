@@ -165,7 +165,9 @@ __global__ void __launch_bounds__(kTile) k_step_persistent(const PersistArgs A) 
                 __syncthreads();
             }
         }
-        if (!grid_sync(A.bar, bar_base + (unsigned long long)(k + 1) * gridDim.x, a.spin_limit, a.error)) return;
+        if (!grid_sync(A.bar, bar_base + (unsigned long long)(k + 1) * gridDim.x + (unsigned long long)A.barrier_extra,
+                       a.spin_limit, a.error))
+            return;
     }
 
     // fold the last step's events into the conductances and clear the buffer

@@ -161,6 +161,7 @@ struct PersistArgs {
     float* acc1;                   // [2][n_total] incoming events, channel 1
     int32_t acc_stride;            // n_total
     int32_t n_steps;
+    int32_t barrier_extra;         // test hook: arrivals the barrier waits for beyond the grid (0 normally)
     GridBarrier* bar;
 };
 
@@ -232,6 +233,7 @@ struct snn_net {
     int32_t engine = 2;                       // 0 plain, 1 persistent, 2 choose
     int32_t persist_steps = 1000;             // steps per persistent launch
     int32_t persist_grid = 0;                 // co-resident CTAs of the persistent kernel
+    int32_t barrier_extra = 0;                // test hook of SNN_OPT_TEST_BARRIER_EXTRA
     int32_t tiled = 2;                        // post-tiled rows: 0 off, 1 all compressed projections, 2 choose
     // graded (differentiable) networks
     bool graded = false;

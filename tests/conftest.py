@@ -10,6 +10,14 @@ if ROOT not in sys.path:
 
 def pytest_configure(config):
     config.addinivalue_line("markers", "gpu: needs a CUDA GPU (runs the CUDA library)")
+    # the C-ABI tests load the library; build it (nvcc cross-compiles) if it is missing
+    lib = os.path.join(ROOT, "paper_1412_0595_gb300", "_build", "libsnn.so")
+    if not os.path.exists(lib):
+        import importlib.util
+        spec = importlib.util.spec_from_file_location("_snn_build", os.path.join(ROOT, "paper_1412_0595_gb300", "build.py"))
+        mod = importlib.util.module_from_spec(spec)
+        spec.loader.exec_module(mod)
+        mod.build()
 
 
 @pytest.fixture(scope="session")

@@ -124,3 +124,28 @@ def test_post_tiled_steps_match_row_kernel(gpu):
     ref.step(150)
     assert np.abs(b.read_host(1, "V") - ref.get(1, "V")).max() <= 1e-3
     assert a.synaptic_events() == b.synaptic_events() == ref.events
+
+
+def test_barrier_wait_times_out_and_reset_recovers(gpu):
+    # the barrier waits for one arrival nobody makes: every CTA gives up after
+    # the spin limit, the host reads SNN_ERR_TIMEOUT, nothing hangs
+    import paper_1412_0595_gb300 as snn
+    spec = I.config_small(steps=50, n_hh=600)
+    net = gpu.Network.from_spec(spec)
+    net.set_option("engine", 1)
+    net.set_option("spin_limit", 2000)
+    net.set_option("test_barrier_extra", 1)
+    net.step(20)
+    with pytest.raises(snn.SNNError) as e:
+        net.sync()
+    assert e.value.name == "SNN_ERR_TIMEOUT"
+    net.set_option("test_barrier_extra", 0)
+    net.set_option("spin_limit", 1 << 22)
+    net.reset()
+    net.step(50)
+    net.sync()
+    ref = gpu.Network.from_spec(spec)
+    ref.set_option("engine", 1)
+    ref.step(50)
+    assert np.abs(net.read_host(1, "V") - ref.read_host(1, "V")).max() < 1e-5
+    assert net.counters(0) == ref.counters(0)
