@@ -77,7 +77,10 @@ enum {
     SNN_OPT_CHUNK = 3,         /* synapses per warp work item of the row kernel (multiple of 128) */
     SNN_OPT_SPIN_LIMIT = 4,    /* iterations of a bounded device wait before SNN_ERR_TIMEOUT */
     SNN_OPT_ENGINE = 5,        /* 0 plain (two kernels per step, graph replay), 1 persistent
-                                  (one cooperative launch for many steps), 2 choose (default:
+                                  (one cooperative launch for many steps), 3 cluster (one
+                                  thread-block cluster of up to 16 CTAs, events in distributed
+                                  shared memory; networks up to 65,536 padded neurons),
+                                  2 choose (default: cluster when the network fits one, else
                                   persistent when every tile gets its own resident CTA) */
     SNN_OPT_PERSIST_STEPS = 6, /* steps per persistent launch; default 1000 */
     SNN_OPT_TEST_BARRIER_EXTRA = 8, /* test hook, 0 (default) or 1: with 1 the persistent
@@ -216,7 +219,7 @@ snn_status snn_reset(snn_net* net, void* stream);
 /* Sets an SNN_OPT_* option (see the enum). */
 snn_status snn_set_option(snn_net* net, int32_t option, int64_t value);
 
-/* Engine snn_step uses with the current options: 0 plain, 1 persistent. */
+/* Engine snn_step uses with the current options: 0 plain, 1 persistent, 3 cluster. */
 snn_status snn_get_engine(snn_net* net, int32_t* engine);
 
 /* Steps simulated since creation or the last reset (synchronises `stream`). */
@@ -231,7 +234,8 @@ snn_status snn_synaptic_events(snn_net* net, int64_t* events, void* stream);
  * kernels: phase 0 = neuron update with spike compaction, 1 = propagation,
  * 2 = one persistent launch of SNN_OPT_PERSIST_STEPS complete steps,
  * 3 = the propagation kernel again on the list last staged by
- * snn_debug_propagate (SNN_ERR_STATE if none).
+ * snn_debug_propagate (SNN_ERR_STATE if none), 4 = one cluster launch of
+ * SNN_OPT_PERSIST_STEPS complete steps (SNN_ERR_STATE if it does not fit).
  * A neuron phase without its propagation advances the state without
  * delivering spikes.  Enqueued on `stream`. */
 snn_status snn_launch_phase(snn_net* net, int32_t phase, void* stream);

@@ -153,10 +153,13 @@ snn_status upload_projs(snn_net* net) {
         d.nspk = net->nspk + 2 * P.d.pre;
         d.pre_count = net->nrn_count + pre.offset;
         d.acc = net->acc + (P.d.channel == 0 ? 0 : 2 * (size_t)std::max(1, net->n_total)) + post.offset;
+        d.post_soa = post.offset;
+        d.channel = P.d.channel;
         d.mode = P.mode;
         d.ptile = kPostTile;
         d.n_ptiles = (post.d.n + kPostTile - 1) / kPostTile;
         d.split = P.split;
+        d.csplit = P.csplit;
     }
     if (!dp.empty())
         CK(cudaMemcpy(net->d_projs, dp.data(), dp.size() * sizeof(DevProj), cudaMemcpyHostToDevice),
@@ -227,9 +230,14 @@ cudaError_t launch_all_projections(snn_net* net, cudaStream_t s) {
     return launch_projections(net, net->d_projs, host.data(), (int)host.size(), s);
 }
 
+bool use_cluster(const snn_net* net) {
+    if (net->cluster_size == 0) return false;
+    return net->engine == 3 || net->engine == 2;
+}
+
 bool use_persistent(const snn_net* net) {
     if (net->engine == 1) return net->persist_grid > 0;
-    if (net->engine == 0) return false;
+    if (net->engine != 2) return false;
     return net->num_tiles > 0 && net->num_tiles <= net->persist_grid;   // one resident CTA per tile
 }
 
@@ -534,6 +542,23 @@ snn_status create_impl(const snn_pop_desc* pops, int32_t n_pops, const snn_proj_
         CK(cudaStreamSynchronize(s), "synchronize");
     }
     CK(persistent_capacity(net->sm_count, &net->persist_grid), "persistent occupancy");
+    {
+        int per = 0;
+        const int cl = cluster_plan(net->num_tiles * kTile, n_pops, &per);
+        bool ok = false;
+        if (cl && !graded_requested(projs, n_projs))
+            CK(cluster_supported(cl, per, net->num_tiles, &ok), "cluster occupancy");
+        net->cluster_size = ok ? cl : 0;
+        net->cluster_per_cta = ok ? per : 0;
+        for (int q = 0; ok && q < n_projs; ++q) {   // each row's segment in each CTA's slice
+            ProjHost& P = net->projs[q];
+            if (P.d.layout != SNN_LAYOUT_CSR) continue;
+            const int32_t n_pre = pops[P.d.pre].n, n_post = pops[P.d.post].n;
+            TRY(dalloc(net, &P.csplit, (size_t)n_pre * (cl + 1) + 1, "cluster row segments"));
+            CK(launch_cluster_splits(P.row_ptr, P.col, n_pre, net->pops[P.d.post].offset, n_post, cl, per, P.csplit,
+                                     s), "cluster row segments");
+        }
+    }
     TRY(setup_tiled(net, s));
     if (graded_requested(projs, n_projs)) TRY(graded_setup(net, s));
     // save the creation state for snn_reset
@@ -622,6 +647,14 @@ snn_status snn_step(snn_net* net, int64_t n_steps, void* stream) {
     cudaStream_t s = (cudaStream_t)stream;
     try {
         if (net->graded) return graded_step(net, n_steps, s);
+        if (use_cluster(net)) {
+            for (int64_t left = n_steps; left > 0;) {
+                const int32_t k = (int32_t)std::min<int64_t>(left, net->persist_steps);
+                CK(launch_cluster(persist_args(net, k), net->cluster_size, net->cluster_per_cta, s), "cluster steps");
+                left -= k;
+            }
+            return SNN_OK;
+        }
         if (use_persistent(net)) {
             CK(enqueue_persistent(net, n_steps, s), "persistent steps");
             return SNN_OK;
@@ -754,8 +787,9 @@ snn_status snn_set_option(snn_net* net, int32_t option, int64_t value) {
         net->spin_limit = (uint32_t)value;
         break;
     case SNN_OPT_ENGINE:
-        if (value < 0 || value > 2) return fail(SNN_ERR_INVALID_ARG, "engine: 0 plain, 1 persistent, 2 choose");
+        if (value < 0 || value > 3) return fail(SNN_ERR_INVALID_ARG, "engine: 0 plain, 1 persistent, 2 choose, 3 cluster");
         if (value == 1 && net->persist_grid <= 0) return fail(SNN_ERR_STATE, "persistent kernel cannot be resident");
+        if (value == 3 && net->cluster_size == 0) return fail(SNN_ERR_STATE, "network does not fit one cluster");
         net->engine = (int32_t)value;
         break;
     case SNN_OPT_TEST_BARRIER_EXTRA:
@@ -779,7 +813,7 @@ snn_status snn_set_option(snn_net* net, int32_t option, int64_t value) {
 
 snn_status snn_get_engine(snn_net* net, int32_t* engine) {
     if (!net || !engine) return fail(SNN_ERR_INVALID_ARG, "bad argument");
-    *engine = use_persistent(net) ? 1 : 0;
+    *engine = net->graded ? 0 : use_cluster(net) ? 3 : use_persistent(net) ? 1 : 0;
     return SNN_OK;
 }
 
@@ -805,9 +839,13 @@ snn_status snn_synaptic_events(snn_net* net, int64_t* events, void* stream) {
 }
 
 snn_status snn_launch_phase(snn_net* net, int32_t phase, void* stream) {
-    if (!net || phase < 0 || phase > 3) return fail(SNN_ERR_INVALID_ARG, "bad network or phase");
+    if (!net || phase < 0 || phase > 4) return fail(SNN_ERR_INVALID_ARG, "bad network or phase");
     cudaStream_t s = (cudaStream_t)stream;
-    if (phase == 3) {
+    if (phase == 4) {
+        if (net->cluster_size == 0) return fail(SNN_ERR_STATE, "network does not fit one cluster");
+        CK(launch_cluster(persist_args(net, net->persist_steps), net->cluster_size, net->cluster_per_cta, s),
+           "cluster phase");
+    } else if (phase == 3) {
         if (!net->dbg_staged) return fail(SNN_ERR_STATE, "no spike list staged by snn_debug_propagate");
         const ProjHost* h = &net->projs[net->dbg_proj];
         CK(launch_projections(net, net->d_dbg_proj, &h, 1, s), "staged propagation");

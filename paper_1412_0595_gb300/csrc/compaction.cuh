@@ -15,9 +15,11 @@ namespace snn {
 // Called by every thread of the CTA (kTile threads) with its spike flag.
 // Returns the tile's spike total; s_off[warp] receives warp offsets within
 // the tile and *s_base the claimed start in the population list.
+// A tile without spikes costs one barrier.
 __device__ __forceinline__ int tile_claim(bool spike, unsigned ballot, int* s_off, int* s_total, int* s_base,
                                           int32_t* nspk_slot) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (__syncthreads_count(spike) == 0) return 0;
     if (lane == 0) s_off[warp] = __popc(ballot);
     __syncthreads();
     if (warp == 0) {
@@ -35,7 +37,6 @@ __device__ __forceinline__ int tile_claim(bool spike, unsigned ballot, int* s_of
         }
     }
     __syncthreads();
-    (void)spike;
     return *s_total;
 }
 

@@ -70,36 +70,62 @@ struct HHRates {
     float am, bm, ah, bh, an, bn;
 };
 
+// 2^x and 1/x on the special-function unit (PTX ex2.approx.ftz.f32 and
+// rcp.approx.ftz.f32: relative error about 2^-22, subnormals flushed).
+__device__ __forceinline__ float ex2_fast(float x) {
+    float y;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
+__device__ __forceinline__ float rcp_fast(float x) {
+    float y;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
 __device__ __forceinline__ HHRates hh_rates(float V) {
-    constexpr float kLog2e = 1.4426950408889634f;
+    constexpr float L = 1.4426950408889634f;             // log2(e)
     constexpr float kExpM5 = 6.737946999085467e-3f;     // exp(-5)
-    const float x = (-52.0f - V) * 0.25f;                // alpha_m argument
-    const float y = (V + 25.0f) * 0.2f;                  // beta_m argument
-    const float z = (-50.0f - V) * 0.2f;                 // alpha_n argument
-    const float Em = exp2f(x * kLog2e);
-    const float E = exp2f(y * kLog2e);
-    const float Eh = exp2f((-48.0f - V) * (kLog2e / 18.0f));
-    const float En = exp2f((-55.0f - V) * (kLog2e / 40.0f));
+    // every argument is one fused multiply-add of V
+    const float x = fmaf(V, -0.25f, -13.0f);             // alpha_m argument (-52 - V)/4
+    const float y = fmaf(V, 0.2f, 5.0f);                 // beta_m argument (V + 25)/5
+    const float z = fmaf(V, -0.2f, -10.0f);              // alpha_n argument (-50 - V)/5
+    const float Em = ex2_fast(fmaf(V, -0.25f * L, -13.0f * L));
+    const float E = ex2_fast(fmaf(V, 0.2f * L, 5.0f * L));
+    const float Eh = ex2_fast(fmaf(V, -L / 18.0f, -48.0f * L / 18.0f));
+    const float En = ex2_fast(fmaf(V, -L / 40.0f, -55.0f * L / 40.0f));
     HHRates r;
-    r.am = 1.28f * (fabsf(x) < 0.1f ? linoid_series(x) : __fdividef(x, Em - 1.0f));
-    r.bm = 1.4f * (fabsf(y) < 0.1f ? linoid_series(y) : __fdividef(y, E - 1.0f));
-    r.an = 0.16f * (fabsf(z) < 0.1f ? linoid_series(z) : __fdividef(z * E, kExpM5 - E));
+    r.am = 1.28f * x * rcp_fast(Em - 1.0f);
+    r.bm = 1.4f * y * rcp_fast(E - 1.0f);
+    r.an = 0.16f * z * E * rcp_fast(kExpM5 - E);
+    // near the removable singularities exp(x) - 1 cancels: use the series
+    const bool near = (fabsf(x) < 0.1f) | (fabsf(y) < 0.1f) | (fabsf(z) < 0.1f);
+    if (near) {
+        if (fabsf(x) < 0.1f) r.am = 1.28f * linoid_series(x);
+        if (fabsf(y) < 0.1f) r.bm = 1.4f * linoid_series(y);
+        if (fabsf(z) < 0.1f) r.an = 0.16f * linoid_series(z);
+    }
     r.ah = 0.128f * Eh;
-    r.bh = __fdividef(4.0f * E, E + 1.0f);
+    r.bh = 4.0f * E * rcp_fast(E + 1.0f);
     r.bn = 0.5f * En;
     return r;
 }
 
 // One forward-Euler substep with every right-hand side at the substep start.
+// The currents are arranged as fused multiply-adds: g (V - E) = fma(g, V, -g E)
+// and dx/dt = alpha - (alpha + beta) x.
 __device__ __forceinline__ void hh_substep(const HHCell& c, float hs, float hs_over_C, float I_in,
                                            float& V, float& m, float& h, float& n) {
     const HHRates r = hh_rates(V);
     const float m3h = m * m * m * h;
     const float n2 = n * n;
-    const float I = I_in - c.gNa * m3h * (V - c.ENa) - c.gK * (n2 * n2) * (V - c.EK) - c.gL * (V - c.EL);
-    const float dm = r.am * (1.0f - m) - r.bm * m;
-    const float dh = r.ah * (1.0f - h) - r.bh * h;
-    const float dn = r.an * (1.0f - n) - r.bn * n;
+    float I = fmaf(-c.gL, V, fmaf(c.gL, c.EL, I_in));
+    I = fmaf(-(n2 * n2), fmaf(c.gK, V, -c.gK * c.EK), I);
+    I = fmaf(-m3h, fmaf(c.gNa, V, -c.gNa * c.ENa), I);
+    const float dm = fmaf(-(r.am + r.bm), m, r.am);
+    const float dh = fmaf(-(r.ah + r.bh), h, r.ah);
+    const float dn = fmaf(-(r.an + r.bn), n, r.an);
     V = fmaf(hs_over_C, I, V);
     m = fmaf(hs, dm, m);
     h = fmaf(hs, dh, h);

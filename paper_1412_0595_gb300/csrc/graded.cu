@@ -57,9 +57,9 @@ __device__ __forceinline__ HHDerivs hh_rate_derivs(float V, const HHRates& r) {
     const float x = (-52.0f - V) * 0.25f;
     const float y = (V + 25.0f) * 0.2f;
     const float z = (-50.0f - V) * 0.2f;
-    const float Em = exp2f(x * kLog2e);
-    const float E = exp2f(y * kLog2e);
-    const float Ez = __fdividef(kExpM5, E);
+    const float Em = ex2_fast(x * kLog2e);
+    const float E = ex2_fast(y * kLog2e);
+    const float Ez = kExpM5 * rcp_fast(E);
     HHDerivs d;
     d.am = 1.28f * dlinoid(x, Em) * -0.25f;
     d.bm = 1.4f * dlinoid(y, E) * 0.2f;

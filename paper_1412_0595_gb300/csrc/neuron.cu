@@ -7,54 +7,75 @@
 // step epoch (ticket / num_tiles), which drives the counter-based random
 // numbers and the parity of the double-buffered list lengths, so nothing is
 // reset between steps and no tile waits for another.
+#include <algorithm>
+
 #include "compaction.cuh"
 #include "neuron_update.cuh"
 
 namespace snn {
 
-__global__ void __launch_bounds__(kTile) k_neuron_step(const NeuronArgs a) {
-    __shared__ unsigned long long s_ticket;
+__global__ void __launch_bounds__(kTile, 6) k_neuron_step(const NeuronArgs a) {
     __shared__ int s_off[kTile / 32];
     __shared__ int s_total, s_base;
-    if (threadIdx.x == 0) s_ticket = atomicAdd(a.ticket, 1ull);
+    __shared__ uint32_t s_t;
+    __shared__ int s_slot;
+    __shared__ DevPop s_pop;
+    // This CTA's tiles are blockIdx.x, blockIdx.x + gridDim.x, ...  It takes
+    // that many tickets with one atomic add; whatever the order of the CTAs,
+    // every ticket of one launch lies in [e * num_tiles, (e + 1) * num_tiles),
+    // so ticket / num_tiles is the step epoch e.
+    const int my_tiles = (a.num_tiles - (int)blockIdx.x + (int)gridDim.x - 1) / (int)gridDim.x;
+    if (threadIdx.x == 0) {
+        const unsigned long long ticket = atomicAdd(a.ticket, (unsigned long long)my_tiles);
+        const unsigned long long epoch = ticket / (unsigned long long)a.num_tiles;
+        s_t = (uint32_t)(epoch - *a.epoch_base);          // simulated step
+        s_slot = (int)(epoch & 1ull);
+    }
     __syncthreads();
-    const unsigned long long ticket = s_ticket;
-    const int tile = (int)(ticket % (unsigned long long)a.num_tiles);
-    const unsigned long long epoch = ticket / (unsigned long long)a.num_tiles;
-    const uint32_t t = (uint32_t)(epoch - *a.epoch_base);      // simulated step
-    const DevPop& P = a.pops[a.tile_pop[tile]];
-    const int local = (tile - P.first_tile) * kTile + (int)threadIdx.x;
-    const bool active = local < P.n;
-    const int idx = P.offset + local;
+    const uint32_t t = s_t;
+    const int slot = s_slot;
     const PhiloxKey key{a.seed_lo, a.seed_hi};
-    const int slot = (int)(epoch & 1ull);
-    if (tile == P.first_tile && threadIdx.x == 0) P.nspk[slot ^ 1] = 0;   // next step's count
-
-    bool spike = false, is_nan = false;
-    if (active) {
-        NeuronState s{};
-        if (P.kind == SNN_POP_HH)
-            s = NeuronState{a.V[idx], a.m[idx], a.h[idx], a.n[idx], a.g0[idx], a.g1[idx], a.iext[idx]};
-        float isyn;
-        spike = neuron_step(P, key, t, local, a.hs, a.n_sub, s, &isyn);
-        if (P.kind == SNN_POP_HH) {
-            is_nan = isnan(s.V);
-            a.V[idx] = s.V; a.m[idx] = s.m; a.h[idx] = s.h; a.n[idx] = s.n;
-            a.g0[idx] = s.g0; a.g1[idx] = s.g1; a.iext[idx] = s.ie;
-            if (a.isyn_rec) a.isyn_rec[idx] = isyn;
-        }
-    }
-
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const unsigned ballot = __ballot_sync(0xffffffffu, spike);
-    const unsigned nan_ballot = __ballot_sync(0xffffffffu, is_nan);
-    if (lane == 0 && nan_ballot) atomicAdd(P.nan_count, (unsigned long long)__popc(nan_ballot));
-    const int total = tile_claim(spike, ballot, s_off, &s_total, &s_base, P.nspk + slot);
-    if (spike) {
-        P.spk[s_base + s_off[warp] + __popc(ballot & ((1u << lane) - 1u))] = local;
-        P.neuron_spikes[local] += 1;
+    int cur_pop = -1;
+    for (int tile = blockIdx.x; tile < a.num_tiles; tile += gridDim.x) {
+        const int p = a.tile_pop[tile];
+        if (p != cur_pop) {                                  // uniform: a new population descriptor
+            __syncthreads();
+            copy_pop(&s_pop, a.pops + p);
+            __syncthreads();
+            cur_pop = p;
+        }
+        const DevPop& P = s_pop;
+        const int local = (tile - P.first_tile) * kTile + (int)threadIdx.x;
+        const bool active = local < P.n;
+        const int idx = P.offset + local;
+        if (tile == P.first_tile && threadIdx.x == 0) P.nspk[slot ^ 1] = 0;   // next step's count
+
+        bool spike = false, is_nan = false;
+        if (active) {
+            NeuronState s{};
+            if (P.kind == SNN_POP_HH)
+                s = NeuronState{a.V[idx], a.m[idx], a.h[idx], a.n[idx], a.g0[idx], a.g1[idx], a.iext[idx]};
+            float isyn;
+            spike = neuron_step(P, key, t, local, a.hs, a.n_sub, s, &isyn);
+            if (P.kind == SNN_POP_HH) {
+                is_nan = isnan(s.V);
+                a.V[idx] = s.V; a.m[idx] = s.m; a.h[idx] = s.h; a.n[idx] = s.n;
+                a.g0[idx] = s.g0; a.g1[idx] = s.g1; a.iext[idx] = s.ie;
+                if (a.isyn_rec) a.isyn_rec[idx] = isyn;
+            }
+        }
+
+        const unsigned ballot = __ballot_sync(0xffffffffu, spike);
+        const unsigned nan_ballot = __ballot_sync(0xffffffffu, is_nan);
+        if (lane == 0 && nan_ballot) atomicAdd(P.nan_count, (unsigned long long)__popc(nan_ballot));
+        const int total = tile_claim(spike, ballot, s_off, &s_total, &s_base, P.nspk + slot);
+        if (spike) {
+            P.spk[s_base + s_off[warp] + __popc(ballot & ((1u << lane) - 1u))] = local;
+            P.neuron_spikes[local] += 1;
+        }
+        if (threadIdx.x == 0 && total) atomicAdd(P.spike_count, (unsigned long long)total);
     }
-    if (threadIdx.x == 0 && total) atomicAdd(P.spike_count, (unsigned long long)total);
 }
 
 __global__ void k_init_state(const DevPop* pops, const int32_t* tile_pop, float* V, float* m,
@@ -77,9 +98,25 @@ __global__ void k_set_epoch_base(unsigned long long* ticket, int num_tiles) {
     ticket[1] = ticket[0] / (unsigned long long)num_tiles;
 }
 
+// Resident CTAs of the step kernel on the current device (cached per device).
+static int neuron_grid_cap() {
+    static int cap[64] = {0};
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return 0;
+    if (cap[dev] == 0) {
+        int sms = 0, per_sm = 0;
+        if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_neuron_step, kTile, 0) != cudaSuccess) return 0;
+        cap[dev] = std::max(1, sms * per_sm);
+    }
+    return cap[dev];
+}
+
 cudaError_t launch_neuron_step(const NeuronArgs& a, cudaStream_t s) {
     if (a.num_tiles == 0) return cudaSuccess;
-    k_neuron_step<<<a.num_tiles, kTile, 0, s>>>(a);
+    const int cap = neuron_grid_cap();
+    if (cap == 0) return cudaErrorUnknown;
+    k_neuron_step<<<std::min(a.num_tiles, cap), kTile, 0, s>>>(a);
     return cudaGetLastError();
 }
 

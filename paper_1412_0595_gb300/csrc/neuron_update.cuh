@@ -8,6 +8,17 @@
 
 namespace snn {
 
+// Copies a population descriptor into shared memory (the calling CTA's
+// threads cooperate; the caller synchronises before use).  Reading the
+// per-population constants from shared memory keeps them off the global
+// load path of every step.
+__device__ __forceinline__ void copy_pop(DevPop* dst, const DevPop* src) {
+    static_assert(sizeof(DevPop) % 4 == 0, "DevPop is copied in 4-byte words");
+    const int words = (int)(sizeof(DevPop) / 4);
+    for (int i = threadIdx.x; i < words; i += blockDim.x)
+        reinterpret_cast<int*>(dst)[i] = reinterpret_cast<const int*>(src)[i];
+}
+
 struct NeuronState {
     float V, m, h, n, g0, g1, ie;
 };

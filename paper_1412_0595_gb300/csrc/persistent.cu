@@ -77,10 +77,11 @@ __device__ __forceinline__ void push_row(const DevProj& q, int i, float* dst, in
 }
 
 template <bool kResident>
-__global__ void __launch_bounds__(kTile) k_step_persistent(const PersistArgs A) {
+__global__ void __launch_bounds__(kTile, 6) k_step_persistent(const PersistArgs A) {
     __shared__ int s_off[kTile / 32];
     __shared__ int s_spk[kTile];
     __shared__ int s_total, s_base;
+    __shared__ DevPop s_pop;
     const NeuronArgs& a = A.n;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const unsigned long long T0 = *a.ticket;                 // a multiple of num_tiles
@@ -108,7 +109,12 @@ __global__ void __launch_bounds__(kTile) k_step_persistent(const PersistArgs A) 
         const int prev = (int)((e64 + 1ull) & 1ull) * NT;    // buffer of step e - 1
         const int cur = (int)(e64 & 1ull) * NT;              // buffer of step e
         for (int tile = blockIdx.x; tile < a.num_tiles; tile += gridDim.x) {
-            const DevPop& P = a.pops[a.tile_pop[tile]];
+            if (!kResident || k == 0) {
+                __syncthreads();                      // previous readers of s_pop are done
+                copy_pop(&s_pop, a.pops + a.tile_pop[tile]);
+                __syncthreads();
+            }
+            const DevPop& P = s_pop;
             const int local = (tile - P.first_tile) * kTile + (int)threadIdx.x;
             const bool active = local < P.n;
             const int idx = P.offset + local;

@@ -63,10 +63,13 @@ struct DevProj {
     const int32_t* nspk;   // [2] list lengths of the pre population (slot e & 1)
     const int32_t* pre_count;   // per-neuron spike counts of the pre population
     float* acc;            // persistent engine: event accumulator (buffer 0), offset to the post population
+    int32_t post_soa;      // SoA offset of the post population
+    int32_t channel;       // post conductance channel
     int32_t mode;          // compressed rows: 0 warp per row chunk, 1 post-tiled (own kernel)
     int32_t n_ptiles;      // post tiles of the post-tiled mode
     int32_t ptile;         // posts per tile
     const int64_t* split;  // [n_pre][n_ptiles + 1] first synapse of each row in each post tile
+    const int64_t* csplit; // cluster engine: [n_pre][cluster size + 1] first synapse of each row in each CTA slice
 };
 
 // Grid barrier of the persistent engine: a monotone arrival counter.  A launch
@@ -199,6 +202,7 @@ struct ProjHost {
     int32_t max_row;
     int32_t mode = 0;          // 1: post-tiled propagation
     int64_t* split = nullptr;
+    int64_t* csplit = nullptr;     // cluster engine row segments
     int64_t* row_ptr = nullptr;
     int32_t* col = nullptr;
     float* w = nullptr;
@@ -234,6 +238,7 @@ struct snn_net {
     int32_t persist_steps = 1000;             // steps per persistent launch
     int32_t persist_grid = 0;                 // co-resident CTAs of the persistent kernel
     int32_t barrier_extra = 0;                // test hook of SNN_OPT_TEST_BARRIER_EXTRA
+    int32_t cluster_size = 0, cluster_per_cta = 0;   // cluster engine plan (0: does not fit)
     int32_t tiled = 2;                        // post-tiled rows: 0 off, 1 all compressed projections, 2 choose
     // graded (differentiable) networks
     bool graded = false;
@@ -331,6 +336,11 @@ cudaError_t launch_propagate_tiled(const DevProj* q, int32_t P, const unsigned l
                                    int blocks, cudaStream_t s);
 constexpr int32_t kPostTile = 8192;          // posts per tile of the post-tiled propagation (32 KiB)
 cudaError_t persistent_capacity(int sm_count, int* blocks);
+int cluster_plan(int n_total, int n_pops, int* per_cta);
+cudaError_t cluster_supported(int cl, int per_cta, int num_tiles, bool* ok);
+cudaError_t launch_cluster_splits(const int64_t* row_ptr, const int32_t* col, int32_t n_pre, int32_t post_soa,
+                                  int32_t n_post, int32_t n_ranks, int32_t per_cta, int64_t* split, cudaStream_t s);
+cudaError_t launch_cluster(const PersistArgs& a, int cl, int per_cta, cudaStream_t s);
 cudaError_t launch_graded_spmv(const GradedArgs& a, cudaStream_t s);
 cudaError_t launch_graded_neuron(const GradedArgs& a, cudaStream_t s);
 cudaError_t launch_graded_release_init(const GradedArgs& a, cudaStream_t s);

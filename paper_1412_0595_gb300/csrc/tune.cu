@@ -172,6 +172,7 @@ snn_status snn_autotune(snn_net* net, int32_t trial_steps, snn_tuning* result, v
             for (int chunk : {512, 1024, 2048})
                 for (int tiled : {0, 2}) cands.push_back({0, blocks, chunk, tiled, 0.0});
         if (net->persist_grid > 0) cands.push_back({1, 4 * sm, 1024, 2, 0.0});
+        if (net->cluster_size > 0) cands.push_back({3, 4 * sm, 1024, 2, 0.0});
         // snapshot of the live network, restored after every trial
         const size_t nb = snapshot_bytes(net);
         void* snap = net->mem.get(nb);

@@ -259,10 +259,10 @@ class Network:
 
     @property
     def engine(self):
-        """Engine snn_step uses: 'plain' or 'persistent'."""
+        """Engine snn_step uses: 'plain', 'persistent' or 'cluster'."""
         v = C.c_int32()
         check(L.lib.snn_get_engine(self.h, C.byref(v)))
-        return "persistent" if v.value == 1 else "plain"
+        return {0: "plain", 1: "persistent", 3: "cluster"}[v.value]
 
     @property
     def t(self):
@@ -356,7 +356,7 @@ class Network:
     def autotune(self, trial_steps=200, stream=None):
         r = L.Tuning()
         check(L.lib.snn_autotune(self.h, int(trial_steps), C.byref(r), _stream(stream)))
-        return {"engine": "persistent" if r.engine == 1 else "plain", "prop_blocks": r.prop_blocks,
+        return {"engine": {0: "plain", 1: "persistent", 3: "cluster"}[r.engine], "prop_blocks": r.prop_blocks,
                 "chunk": r.chunk, "tiled": r.tiled, "us_per_step": r.us_per_step, "cached": bool(r.cached)}
 
     # ------------------------------------------------------------------ checks

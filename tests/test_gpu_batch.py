@@ -101,7 +101,7 @@ def test_autotune_picks_a_configuration_and_keeps_the_trajectory(gpu):
     a.step(50)
     b.step(50)
     r = a.autotune(trial_steps=100)
-    assert r["engine"] in ("plain", "persistent") and r["us_per_step"] > 0 and not r["cached"]
+    assert r["engine"] in ("plain", "persistent", "cluster") and r["us_per_step"] > 0 and not r["cached"]
     assert a.t == 50
     a.step(200)
     b.step(200)

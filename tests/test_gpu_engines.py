@@ -16,20 +16,25 @@ def _rel_ok(got, want, rel=1e-5):
     return np.all(np.abs(got - want) <= rel * np.maximum(np.abs(want), floor) + 1e-30)
 
 
-def test_small_networks_choose_the_persistent_engine(gpu):
+def test_engine_choice(gpu):
     net = gpu.Network.from_spec(I.config_four_pop(steps=1))
+    assert net.engine == "cluster"                 # 10,220 neurons fit one 16-CTA cluster
+    net.set_option("engine", 1)
     assert net.engine == "persistent"
     net.set_option("engine", 0)
     assert net.engine == "plain"
+    big = gpu.Network.from_spec(I.config_small(steps=1, n_hh=200_000))
+    assert big.engine == "persistent"              # too big for a cluster, one resident CTA per tile
 
 
-def test_persistent_engine_matches_oracle_step_by_step(gpu):
+@pytest.mark.parametrize("engine", [1, 3])
+def test_persistent_engine_matches_oracle_step_by_step(gpu, engine):
     pops = [I.source_pop(257, 500.0), I.hh_pop(1), I.hh_pop(255), I.hh_pop(513)]
     projs = [I.proj(0, 1, "csr", 0.5, ("uniform", 0, 3.0)), I.proj(0, 2, "dense", 1.0, ("uniform", 0, 0.3)),
              I.proj(0, 3, "csr", 0.1, ("uniform", 0, 3.0), channel=1)]
     spec = I.net(pops, projs, dt=0.1, steps=1)
     net = gpu.Network.from_spec(spec)
-    net.set_option("engine", 1)
+    net.set_option("engine", engine)
     net.set_option("record_isyn", 1)
     ref = oracle.from_spec(spec)
     for t in range(60):
@@ -45,11 +50,12 @@ def test_persistent_engine_matches_oracle_step_by_step(gpu):
         assert net.counters(p) == ref.counters(p)
 
 
-def test_persistent_engine_long_launch_matches_oracle(gpu):
+@pytest.mark.parametrize("engine", [1, 3])
+def test_persistent_engine_long_launch_matches_oracle(gpu, engine):
     # forced activity: the HH population spikes, rows are pushed by their owners
     spec = I.config_small(steps=3000, n_hh=400, n_src=100, p=0.2, weight_hi=60.0)
     net = gpu.Network.from_spec(spec)
-    assert net.engine == "persistent"
+    net.set_option("engine", engine)
     net.set_option("persist_steps", 700)        # several launches, ragged last one
     ref = oracle.from_spec(spec)
     net.step(spec["steps"])
@@ -67,7 +73,7 @@ def test_engines_alternate_on_one_trajectory(gpu):
     b = gpu.Network.from_spec(spec)
     a.set_option("engine", 0)
     a.step(300)
-    for eng in (1, 0, 1):
+    for eng in (1, 0, 3):
         b.set_option("engine", eng)
         b.step(100)
     for p in range(4):
@@ -149,3 +155,21 @@ def test_barrier_wait_times_out_and_reset_recovers(gpu):
     ref.step(50)
     assert np.abs(net.read_host(1, "V") - ref.read_host(1, "V")).max() < 1e-5
     assert net.counters(0) == ref.counters(0)
+
+
+def test_cluster_engine_spiking_four_population_network(gpu):
+    # the cluster engine on the four-population shape with forced activity in
+    # every population (dense and compressed rows, both channels)
+    spec = I.config_four_pop(steps=600, n_mid=3000, weight=("lognormal", 5.0, 0.5))
+    a = gpu.Network.from_spec(spec)
+    b = gpu.Network.from_spec(spec)
+    a.set_option("engine", 3)
+    b.set_option("engine", 0)
+    a.step(600)
+    b.step(600)
+    ref = oracle.from_spec(spec)
+    ref.step(600)
+    for p in range(4):
+        ca, cb, co = a.counters(p)[0], b.counters(p)[0], ref.counters(p)[0]
+        assert abs(ca - co) <= 0.02 * co + 1 and abs(cb - co) <= 0.02 * co + 1, (p, ca, cb, co)
+    assert a.counters(1)[0] > 1000 and a.counters(2)[0] > 100 and a.counters(3)[0] > 10
