@@ -350,15 +350,16 @@ def _flush_l2(buf):
     buf.add_(1.0)
 
 
-def _persistent_time_ms(net, reps, torch):
-    """Average device time of one persistent launch (SNN_OPT_PERSIST_STEPS
-    complete steps), timed with events on the launching stream."""
+def _persistent_time_ms(net, reps, torch, phase=2):
+    """Average device time of one multi-step launch (SNN_OPT_PERSIST_STEPS
+    complete steps; phase 2 the persistent kernel, 4 the cluster kernel),
+    timed with events on the launching stream."""
     s = torch.cuda.current_stream()
-    net.launch_phase(2)
+    net.launch_phase(phase)
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record(s)
     for _ in range(reps):
-        net.launch_phase(2)
+        net.launch_phase(phase)
     e1.record(s)
     e1.synchronize()
     net.sync()
@@ -451,7 +452,8 @@ def run_ours(a):
     net.set_option("persist_steps", PERSIST)
     t_neuron = _phase_time_ms(net, 0, a.phase_reps, torch)
     t_prop = _phase_time_ms(net, 1, a.phase_reps, torch)
-    t_persist = _persistent_time_ms(net, 3, torch) if engine == "persistent" else None
+    multi = engine in ("persistent", "cluster")
+    t_persist = _persistent_time_ms(net, 3, torch, 4 if engine == "cluster" else 2) if multi else None
     peaks, src = _peaks()
     sm_mhz = float(peaks.get("sm_max_mhz", 2070.0))
     fp32_peak = SM_COUNT * FP32_LANES * 2 * sm_mhz * 1e6 / 1e12        # TFLOP/s
@@ -472,16 +474,21 @@ def run_ours(a):
     prop_gbs = prop_bytes / (t_prop * 1e-3) / 1e9
     other = {"k_neuron_step_us": 1e3 * t_neuron, "k_propagate_us": 1e3 * t_prop,
              "neuron_tflops": neuron_tflops, "propagate_gbs": prop_gbs}
-    if engine == "persistent":
+    if multi:
+        kname = "k_step_cluster" if engine == "cluster" else "k_step_persistent"
         flops = PERSIST * n_hh * flops_per_neuron_step
         ach = flops / (t_persist * 1e-3) / 1e12
-        roof = {"kernel": "k_step_persistent", "bound": "alu", "achieved": ach, "peak": fp32_peak,
+        roof = {"kernel": kname, "bound": "alu", "achieved": ach, "peak": fp32_peak,
                 "unit": "TFLOP/s", "frac": ach / fp32_peak, "traffic": None,
                 "peak_source": "FP32 FMA peak from 152 SMs x 128 lanes x 2 x max SM clock "
                                f"({sm_mhz:.0f} MHz, {src})",
                 "launch_us": 1e3 * t_persist, "steps_per_launch": PERSIST, "flops_per_launch": flops,
                 "us_per_step": 1e3 * t_persist / PERSIST}
-        other["k_step_persistent_us_per_step"] = 1e3 * t_persist / PERSIST
+        if engine == "cluster":
+            sms = net.cluster_size
+            roof["sms_used"] = sms
+            roof["frac_of_used_sms"] = ach / (fp32_peak * sms / SM_COUNT)
+        other[kname + "_us_per_step"] = 1e3 * t_persist / PERSIST
     elif t_neuron >= t_prop:
         roof = {"kernel": "k_neuron_step", "bound": "alu", "achieved": neuron_tflops, "peak": fp32_peak,
                 "unit": "TFLOP/s", "frac": neuron_tflops / fp32_peak, "traffic": None,
@@ -545,7 +552,7 @@ def run_ours(a):
                 "batched": batched,
                 "differentiable": differentiable,
                 "gscale_fit": gscale_fit,
-                "gpu_launches": a.steps * ((-(-a.sim_steps // 1000)) + 2 if engine == "persistent"
+                "gpu_launches": a.steps * ((-(-a.sim_steps // 1000)) + 2 if multi
                                            else 2 * a.sim_steps + 2),
                 "clocks": clk.summary()}
         print(json.dumps(line), flush=True)

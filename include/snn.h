@@ -88,6 +88,8 @@ enum {
                                   comes, so every CTA runs out of SNN_OPT_SPIN_LIMIT and the
                                   next synchronising call returns SNN_ERR_TIMEOUT; snn_reset
                                   recovers the network */
+    SNN_OPT_CLUSTER_CTAS = 9,  /* read only (snn_get_option): CTAs of the cluster engine's plan,
+                                  0 when the network does not fit one cluster */
     SNN_OPT_TILED = 7          /* compressed-row propagation of the plain engine: 0 one warp per
                                   row chunk with global atomics, 1 post-tiled through shared
                                   memory, 2 choose (default: post-tiled when a row has
@@ -218,6 +220,10 @@ snn_status snn_reset(snn_net* net, void* stream);
 
 /* Sets an SNN_OPT_* option (see the enum). */
 snn_status snn_set_option(snn_net* net, int32_t option, int64_t value);
+
+/* Reads the current value of an SNN_OPT_* option into *value (host
+ * pointer).  SNN_ERR_INVALID_ARG for an unknown option or a NULL pointer. */
+snn_status snn_get_option(const snn_net* net, int32_t option, int64_t* value);
 
 /* Engine snn_step uses with the current options: 0 plain, 1 persistent, 3 cluster. */
 snn_status snn_get_engine(snn_net* net, int32_t* engine);

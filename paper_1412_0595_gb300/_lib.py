@@ -21,7 +21,7 @@ SYN_EXP, SYN_GRADED = 0, 1
 FIELD = {"V": 0, "m": 1, "h": 2, "n": 3, "g0": 4, "g1": 5, "iext": 6, "isyn": 7, "spikes": 8, "nspk": 9,
          "spike_count": 10, "nan_count": 11, "neuron_spikes": 12}
 OPT = {"record_isyn": 0, "graph_steps": 1, "prop_blocks": 2, "chunk": 3, "spin_limit": 4, "engine": 5,
-       "persist_steps": 6, "tiled": 7, "test_barrier_extra": 8}
+       "persist_steps": 6, "tiled": 7, "test_barrier_extra": 8, "cluster_ctas": 9}
 
 
 class PopDesc(C.Structure):
@@ -83,6 +83,7 @@ def _load():
         "snn_write_state": [vp, i32, i32, vp, sz, i32, vp],
         "snn_reset": [vp, vp],
         "snn_set_option": [vp, i32, i64],
+        "snn_get_option": [vp, i32, C.POINTER(C.c_int64)],
         "snn_get_step": [vp, P(i64), vp],
         "snn_get_engine": [vp, P(i32)],
         "snn_synaptic_events": [vp, P(i64), vp],

@@ -765,6 +765,24 @@ snn_status snn_reset(snn_net* net, void* stream) {
     return SNN_OK;
 }
 
+snn_status snn_get_option(const snn_net* net, int32_t option, int64_t* value) {
+    if (!net || !value) return fail(SNN_ERR_INVALID_ARG, "net or value is NULL");
+    switch (option) {
+    case SNN_OPT_RECORD_ISYN: *value = net->record_isyn ? 1 : 0; break;
+    case SNN_OPT_GRAPH_STEPS: *value = net->graph_steps; break;
+    case SNN_OPT_PROP_BLOCKS: *value = net->prop_blocks; break;
+    case SNN_OPT_CHUNK: *value = net->chunk; break;
+    case SNN_OPT_SPIN_LIMIT: *value = net->spin_limit; break;
+    case SNN_OPT_ENGINE: *value = net->engine; break;
+    case SNN_OPT_PERSIST_STEPS: *value = net->persist_steps; break;
+    case SNN_OPT_TILED: *value = net->tiled; break;
+    case SNN_OPT_TEST_BARRIER_EXTRA: *value = net->barrier_extra; break;
+    case SNN_OPT_CLUSTER_CTAS: *value = net->cluster_size; break;
+    default: return fail(SNN_ERR_INVALID_ARG, "unknown option");
+    }
+    return SNN_OK;
+}
+
 snn_status snn_set_option(snn_net* net, int32_t option, int64_t value) {
     if (!net) return fail(SNN_ERR_INVALID_ARG, "net is NULL");
     switch (option) {

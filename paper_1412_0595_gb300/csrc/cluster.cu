@@ -30,11 +30,18 @@ constexpr int kCT = 1024;          // threads per CTA
 constexpr int kMaxSlicePops = 4 * kCT / kTile + 1;   // populations one CTA's slice can touch
 constexpr int kMaxClusterTiles = 16 * 4 * kCT / kTile;  // tiles of the largest network one cluster holds
 
-__device__ __forceinline__ void st_cluster_u32(const uint32_t* local_addr, int rank, uint32_t v) {
+__device__ __forceinline__ void st_cluster_u64(const unsigned long long* local_addr, int rank, unsigned long long v) {
     const uint32_t laddr = (uint32_t)__cvta_generic_to_shared(local_addr);
     uint32_t raddr;
     asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(raddr) : "r"(laddr), "r"(rank));
-    asm volatile("st.shared::cluster.u32 [%0], %1;" ::"r"(raddr), "r"(v) : "memory");
+    asm volatile("st.shared::cluster.u64 [%0], %1;" ::"r"(raddr), "l"(v) : "memory");
+}
+
+// A spike word: the low 32 bits of the step epoch above the warp's ballot.
+// A word whose tag is not the step being read holds no spikes of that step,
+// so the words are never cleared.
+__device__ __forceinline__ uint32_t word_spikes(unsigned long long w, uint32_t tag) {
+    return (uint32_t)(w >> 32) == tag ? (uint32_t)w : 0u;
 }
 
 // Adds this CTA's share of the outgoing rows of spiking neuron `idx` (SoA
@@ -85,22 +92,24 @@ __device__ __forceinline__ void pull_row(const PersistArgs& A, const int32_t* s_
 template <int NPT>
 __global__ void __launch_bounds__(kCT, 1) k_step_cluster(const PersistArgs A, int per_cta) {
     extern __shared__ float s_mem[];
-    // [channel 0/1][per_cta] accumulators, then the spike bitmask [2 parities][n_words]
-    float* acc = s_mem;
-    uint32_t* bits = reinterpret_cast<uint32_t*>(s_mem + 2 * per_cta);
+    // spike words [2 parities][n_words] (8-byte aligned at the start), then the
+    // accumulators [channel 0/1][per_cta]
+    unsigned long long* bits = reinterpret_cast<unsigned long long*>(s_mem);
+    const int n_words = A.n.num_tiles * (kTile / 32);
+    float* acc = reinterpret_cast<float*>(bits + 2 * n_words);
     __shared__ DevPop s_pops[kMaxSlicePops];
     __shared__ int32_t s_tile_pop[kMaxClusterTiles], s_tile_local[kMaxClusterTiles];
     __shared__ int32_t s_out_begin[kMaxClusterTiles + 1];
     __shared__ uint8_t s_tile_heavy[kMaxClusterTiles];
     __shared__ int32_t s_heavy[32];                        // bitmask words of heavy rows
     __shared__ int32_t s_n_heavy;
+    __shared__ unsigned long long s_pop_spikes[kMaxSlicePops];   // spikes of this launch per slice population
     cg::cluster_group cluster = cg::this_cluster();
     const NeuronArgs& a = A.n;
     const int n_ranks = (int)cluster.num_blocks();
     const int rank = (int)cluster.block_rank();
     const int base = rank * per_cta;                       // first owned SoA index
     const int n_soa = a.num_tiles * kTile;
-    const int n_words = n_soa / 32;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const unsigned long long T0 = *a.ticket;
     const unsigned long long epoch0 = T0 / (unsigned long long)a.num_tiles;
@@ -111,7 +120,8 @@ __global__ void __launch_bounds__(kCT, 1) k_step_cluster(const PersistArgs A, in
     const int p_hi = last_idx >= base ? a.tile_pop[last_idx / kTile] : p_lo - 1;
     for (int p = p_lo; p <= p_hi; ++p) copy_pop(s_pops + (p - p_lo), a.pops + p);
     for (int j = threadIdx.x; j < 2 * per_cta; j += kCT) acc[j] = 0.0f;
-    for (int j = threadIdx.x; j < 2 * n_words; j += kCT) bits[j] = 0u;
+    for (int j = threadIdx.x; j < 2 * n_words; j += kCT) bits[j] = 0ull;
+    for (int p = threadIdx.x; p < kMaxSlicePops; p += kCT) s_pop_spikes[p] = 0ull;
     for (int tl = threadIdx.x; tl < a.num_tiles; tl += kCT) {
         const int p = a.tile_pop[tl];
         s_tile_pop[tl] = p;
@@ -153,7 +163,7 @@ __global__ void __launch_bounds__(kCT, 1) k_step_cluster(const PersistArgs A, in
     }
 
     NeuronState st[NPT];
-    int pop_of[NPT], local_of[NPT];
+    int pop_of[NPT], local_of[NPT], n_spk[NPT];
     bool live[NPT];
 #pragma unroll
     for (int u = 0; u < NPT; ++u) {
@@ -162,6 +172,7 @@ __global__ void __launch_bounds__(kCT, 1) k_step_cluster(const PersistArgs A, in
         live[u] = false;
         pop_of[u] = 0;
         local_of[u] = 0;
+        n_spk[u] = 0;
         st[u] = NeuronState{};
         if (off < per_cta && idx < n_soa) {
             const int tile = idx / kTile;
@@ -177,22 +188,29 @@ __global__ void __launch_bounds__(kCT, 1) k_step_cluster(const PersistArgs A, in
             }
         }
     }
-    cluster.sync();                                        // bitmasks cleared everywhere
+    // the list lengths of the launch's last step (and of the step after it)
+    // start at zero; only the last step writes the API spike list
+#pragma unroll
+    for (int u = 0; u < NPT; ++u)
+        if (live[u] && local_of[u] == 0) {
+            s_pops[pop_of[u]].nspk[0] = 0;
+            s_pops[pop_of[u]].nspk[1] = 0;
+        }
+    cluster.sync();                                        // words and list lengths cleared everywhere
 
     for (int k = 0; k <= A.n_steps; ++k) {
         const unsigned long long e64 = epoch0 + (unsigned long long)k;
         const int slot = (int)(e64 & 1ull);
-        uint32_t* prev_bits = bits + (slot ^ 1) * n_words;
         // ---- pull: the previous step's spikes, my slice of their rows --------
-        // Light rows: each lane reads one word of the bitmask (and clears it);
-        // the warp then adds, spike by spike, this CTA's segment of each row.
-        // Heavy rows: every warp reads the heavy words and adds a 1/32 share of
-        // each segment.
+        // Light rows: each lane reads one word; the warp then adds, spike by
+        // spike, this CTA's segment of each row.  Heavy rows: every warp reads
+        // the heavy words and adds a 1/32 share of each segment.
         if (k > 0) {
+            const unsigned long long* prev = bits + (slot ^ 1) * n_words;
+            const uint32_t tag = (uint32_t)(e64 - 1ull);
             for (int w0 = warp * 32; w0 < n_words; w0 += kCT) {
                 const int wd = w0 + lane;
-                uint32_t m = (wd < n_words && !s_tile_heavy[wd / (kTile / 32)]) ? prev_bits[wd] : 0u;
-                if (m) prev_bits[wd] = 0u;
+                const uint32_t m = (wd < n_words && !s_tile_heavy[wd / (kTile / 32)]) ? word_spikes(prev[wd], tag) : 0u;
                 unsigned nz = __ballot_sync(0xffffffffu, m != 0u);
                 while (nz) {
                     const int l = __ffs(nz) - 1;
@@ -209,7 +227,7 @@ __global__ void __launch_bounds__(kCT, 1) k_step_cluster(const PersistArgs A, in
             const int n_heavy = s_n_heavy;
             if (n_heavy > 0) {
                 const int hw = lane < n_heavy ? s_heavy[lane] : 0;
-                const uint32_t hm = lane < n_heavy ? prev_bits[hw] : 0u;
+                const uint32_t hm = lane < n_heavy ? word_spikes(prev[hw], tag) : 0u;
                 unsigned nz = __ballot_sync(0xffffffffu, hm != 0u);
                 while (nz) {
                     const int l = __ffs(nz) - 1;
@@ -224,12 +242,12 @@ __global__ void __launch_bounds__(kCT, 1) k_step_cluster(const PersistArgs A, in
                     }
                 }
             }
-            __syncthreads();                                // events in acc; heavy words read by every warp
-            if (threadIdx.x < n_heavy) prev_bits[s_heavy[threadIdx.x]] = 0u;
+            __syncthreads();                                // events in acc
         }
         if (k == A.n_steps) break;                         // the last pull folds into g below
         const uint32_t t = (uint32_t)(e64 - ebase);
-        uint32_t* cur_bits = bits + slot * n_words;
+        const bool last = k == A.n_steps - 1;
+        unsigned long long* cur = bits + slot * n_words;
 #pragma unroll
         for (int u = 0; u < NPT; ++u) {
             const int off = threadIdx.x + u * kCT;
@@ -237,7 +255,6 @@ __global__ void __launch_bounds__(kCT, 1) k_step_cluster(const PersistArgs A, in
             bool spike = false;
             if (live[u]) {
                 const DevPop& P = s_pops[pop_of[u]];
-                if (local_of[u] == 0) P.nspk[slot ^ 1] = 0;     // next step's count (one writer per population)
                 if (P.kind == SNN_POP_HH) {
                     st[u].g0 += acc[off];
                     st[u].g1 += acc[per_cta + off];
@@ -250,34 +267,34 @@ __global__ void __launch_bounds__(kCT, 1) k_step_cluster(const PersistArgs A, in
                     if (isnan(st[u].V)) atomicAdd(P.nan_count, 1ull);
                     if (a.isyn_rec) a.isyn_rec[idx] = isyn;
                 }
+                n_spk[u] += spike ? 1 : 0;
             }
             const unsigned ballot = __ballot_sync(0xffffffffu, spike);
             if (ballot && off < per_cta) {
-                // the warp's 32 neurons are one word of every CTA's bitmask
+                // the warp's 32 neurons are one word of every CTA's spike words
                 const int wd = (base + u * kCT + warp * 32) / 32;
-                if (lane < n_ranks) st_cluster_u32(cur_bits + wd, lane, ballot);
-                // API spike list and counters (a warp's neurons share one population)
-                const DevPop& P = s_pops[pop_of[u]];
-                int pos = 0;
-                if (lane == 0) {
-                    pos = atomicAdd(P.nspk + slot, __popc(ballot));
-                    atomicAdd(P.spike_count, (unsigned long long)__popc(ballot));
-                }
-                pos = __shfl_sync(0xffffffffu, pos, 0);
-                if (spike) {
-                    P.spk[pos + __popc(ballot & ((1u << lane) - 1u))] = local_of[u];
-                    P.neuron_spikes[local_of[u]] += 1;
+                if (lane < n_ranks) st_cluster_u64(cur + wd, lane, ((unsigned long long)(uint32_t)e64 << 32) | ballot);
+                // a warp's neurons share one population
+                if (lane == 0) atomicAdd(s_pop_spikes + pop_of[u], (unsigned long long)__popc(ballot));
+                if (last) {                                // the API spike list of the last step
+                    const DevPop& P = s_pops[pop_of[u]];
+                    int pos = 0;
+                    if (lane == 0) pos = atomicAdd(P.nspk + slot, __popc(ballot));
+                    pos = __shfl_sync(0xffffffffu, pos, 0);
+                    if (spike) P.spk[pos + __popc(ballot & ((1u << lane) - 1u))] = local_of[u];
                 }
             }
         }
-        cluster.sync();                                    // this step's spikes are in every bitmask
+        cluster.sync();                                    // this step's spikes are in every CTA's words
     }
 
-    // fold the last step's events (pulled above) and write the state back
+    // fold the last step's events (pulled above), write the state and the
+    // launch's spike counts back
 #pragma unroll
     for (int u = 0; u < NPT; ++u) {
         if (!live[u]) continue;
         const DevPop& P = s_pops[pop_of[u]];
+        if (n_spk[u]) P.neuron_spikes[local_of[u]] += n_spk[u];
         if (P.kind != SNN_POP_HH) continue;
         const int off = threadIdx.x + u * kCT;
         const int idx = base + off;
@@ -286,6 +303,8 @@ __global__ void __launch_bounds__(kCT, 1) k_step_cluster(const PersistArgs A, in
         a.V[idx] = st[u].V; a.m[idx] = st[u].m; a.h[idx] = st[u].h; a.n[idx] = st[u].n;
         a.g0[idx] = st[u].g0; a.g1[idx] = st[u].g1; a.iext[idx] = st[u].ie;
     }
+    const int tp = (int)threadIdx.x;                       // signed: an empty slice has p_hi - p_lo = -1
+    if (tp <= p_hi - p_lo && s_pop_spikes[tp]) atomicAdd(s_pops[tp].spike_count, s_pop_spikes[tp]);
     cluster.sync();                                        // no CTA leaves while others may read its memory
     if (rank == 0 && threadIdx.x == 0)
         *a.ticket = T0 + (unsigned long long)A.n_steps * (unsigned long long)a.num_tiles;
@@ -311,7 +330,7 @@ __global__ void k_cluster_splits(const int64_t* row_ptr, const int32_t* col, int
 }
 
 size_t cluster_smem(int per_cta, int num_tiles) {
-    return sizeof(float) * 2 * (size_t)per_cta + sizeof(uint32_t) * 2 * (size_t)num_tiles * (kTile / 32);
+    return sizeof(unsigned long long) * 2 * (size_t)num_tiles * (kTile / 32) + sizeof(float) * 2 * (size_t)per_cta;
 }
 
 template <int NPT>

@@ -257,6 +257,16 @@ class Network:
     def set_option(self, name, value):
         check(L.lib.snn_set_option(self.h, L.OPT[name], int(value)))
 
+    def get_option(self, name):
+        v = C.c_int64(0)
+        check(L.lib.snn_get_option(self.h, L.OPT[name], C.byref(v)))
+        return int(v.value)
+
+    @property
+    def cluster_size(self):
+        """CTAs (SMs) of the cluster engine's plan; 0 if the network does not fit one cluster."""
+        return self.get_option("cluster_ctas")
+
     @property
     def engine(self):
         """Engine snn_step uses: 'plain', 'persistent' or 'cluster'."""

@@ -25,6 +25,18 @@ def test_engine_choice(gpu):
     assert net.engine == "plain"
     big = gpu.Network.from_spec(I.config_small(steps=1, n_hh=200_000))
     assert big.engine == "persistent"              # too big for a cluster, one resident CTA per tile
+    assert big.cluster_size == 0
+
+
+def test_options_read_back(gpu):
+    net = gpu.Network.from_spec(I.config_four_pop(steps=1))
+    # 43 tiles of 256 neurons over 16 CTAs: 3 tiles (768 neurons) per CTA
+    assert net.cluster_size == 16
+    for name, value in (("persist_steps", 250), ("chunk", 512), ("graph_steps", 7), ("engine", 1), ("tiled", 0)):
+        net.set_option(name, value)
+        assert net.get_option(name) == value
+    with pytest.raises(Exception):
+        net.set_option("cluster_ctas", 8)          # read only
 
 
 @pytest.mark.parametrize("engine", [1, 3])
