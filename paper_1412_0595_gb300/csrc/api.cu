@@ -189,14 +189,15 @@ NeuronArgs neuron_args(snn_net* net) {
 int prop_blocks(snn_net* net) { return net->prop_blocks > 0 ? net->prop_blocks : net->sm_count * 4; }
 
 // Post-tiled propagation pays off when a row has many synapses in each post
-// tile (at least ~1024: density x tile >= 1024) and there are several tiles.
+// tile (at least 256: density x tile >= 256, i.e. density >= 1/8) and there
+// are several tiles.
 bool want_tiled(const snn_net* net, const ProjHost& P) {
     if (P.d.layout != SNN_LAYOUT_CSR || net->tiled == 0) return false;
     if (net->tiled == 1) return true;
     const int32_t n_pre = net->pops[P.d.pre].d.n, n_post = net->pops[P.d.post].d.n;
     if (n_post <= 2 * kPostTile || n_pre == 0) return false;
     const double per_tile = (double)P.nnz / n_pre * kPostTile / n_post;
-    return per_tile >= 1024.0;
+    return per_tile >= 256.0;
 }
 
 snn_status setup_tiled(snn_net* net, cudaStream_t s) {
@@ -219,7 +220,8 @@ cudaError_t launch_projections(snn_net* net, const DevProj* dev, const ProjHost*
     cudaError_t e = launch_propagate(p, prop_blocks(net), s);
     for (int q = 0; q < n && e == cudaSuccess; ++q)
         if (host[q]->mode == 1)
-            e = launch_propagate_tiled(dev + q, kPostTile, net->ticket, std::max(1, net->num_tiles), net->sm_count * 4, s);
+            e = launch_propagate_tiled(dev + q, kPostTile, net->ticket, std::max(1, net->num_tiles), net->sm_count,
+                                       net->error, net->spin_limit, s);
     return e;
 }
 

@@ -87,28 +87,29 @@ __device__ __forceinline__ float rcp_fast(float x) {
 __device__ __forceinline__ HHRates hh_rates(float V) {
     constexpr float L = 1.4426950408889634f;             // log2(e)
     constexpr float kExpM5 = 6.737946999085467e-3f;     // exp(-5)
-    // every argument is one fused multiply-add of V
-    const float x = fmaf(V, -0.25f, -13.0f);             // alpha_m argument (-52 - V)/4
-    const float y = fmaf(V, 0.2f, 5.0f);                 // beta_m argument (V + 25)/5
-    const float z = fmaf(V, -0.2f, -10.0f);              // alpha_n argument (-50 - V)/5
+    // every argument is one fused multiply-add of V; the rate constants
+    // 1.28, 1.4 and 0.16 are folded into the linear factors, 0.128 and 0.5
+    // into the exponents (log2 0.128 and log2 0.5 = -1)
+    const float xs = fmaf(V, -0.25f * 1.28f, -13.0f * 1.28f);   // 1.28 (-52 - V)/4
+    const float ys = fmaf(V, 0.2f * 1.4f, 5.0f * 1.4f);         // 1.4 (V + 25)/5
+    const float zs = fmaf(V, -0.2f * 0.16f, -10.0f * 0.16f);    // 0.16 (-50 - V)/5
     const float Em = ex2_fast(fmaf(V, -0.25f * L, -13.0f * L));
     const float E = ex2_fast(fmaf(V, 0.2f * L, 5.0f * L));
-    const float Eh = ex2_fast(fmaf(V, -L / 18.0f, -48.0f * L / 18.0f));
-    const float En = ex2_fast(fmaf(V, -L / 40.0f, -55.0f * L / 40.0f));
     HHRates r;
-    r.am = 1.28f * x * rcp_fast(Em - 1.0f);
-    r.bm = 1.4f * y * rcp_fast(E - 1.0f);
-    r.an = 0.16f * z * E * rcp_fast(kExpM5 - E);
+    r.ah = ex2_fast(fmaf(V, -L / 18.0f, -48.0f * L / 18.0f - 2.965784284662087f));
+    r.bn = ex2_fast(fmaf(V, -L / 40.0f, -55.0f * L / 40.0f - 1.0f));
+    r.am = xs * rcp_fast(Em - 1.0f);
+    r.bm = ys * rcp_fast(E - 1.0f);
+    r.an = zs * E * rcp_fast(kExpM5 - E);
     // near the removable singularities exp(x) - 1 cancels: use the series
-    const bool near = (fabsf(x) < 0.1f) | (fabsf(y) < 0.1f) | (fabsf(z) < 0.1f);
+    const bool near = (fabsf(xs) < 0.1f * 1.28f) | (fabsf(ys) < 0.1f * 1.4f) | (fabsf(zs) < 0.1f * 0.16f);
     if (near) {
+        const float x = fmaf(V, -0.25f, -13.0f), y = fmaf(V, 0.2f, 5.0f), z = fmaf(V, -0.2f, -10.0f);
         if (fabsf(x) < 0.1f) r.am = 1.28f * linoid_series(x);
         if (fabsf(y) < 0.1f) r.bm = 1.4f * linoid_series(y);
         if (fabsf(z) < 0.1f) r.an = 0.16f * linoid_series(z);
     }
-    r.ah = 0.128f * Eh;
     r.bh = 4.0f * E * rcp_fast(E + 1.0f);
-    r.bn = 0.5f * En;
     return r;
 }
 

@@ -333,8 +333,8 @@ cudaError_t launch_count_events(const DevProj* projs, int n_projs, unsigned long
 cudaError_t launch_row_splits(const int64_t* row_ptr, const int32_t* col, int32_t n_pre, int32_t n_tiles, int32_t P,
                               int64_t* split, cudaStream_t s);
 cudaError_t launch_propagate_tiled(const DevProj* q, int32_t P, const unsigned long long* ticket, int32_t num_tiles,
-                                   int blocks, cudaStream_t s);
-constexpr int32_t kPostTile = 8192;          // posts per tile of the post-tiled propagation (32 KiB)
+                                   int sm_count, uint32_t* error, uint32_t spin_limit, cudaStream_t s);
+constexpr int32_t kPostTile = 2048;          // posts per tile of the post-tiled propagation (8 KiB)
 cudaError_t persistent_capacity(int sm_count, int* blocks);
 int cluster_plan(int n_total, int n_pops, int* per_cta);
 cudaError_t cluster_supported(int cl, int per_cta, int num_tiles, bool* ok);

@@ -109,17 +109,23 @@ def test_persistent_engine_with_more_tiles_than_resident_ctas(gpu):
     assert net.counters(0) == ref.counters(0)
 
 
-@pytest.mark.parametrize("n_post", [20001, 8192, 3])
-def test_post_tiled_propagation_matches_oracle(gpu, n_post):
-    spec = I.net([I.source_pop(64, 0.0), I.hh_pop(n_post)],
-                 [I.proj(0, 1, "csr", 0.4, ("uniform", 0.0, 1.0))], dt=0.1, steps=1)
+@pytest.mark.parametrize("n_pre,n_post,p,ks", [
+    (64, 20001, 0.4, (1, 5, 64)),
+    (64, 8192, 0.4, (1, 5, 64)),
+    (64, 3, 0.4, (1, 5, 64)),
+    (64, 20001, 0.9, (1, 64)),            # segments of ~3,700 synapses per row and tile
+    (40000, 20001, 0.01, (40000,)),       # ~1,300 pieces per CTA: several descriptor batches
+])
+def test_post_tiled_propagation_matches_oracle(gpu, n_pre, n_post, p, ks):
+    spec = I.net([I.source_pop(n_pre, 0.0), I.hh_pop(n_post)],
+                 [I.proj(0, 1, "csr", p, ("uniform", 0.0, 1.0))], dt=0.1, steps=1)
     net = gpu.Network.from_spec(spec)
     net.set_option("engine", 0)
     net.set_option("tiled", 1)
     ref = oracle.from_spec(spec)
     rng = np.random.default_rng(2)
-    for k in (1, 5, 64):
-        spk = np.sort(rng.choice(64, k, replace=False)).astype(np.int32)
+    for k in ks:
+        spk = np.sort(rng.choice(n_pre, k, replace=False)).astype(np.int32)
         net.debug_propagate(0, spk)
         ref.deliver(0, spk)
         assert _rel_ok(net.read_host(1, "g0"), ref.get(1, "g0"))
