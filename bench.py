@@ -11,9 +11,9 @@ Metric: synaptic events/s (events = stored synapses of the spiking rows,
 counted exactly from per-neuron spike counts), with HH neuron-steps/s beside
 it.  Inputs are resident in HBM when the timed region starts; L2 is flushed
 (256 MiB written, then another 256 MiB read) between timed steps.  `e2e`
-repeats the measurement through
-the public API from pinned host buffers (weights and initial potentials
-copied in, connectivity drawn on the device, counters copied out).
+repeats the measurement through the public API from pinned host buffers
+(weights and initial potentials copied in, connectivity drawn on the device,
+counters copied out).
 
 --impl reference times the FP64 CPU oracle (the only reference this method
 has) on a bounded sample of the same workload.

@@ -56,31 +56,43 @@ __device__ __forceinline__ void dense_item(const DevProj& q, int64_t r, int lane
     const int pb = (int)(r - sb * q.chunks);
     const int ns = q.nspk[slot];
     const int s_beg = (int)sb * kDenseRows;
-    const int s_end = min(ns, s_beg + kDenseRows);
+    const int cnt = min(ns, s_beg + kDenseRows) - s_beg;          // spiking rows of this item (<= 32)
     const int n_post = q.n_post;
     const int j = pb * kDensePosts + 4 * lane;
-    if (j >= n_post) return;
+    const bool in = j < n_post;
+    // lane t holds the t-th spiking row, so the weight loads below do not wait
+    // on a spike-list load; eight rows are in flight per lane
+    const int my_row = lane < cnt ? q.spk[s_beg + lane] : 0;
     float a0 = 0.f, a1 = 0.f, a2 = 0.f, a3 = 0.f;
+    const float sc = q.scale;
     if ((n_post & 3) == 0) {
-        for (int s = s_beg; s < s_end; ++s) {
-            const float4 w4 = __ldcs(reinterpret_cast<const float4*>(q.w + (int64_t)q.spk[s] * n_post + j));
-            a0 += w4.x; a1 += w4.y; a2 += w4.z; a3 += w4.w;
+#pragma unroll 8
+        for (int t = 0; t < cnt; ++t) {
+            const int row = __shfl_sync(0xffffffffu, my_row, t);
+            if (in) {
+                const float4 w4 = __ldcs(reinterpret_cast<const float4*>(q.w + (int64_t)row * n_post + j));
+                a0 += w4.x; a1 += w4.y; a2 += w4.z; a3 += w4.w;
+            }
         }
-        const float sc = q.scale;
-        atomicAdd(reinterpret_cast<float4*>(q.g + j), make_float4(sc * a0, sc * a1, sc * a2, sc * a3));
+        if (in) atomicAdd(reinterpret_cast<float4*>(q.g + j), make_float4(sc * a0, sc * a1, sc * a2, sc * a3));
     } else {
-        for (int s = s_beg; s < s_end; ++s) {
-            const float* row = q.w + (int64_t)q.spk[s] * n_post + j;
-            a0 += row[0];
-            if (j + 1 < n_post) a1 += row[1];
-            if (j + 2 < n_post) a2 += row[2];
-            if (j + 3 < n_post) a3 += row[3];
+#pragma unroll 4
+        for (int t = 0; t < cnt; ++t) {
+            const int row = __shfl_sync(0xffffffffu, my_row, t);
+            if (in) {
+                const float* w = q.w + (int64_t)row * n_post + j;
+                a0 += w[0];
+                if (j + 1 < n_post) a1 += w[1];
+                if (j + 2 < n_post) a2 += w[2];
+                if (j + 3 < n_post) a3 += w[3];
+            }
         }
-        const float sc = q.scale;
-        atomicAdd(q.g + j, sc * a0);
-        if (j + 1 < n_post) atomicAdd(q.g + j + 1, sc * a1);
-        if (j + 2 < n_post) atomicAdd(q.g + j + 2, sc * a2);
-        if (j + 3 < n_post) atomicAdd(q.g + j + 3, sc * a3);
+        if (in) {
+            atomicAdd(q.g + j, sc * a0);
+            if (j + 1 < n_post) atomicAdd(q.g + j + 1, sc * a1);
+            if (j + 2 < n_post) atomicAdd(q.g + j + 2, sc * a2);
+            if (j + 3 < n_post) atomicAdd(q.g + j + 3, sc * a3);
+        }
     }
 }
 
