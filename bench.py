@@ -68,6 +68,11 @@ def _args():
     ap.add_argument("--no-gscale", action="store_true", help="skip the gScale sweep and fit")
     ap.add_argument("--no-scale-point", action="store_true",
                     help="skip the forced-activity propagation measurement at 100 x 1,000,000, p = 0.5")
+    ap.add_argument("--profile", choices=["cluster", "tiled", "dense", "neuron", "graded"],
+                    help="run a few launches of one kernel on its workload and exit (a target for ncu)")
+    ap.add_argument("--record-traffic", nargs=3, metavar=("KERNEL", "BYTES", "COMMAND"),
+                    help="store an ncu DRAM byte count per launch of KERNEL (with a hash of its sources) in "
+                         "profiles/traffic.json and exit")
     return ap.parse_args()
 
 
@@ -491,7 +496,7 @@ def run_ours(a):
         flops = PERSIST * n_hh * flops_per_neuron_step
         ach = flops / (t_persist * 1e-3) / 1e12
         roof = {"kernel": kname, "bound": "alu", "achieved": ach, "peak": fp32_peak,
-                "unit": "TFLOP/s", "frac": ach / fp32_peak, "traffic": None,
+                "unit": "TFLOP/s", "frac": ach / fp32_peak, "traffic": _traffic(kname),
                 "peak_source": "FP32 FMA peak from 152 SMs x 128 lanes x 2 x max SM clock "
                                f"({sm_mhz:.0f} MHz, {src})",
                 "launch_us": 1e3 * t_persist, "steps_per_launch": PERSIST, "flops_per_launch": flops,
@@ -522,6 +527,8 @@ def run_ours(a):
         for layout in ("csr", "dense"):
             r = _forced_propagation(snn, torch, dev, 1_000_000, 0.5, layout, flush=flush)
             r["frac_hbm"] = r["gbs"] / hbm
+            r["kernel"] = "k_propagate_tiled" if layout == "csr" else "k_propagate"
+            r["traffic"] = _traffic(r["kernel"])
             scale.append(r)
 
     # ---- end to end through the public API from pinned host buffers ----
@@ -638,9 +645,102 @@ def _e2e(a, spec, dev, torch, snn):
                     "network creation, 10,000 time steps, D2H of counters"}
 
 
+def run_profile(a):
+    """A few launches of one kernel on its workload, nothing timed: the
+    command the ncu summaries under profiles/ were captured from.
+      cluster: the four-population network, cluster engine, 1000 steps per launch;
+      tiled:   forced-activity propagation, 100 rows x 1,000,000 posts, p = 0.5, CSR;
+      dense:   the same with dense rows;
+      neuron:  8,000,000 HH neurons, one neuron phase per launch;
+      graded:  the differentiable workload (20,000 middle neurons), 200 steps
+               recorded forward and the adjoint."""
+    import torch
+
+    import paper_1412_0595_gb300 as snn
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    if a.profile == "cluster":
+        net = snn.Network.from_spec(I.config_four_pop(steps=1), device=dev)
+        net.set_option("engine", 3)
+        net.set_option("persist_steps", 1000)
+        for _ in range(3):
+            net.launch_phase(4)
+    elif a.profile in ("tiled", "dense"):
+        flush = _flush_buffers(torch, dev)
+        _forced_propagation(snn, torch, dev, 1_000_000, 0.5, "csr" if a.profile == "tiled" else a.profile, reps=3,
+                            flush=flush)
+        return
+    elif a.profile == "neuron":
+        net = snn.Network.from_spec(I.net([I.hh_pop(8_000_000)], [], dt=0.1, steps=1), device=dev)
+        net.set_option("engine", 0)
+        for _ in range(4):
+            net.launch_phase(0)
+    else:
+        spec = I.config_graded(steps=200)
+        net = snn.GradedNetwork.from_spec(spec, device=dev)
+        target = torch.from_numpy(I.target_trace(spec, 200, spec["pops"][-1]["n"])).to(dev)
+        net.forward_record(target, checkpoint_every=100)
+        net.backward()
+    torch.cuda.synchronize()
+    net.sync()
+    net.close()
+
+
+_KERNEL_SOURCES = {
+    "k_step_cluster": ["cluster.cu", "neuron_update.cuh", "device_math.cuh", "compaction.cuh", "snn_internal.cuh"],
+    "k_neuron_step": ["neuron.cu", "neuron_update.cuh", "device_math.cuh", "compaction.cuh", "snn_internal.cuh"],
+    "k_propagate_tiled": ["propagate_tiled.cu", "snn_internal.cuh"],
+    "k_propagate": ["propagate.cu", "snn_internal.cuh"],
+}
+
+
+def _sources_sha256(rels):
+    import hashlib
+    h = hashlib.sha256()
+    for rel in rels:
+        with open(os.path.join(ROOT, rel), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()
+
+
+def record_traffic(kernel, nbytes, command):
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    try:
+        with open(path) as f:
+            table = json.load(f)
+    except (OSError, ValueError):
+        table = {}
+    rels = ["paper_1412_0595_gb300/csrc/" + x for x in _KERNEL_SOURCES[kernel]]
+    table[kernel] = {"bytes_per_launch": float(nbytes), "command": command, "sources": rels,
+                     "sources_sha256": _sources_sha256(rels)}
+    with open(path, "w") as f:
+        json.dump(table, f, indent=1, sort_keys=True)
+        f.write("\n")
+
+
+def _traffic(kernel):
+    """DRAM bytes per launch of `kernel` from the committed ncu table
+    (profiles/traffic.json), or None when the kernel's sources changed since
+    the counters were taken (the table stores a hash of them)."""
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    try:
+        with open(path) as f:
+            table = json.load(f)
+    except (OSError, ValueError):
+        return None
+    row = table.get(kernel)
+    if not row:
+        return None
+    return row["bytes_per_launch"] if _sources_sha256(row["sources"]) == row["sources_sha256"] else None
+
+
 def main():
     a = _args()
-    if a.sweep:
+    if a.record_traffic:
+        record_traffic(*a.record_traffic)
+    elif a.profile:
+        run_profile(a)
+    elif a.sweep:
         run_sweep(a)
     elif a.impl == "reference":
         run_reference(a)
