@@ -66,6 +66,8 @@ def _args():
     ap.add_argument("--batch-steps", type=int, default=5000)
     ap.add_argument("--no-graded", action="store_true", help="skip the differentiable-form measurement")
     ap.add_argument("--no-gscale", action="store_true", help="skip the gScale sweep and fit")
+    ap.add_argument("--no-occupancy", action="store_true",
+                    help="skip the occupancy-rule baseline (the paper's block sizing) beside the autotuned run")
     ap.add_argument("--no-scale-point", action="store_true",
                     help="skip the forced-activity propagation measurement at 100 x 1,000,000, p = 0.5")
     ap.add_argument("--profile", choices=["cluster", "tiled", "dense", "neuron", "graded"],
@@ -531,6 +533,11 @@ def run_ours(a):
             r["traffic"] = _traffic(r["kernel"])
             scale.append(r)
 
+    # ---- the paper's occupancy rule as a baseline to the autotuner ----
+    occupancy = None
+    if not a.no_occupancy and rank == 0:
+        occupancy = _occupancy_baseline(snn, torch, dev, spec, a.sim_steps, value, flush)
+
     # ---- end to end through the public API from pinned host buffers ----
     e2e = None
     if not a.no_e2e:
@@ -568,6 +575,7 @@ def run_ours(a):
                 "e2e": e2e,
                 "engine": engine,
                 "autotune": tune,
+                "occupancy_baseline": occupancy,
                 "batched": batched,
                 "differentiable": differentiable,
                 "gscale_fit": gscale_fit,
@@ -578,6 +586,32 @@ def run_ours(a):
     net.close()
     if world > 1:
         dist.destroy_process_group()
+
+
+def _occupancy_baseline(snn, torch, dev, spec, sim_steps, tuned_value, flush):
+    """The same workload under the configuration the paper's occupancy rule
+    gives (Sec. 3: plain two-kernel step, grids filled to the resident-block
+    limit), timed like the headline run; the autotuned/occupancy ratio is the
+    autotuner's gain."""
+    net = snn.Network.from_spec(spec, device=dev)
+    cfg = net.occupancy_config(trial_steps=500)
+    stream = torch.cuda.current_stream()
+    ms = []
+    for k in range(4):
+        net.reset()
+        _flush_l2(flush)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        net.step(sim_steps)
+        e1.record(stream)
+        e1.synchronize()
+        if k:
+            ms.append(e0.elapsed_time(e1))
+    ev = net.synaptic_events()
+    net.close()
+    value = ev / (statistics.median(ms) * 1e-3)
+    return {"config": cfg, "ms_per_run": statistics.median(ms), "value": value, "unit": "synaptic events/s",
+            "autotuned_over_occupancy": tuned_value / value}
 
 
 def _e2e(a, spec, dev, torch, snn):

@@ -377,6 +377,16 @@ typedef struct snn_tuning {
  * occupancy-based (Sec. 3); this replaces it with measurement. */
 snn_status snn_autotune(snn_net* net, int32_t trial_steps, snn_tuning* result, void* stream);
 
+/* Applies the configuration of the paper's occupancy rule (Sec. 3: the block
+ * and grid sizes follow from the resident warps per SM, not from a
+ * measurement): the plain two-kernel step, propagation grid = SMs x resident
+ * row-kernel CTAs per SM, row chunk 1024, no post tiling.  It times that
+ * configuration with the same trial procedure as snn_autotune (state restored
+ * afterwards) and reports it in `result` (may be NULL; `cached` is 0), so the
+ * tuned-versus-occupancy speed-up can be read off.  SNN_ERR_STATE for a
+ * graded network.  Synchronises `stream`. */
+snn_status snn_occupancy_config(snn_net* net, int32_t trial_steps, snn_tuning* result, void* stream);
+
 /* Message of the last failed call on this thread ("" if none). */
 const char* snn_last_error(void);
 

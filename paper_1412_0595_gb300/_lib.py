@@ -103,6 +103,7 @@ def _load():
         "snn_save_state": [vp, vp, sz, i32, vp],
         "snn_load_state": [vp, vp, sz, i32, vp],
         "snn_autotune": [vp, i32, P(Tuning), vp],
+        "snn_occupancy_config": [vp, i32, P(Tuning), vp],
     }
     for name, args in sig.items():
         f = getattr(L, name)

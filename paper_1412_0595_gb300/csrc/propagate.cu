@@ -136,6 +136,10 @@ __global__ void __launch_bounds__(kPropThreads) k_propagate(const PropArgs a) {
     }
 }
 
+cudaError_t propagate_occupancy(int* per_sm) {
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, k_propagate, kPropThreads, 0);
+}
+
 cudaError_t launch_propagate(const PropArgs& a, int blocks, cudaStream_t s) {
     if (a.n_projs == 0 || a.num_tiles == 0) return cudaSuccess;
     const size_t smem = sizeof(int64_t) * (size_t)(a.n_projs + 1);

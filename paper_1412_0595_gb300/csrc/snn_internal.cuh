@@ -332,6 +332,7 @@ cudaError_t launch_csr_fill(uint64_t seed, uint32_t tag, int64_t n_pre, int64_t 
 cudaError_t launch_count_events(const DevProj* projs, int n_projs, unsigned long long* out, cudaStream_t s);
 cudaError_t launch_row_splits(const int64_t* row_ptr, const int32_t* col, int32_t n_pre, int32_t n_tiles, int32_t P,
                               int64_t* split, cudaStream_t s);
+cudaError_t propagate_occupancy(int* per_sm);   // resident row-kernel CTAs per SM (no dynamic smem)
 cudaError_t launch_propagate_tiled(const DevProj* q, int32_t P, const unsigned long long* ticket, int32_t num_tiles,
                                    int sm_count, uint32_t* error, uint32_t spin_limit, cudaStream_t s);
 constexpr int32_t kPostTile = 2048;          // posts per tile of the post-tiled propagation (8 KiB)

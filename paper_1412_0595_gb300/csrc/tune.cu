@@ -8,7 +8,7 @@
 // floating-point atomic adds.
 //
 // The autotuner times candidate launch configurations -- engine (plain /
-// persistent), propagation CTAs, compressed-row chunk, post-tiled rows -- on
+// persistent / cluster), propagation CTAs, compressed-row chunk, post-tiled rows -- on
 // short trial runs from a snapshot of the live network, keeps the fastest,
 // and restores the snapshot, so tuning never changes the trajectory.  Results
 // are cached per device and network shape for the life of the process.
@@ -129,6 +129,76 @@ std::string shape_key(snn_net* net) {
     return k;
 }
 
+// Times one configuration on `trial_steps` steps from the snapshot `snap`
+// (a warm-up run first, both from the same state); leaves the state at the
+// end of the trial.
+snn_status trial(snn_net* net, Choice& c, int32_t trial_steps, void* snap, size_t nb, cudaEvent_t e0, cudaEvent_t e1,
+                 void* stream) {
+    cudaStream_t s = (cudaStream_t)stream;
+    snn_status st;
+    if ((st = snn_set_option(net, SNN_OPT_ENGINE, c.engine)) != SNN_OK) return st;
+    if ((st = snn_set_option(net, SNN_OPT_PROP_BLOCKS, c.prop_blocks)) != SNN_OK) return st;
+    if ((st = snn_set_option(net, SNN_OPT_CHUNK, c.chunk)) != SNN_OK) return st;
+    if ((st = snn_set_option(net, SNN_OPT_TILED, c.tiled)) != SNN_OK) return st;
+    if ((st = snn_load_state(net, snap, nb, 1, stream)) != SNN_OK) return st;
+    if ((st = snn_step(net, std::min<int64_t>(trial_steps, net->graph_steps), stream)) != SNN_OK) return st;  // warm
+    if ((st = snn_load_state(net, snap, nb, 1, stream)) != SNN_OK) return st;
+    cudaEventRecord(e0, s);
+    if ((st = snn_step(net, trial_steps, stream)) != SNN_OK) return st;
+    cudaEventRecord(e1, s);
+    if ((st = snn_sync(net, stream)) != SNN_OK) return st;
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    c.us_per_step = 1e3 * ms / trial_steps;
+    return SNN_OK;
+}
+
+// Times the candidates from a snapshot of the live network, restores it, and
+// returns the fastest in *best (options restored on failure).
+snn_status time_candidates(snn_net* net, std::vector<Choice>& cands, int32_t trial_steps, Choice* best,
+                           void* stream) {
+    const size_t nb = snapshot_bytes(net);
+    void* snap = net->mem.get(nb);
+    if (!snap) return fail(SNN_ERR_OOM, "tuning snapshot");
+    snn_status st = snn_save_state(net, snap, nb, 1, stream);
+    const int32_t engine0 = net->engine, blocks0 = net->prop_blocks, chunk0 = net->chunk, tiled0 = net->tiled;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (st == SNN_OK && (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess))
+        st = fail(SNN_ERR_CUDA, "create events");
+    best->us_per_step = 1e30;
+    for (Choice& c : cands) {
+        if (st != SNN_OK) break;
+        if ((st = trial(net, c, trial_steps, snap, nb, e0, e1, stream)) != SNN_OK) break;
+        if (c.us_per_step < best->us_per_step) *best = c;
+    }
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    const snn_status rs = snn_load_state(net, snap, nb, 1, stream);
+    net->mem.put(snap);
+    if (st != SNN_OK) {
+        net->engine = engine0; net->prop_blocks = blocks0; net->chunk = chunk0; net->tiled = tiled0;
+        return st;
+    }
+    return rs;
+}
+
+snn_status apply(snn_net* net, const Choice& c, bool cached, snn_tuning* result) {
+    snn_status st = snn_set_option(net, SNN_OPT_ENGINE, c.engine);
+    if (st == SNN_OK) st = snn_set_option(net, SNN_OPT_PROP_BLOCKS, c.prop_blocks);
+    if (st == SNN_OK) st = snn_set_option(net, SNN_OPT_CHUNK, c.chunk);
+    if (st == SNN_OK) st = snn_set_option(net, SNN_OPT_TILED, c.tiled);
+    if (st != SNN_OK) return st;
+    if (result) {
+        result->engine = c.engine;
+        result->prop_blocks = c.prop_blocks;
+        result->chunk = c.chunk;
+        result->tiled = c.tiled;
+        result->us_per_step = c.us_per_step;
+        result->cached = cached ? 1 : 0;
+    }
+    return SNN_OK;
+}
+
 }  // namespace
 
 extern "C" {
@@ -153,7 +223,6 @@ snn_status snn_load_state(snn_net* net, const void* src, size_t bytes, int32_t s
 
 snn_status snn_autotune(snn_net* net, int32_t trial_steps, snn_tuning* result, void* stream) {
     if (!net || trial_steps < 1) return fail(SNN_ERR_INVALID_ARG, "bad network or trial length");
-    cudaStream_t s = (cudaStream_t)stream;
     const std::string key = shape_key(net) + "|" + std::to_string(trial_steps);
     Choice best{};
     bool cached = false;
@@ -173,60 +242,27 @@ snn_status snn_autotune(snn_net* net, int32_t trial_steps, snn_tuning* result, v
                 for (int tiled : {0, 2}) cands.push_back({0, blocks, chunk, tiled, 0.0});
         if (net->persist_grid > 0) cands.push_back({1, 4 * sm, 1024, 2, 0.0});
         if (net->cluster_size > 0) cands.push_back({3, 4 * sm, 1024, 2, 0.0});
-        // snapshot of the live network, restored after every trial
-        const size_t nb = snapshot_bytes(net);
-        void* snap = net->mem.get(nb);
-        if (!snap) return fail(SNN_ERR_OOM, "autotune snapshot");
-        snn_status st = snn_save_state(net, snap, nb, 1, stream);
-        const int32_t engine0 = net->engine, blocks0 = net->prop_blocks, chunk0 = net->chunk, tiled0 = net->tiled;
-        cudaEvent_t e0 = nullptr, e1 = nullptr;
-        if (st == SNN_OK && (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess))
-            st = fail(SNN_ERR_CUDA, "create events");
-        best.us_per_step = 1e30;
-        for (Choice& c : cands) {
-            if (st != SNN_OK) break;
-            if ((st = snn_set_option(net, SNN_OPT_ENGINE, c.engine)) != SNN_OK) break;
-            if ((st = snn_set_option(net, SNN_OPT_PROP_BLOCKS, c.prop_blocks)) != SNN_OK) break;
-            if ((st = snn_set_option(net, SNN_OPT_CHUNK, c.chunk)) != SNN_OK) break;
-            if ((st = snn_set_option(net, SNN_OPT_TILED, c.tiled)) != SNN_OK) break;
-            if ((st = snn_load_state(net, snap, nb, 1, stream)) != SNN_OK) break;
-            if ((st = snn_step(net, std::min<int64_t>(trial_steps, net->graph_steps), stream)) != SNN_OK) break;  // warm
-            if ((st = snn_load_state(net, snap, nb, 1, stream)) != SNN_OK) break;
-            cudaEventRecord(e0, s);
-            if ((st = snn_step(net, trial_steps, stream)) != SNN_OK) break;
-            cudaEventRecord(e1, s);
-            if ((st = snn_sync(net, stream)) != SNN_OK) break;
-            float ms = 0.f;
-            cudaEventElapsedTime(&ms, e0, e1);
-            c.us_per_step = 1e3 * ms / trial_steps;
-            if (c.us_per_step < best.us_per_step) best = c;
-        }
-        if (e0) cudaEventDestroy(e0);
-        if (e1) cudaEventDestroy(e1);
-        const snn_status rs = snn_load_state(net, snap, nb, 1, stream);
-        net->mem.put(snap);
-        if (st != SNN_OK) {
-            net->engine = engine0; net->prop_blocks = blocks0; net->chunk = chunk0; net->tiled = tiled0;
-            return st;
-        }
-        if (rs != SNN_OK) return rs;
+        const snn_status st = time_candidates(net, cands, trial_steps, &best, stream);
+        if (st != SNN_OK) return st;
         std::lock_guard<std::mutex> lock(g_cache_mu);
         g_cache[key] = best;
     }
-    snn_status st = snn_set_option(net, SNN_OPT_ENGINE, best.engine);
-    if (st == SNN_OK) st = snn_set_option(net, SNN_OPT_PROP_BLOCKS, best.prop_blocks);
-    if (st == SNN_OK) st = snn_set_option(net, SNN_OPT_CHUNK, best.chunk);
-    if (st == SNN_OK) st = snn_set_option(net, SNN_OPT_TILED, best.tiled);
+    return apply(net, best, cached, result);
+}
+
+snn_status snn_occupancy_config(snn_net* net, int32_t trial_steps, snn_tuning* result, void* stream) {
+    if (!net || trial_steps < 1) return fail(SNN_ERR_INVALID_ARG, "bad network or trial length");
+    if (net->graded) return fail(SNN_ERR_STATE, "graded networks have no launch options");
+    // Sec. 3's rule: the two-kernel step with each kernel's grid filled to its
+    // occupancy limit (resident blocks per SM x SMs); no measurement involved.
+    int per_sm = 0;
+    const cudaError_t e = propagate_occupancy(&per_sm);
+    if (e != cudaSuccess) return cuda_fail(e, "propagation occupancy");
+    std::vector<Choice> one{{0, std::max(1, per_sm) * net->sm_count, 1024, 0, 0.0}};
+    Choice c{};
+    const snn_status st = time_candidates(net, one, trial_steps, &c, stream);
     if (st != SNN_OK) return st;
-    if (result) {
-        result->engine = best.engine;
-        result->prop_blocks = best.prop_blocks;
-        result->chunk = best.chunk;
-        result->tiled = best.tiled;
-        result->us_per_step = best.us_per_step;
-        result->cached = cached ? 1 : 0;
-    }
-    return SNN_OK;
+    return apply(net, c, false, result);
 }
 
 }  // extern "C"

@@ -363,11 +363,21 @@ class Network:
             b = buf.contiguous()
             check(L.lib.snn_load_state(self.h, b.data_ptr(), b.numel(), 0, _stream(stream)))
 
+    @staticmethod
+    def _tuning(r):
+        return {"engine": {0: "plain", 1: "persistent", 3: "cluster"}[r.engine], "prop_blocks": r.prop_blocks,
+                "chunk": r.chunk, "tiled": r.tiled, "us_per_step": r.us_per_step, "cached": bool(r.cached)}
+
     def autotune(self, trial_steps=200, stream=None):
         r = L.Tuning()
         check(L.lib.snn_autotune(self.h, int(trial_steps), C.byref(r), _stream(stream)))
-        return {"engine": {0: "plain", 1: "persistent", 3: "cluster"}[r.engine], "prop_blocks": r.prop_blocks,
-                "chunk": r.chunk, "tiled": r.tiled, "us_per_step": r.us_per_step, "cached": bool(r.cached)}
+        return self._tuning(r)
+
+    def occupancy_config(self, trial_steps=200, stream=None):
+        """The paper's occupancy-based configuration (Sec. 3), applied and timed."""
+        r = L.Tuning()
+        check(L.lib.snn_occupancy_config(self.h, int(trial_steps), C.byref(r), _stream(stream)))
+        return self._tuning(r)
 
     # ------------------------------------------------------------------ checks
     def debug_propagate(self, q, spk, stream=None):

@@ -110,3 +110,23 @@ def test_autotune_picks_a_configuration_and_keeps_the_trajectory(gpu):
         assert a.counters(p) == b.counters(p)
     c = gpu.Network.from_spec(spec)
     assert c.autotune(trial_steps=100)["cached"]
+
+
+def test_occupancy_configuration_is_the_plain_step_and_keeps_the_trajectory(gpu):
+    # the paper's occupancy rule (Sec. 3) as a baseline beside the autotuner
+    spec = I.config_four_pop(steps=300, n_mid=3000)
+    a = gpu.Network.from_spec(spec)
+    b = gpu.Network.from_spec(spec)
+    a.step(50)
+    b.step(50)
+    r = a.occupancy_config(trial_steps=100)
+    assert r["engine"] == "plain" and r["tiled"] == 0 and r["chunk"] == 1024 and not r["cached"]
+    assert r["prop_blocks"] % 152 == 0 and r["us_per_step"] > 0
+    assert a.engine == "plain" and a.t == 50
+    a.step(200)
+    b.step(200)
+    for p in range(4):
+        assert np.abs(a.read_host(p, "V") - b.read_host(p, "V")).max() < 1e-4
+        assert a.counters(p) == b.counters(p)
+    with pytest.raises(Exception):
+        gpu.GradedNetwork.from_spec(I.config_graded_small(steps=10)).occupancy_config()
