@@ -93,7 +93,7 @@ enum {
     SNN_OPT_TILED = 7          /* compressed-row propagation of the plain engine: 0 one warp per
                                   row chunk with global atomics, 1 post-tiled through shared
                                   memory, 2 choose (default: post-tiled when a row has
-                                  >= 1024 synapses per 8192-post tile, over > 16384 posts) */
+                                  >= 256 synapses per 2048-post tile, over >= 16384 posts) */
 };
 
 /* A population.  kind SNN_POP_HH: Traub-Miles HH neurons with the given

@@ -29,6 +29,7 @@ _SOURCES = [_HERE / "snn_oracle.c", _HERE / "snn_oracle_graded.c"]
 
 POP_HH = 0
 POP_SOURCE = 1
+POP_IZH = 2
 
 FIELD = {"V": 0, "m": 1, "h": 2, "n": 3, "g0": 4, "g1": 5, "iext": 6, "isyn": 7}
 
@@ -57,6 +58,7 @@ class OraclePop(C.Structure):
         ("v_thresh", C.c_double), ("src_rate_hz", C.c_double),
         ("drive_rate_hz", C.c_double), ("drive_amp", C.c_double), ("drive_tau", C.c_double),
         ("v0", C.POINTER(C.c_double)),
+        ("izh", C.c_double * 8), ("noise_sigma", C.c_double), ("bias", C.c_double),
     ]
 
 
@@ -117,6 +119,10 @@ def lib():
         L.oracle_source_spike.argtypes = [C.c_uint64, C.c_uint32, C.c_uint32, C.c_uint32,
                                           C.c_double, C.c_double]
         L.oracle_source_spike.restype = C.c_int
+        L.oracle_izh_r.argtypes = [C.c_uint64, C.c_uint32, C.c_uint32]
+        L.oracle_izh_r.restype = C.c_double
+        L.oracle_izh_noise.argtypes = [C.c_uint64, C.c_uint32, C.c_uint32, C.c_uint32]
+        L.oracle_izh_noise.restype = C.c_double
         if hasattr(L, "oracle_graded_create"):
             _bind_graded(L)
     return _lib
@@ -194,6 +200,16 @@ def source_spike(seed, tag, t, i, rate_hz, dt):
     return int(lib().oracle_source_spike(seed, tag, t, i, rate_hz, dt))
 
 
+def izh_r(seed, tag, i):
+    """Per-neuron parameter draw r of an Izhikevich population."""
+    return float(lib().oracle_izh_r(seed, tag, i))
+
+
+def izh_noise(seed, tag, t, i):
+    """Irwin-Hall input noise z of neuron i at step t."""
+    return float(lib().oracle_izh_noise(seed, tag, t, i))
+
+
 # --------------------------------------------------------------------------
 # Network
 # --------------------------------------------------------------------------
@@ -213,7 +229,7 @@ class OracleNet:
         P = (OraclePop * len(pops))()
         for k, d in enumerate(pops):
             p = P[k]
-            p.kind = POP_SOURCE if d["kind"] == "source" else POP_HH
+            p.kind = {"source": POP_SOURCE, "hh": POP_HH, "izh": POP_IZH}[d["kind"]]
             p.n = d["n"]
             hh = d.get("hh") or {}
             for f in ("C", "gNa", "ENa", "gK", "EK", "gL", "EL"):
@@ -228,6 +244,12 @@ class OracleNet:
             p.drive_rate_hz = float(drv.get("rate_hz", 0.0))
             p.drive_amp = float(drv.get("amp", 0.0))
             p.drive_tau = float(drv.get("tau", 0.0))
+            izh = d.get("izh")
+            if izh is not None:
+                for j, f in enumerate(("a0", "a1", "b0", "b1", "c0", "c2", "d0", "d2")):
+                    p.izh[j] = float(izh[f])
+                p.noise_sigma = float(izh.get("noise", 0.0))
+                p.bias = float(izh.get("bias", 0.0))
             v0 = d.get("v0")
             if v0 is not None:
                 v0 = np.ascontiguousarray(v0, dtype=np.float64)

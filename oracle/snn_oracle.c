@@ -64,7 +64,7 @@ void oracle_philox4x32_10(const uint32_t ctr_in[4], const uint32_t key_in[2], ui
 }
 
 /* Stream identifiers carried in counter word 3. */
-enum { STREAM_SOURCE = 1, STREAM_DRIVE = 2, STREAM_CSR = 3 };
+enum { STREAM_SOURCE = 1, STREAM_DRIVE = 2, STREAM_CSR = 3, STREAM_IZH_PARAM = 5, STREAM_IZH_NOISE = 6 };
 
 /* One 32-bit draw: key = seed, counter = (a, b, tag, stream), word `word`. */
 static uint32_t draw_u32(uint64_t seed, uint32_t a, uint32_t b, uint32_t tag,
@@ -75,6 +75,32 @@ static uint32_t draw_u32(uint64_t seed, uint32_t a, uint32_t b, uint32_t tag,
     uint32_t out[4];
     oracle_philox4x32_10(ctr, key, out);
     return out[word];
+}
+
+/* Per-neuron parameter draw r of an Izhikevich population: the top 24 bits
+ * of word 0 of Philox(counter = (i, 0, tag, STREAM_IZH_PARAM)) times 2^-24,
+ * uniform on [0, 1) and exact in FP32 and FP64. */
+double oracle_izh_r(uint64_t seed, uint32_t tag, uint32_t i)
+{
+    return (double)(draw_u32(seed, i, 0, tag, STREAM_IZH_PARAM, 0) >> 8) * 0x1p-24;
+}
+
+/* Approximately normal input noise of neuron i at step t (Irwin-Hall: the
+ * sum of 12 uniforms minus 6 has mean 0 and variance 1): the top 20 bits of
+ * the 12 words of Philox(counter = (i, t, tag, STREAM_IZH_NOISE + k)),
+ * k = 0, 1, 2, summed as integers S < 12 * 2^20, z = (S - 6 * 2^20) 2^-20.
+ * z is exact in FP32, so both sides draw identical values. */
+double oracle_izh_noise(uint64_t seed, uint32_t tag, uint32_t t, uint32_t i)
+{
+    int64_t S = 0;
+    for (uint32_t k = 0; k < 3; ++k) {
+        uint32_t ctr[4] = {i, t, tag, STREAM_IZH_NOISE + k};
+        uint32_t key[2] = {(uint32_t)(seed & 0xffffffffu), (uint32_t)(seed >> 32)};
+        uint32_t out[4];
+        oracle_philox4x32_10(ctr, key, out);
+        for (int w = 0; w < 4; ++w) S += out[w] >> 12;
+    }
+    return (double)(S - 6 * (1 << 20)) * 0x1p-20;
 }
 
 /* Integer Bernoulli threshold round(p * 2^32), clamped to [0, 2^32]; an
@@ -150,7 +176,7 @@ void oracle_hh_currents(const double p[7], double V, double m, double h, double 
 /* ------------------------------------------------------------------------ */
 /* Network description, mirrored by the Python shim.                         */
 /* ------------------------------------------------------------------------ */
-enum { POP_HH = 0, POP_SOURCE = 1 };
+enum { POP_HH = 0, POP_SOURCE = 1, POP_IZH = 2 };
 
 typedef struct {
     int32_t kind;             /* POP_HH or POP_SOURCE */
@@ -164,6 +190,14 @@ typedef struct {
     double drive_amp;         /* pA added per drive event */
     double drive_tau;         /* ms, decay of the drive current */
     const double* v0;         /* n initial potentials, or NULL for EL */
+    /* POP_IZH (the cortical neuron model of ref. [9] of the paper, Sec. 5.1):
+     * a = izh[0] + izh[1] r, b = izh[2] + izh[3] r, c = izh[4] + izh[5] r^2,
+     * d = izh[6] + izh[7] r^2 with one uniform r per neuron; input current
+     * bias + noise_sigma * z per step, z the Irwin-Hall normal of
+     * oracle_izh_noise, plus the synaptic current g0 + g1 (current pulses). */
+    double izh[8];
+    double noise_sigma;
+    double bias;
 } oracle_pop;
 
 typedef struct {
@@ -263,6 +297,12 @@ oracle_net* oracle_net_create(const oracle_pop* pops, int n_pops, const oracle_p
             double v = pops[p].v0 ? pops[p].v0[i] : pops[p].EL;
             P->V[i] = v;
             if (pops[p].kind == POP_HH) steady_gates(v, &P->m[i], &P->h[i], &P->n[i]);
+            if (pops[p].kind == POP_IZH) {
+                /* h holds the neuron's parameter draw r, m the recovery variable u = b v */
+                double r = oracle_izh_r(seed, P->tag, (uint32_t)i);
+                P->h[i] = r;
+                P->m[i] = (pops[p].izh[2] + pops[p].izh[3] * r) * v;
+            }
         }
     }
     for (int q = 0; q < n_projs; ++q) {
@@ -270,7 +310,7 @@ oracle_net* oracle_net_create(const oracle_pop* pops, int n_pops, const oracle_p
         const oracle_proj* d = &projs[q];
         Q->desc = *d;
         if (d->pre < 0 || d->pre >= n_pops || d->post < 0 || d->post >= n_pops ||
-            d->channel < 0 || d->channel > 1 || net->pops[d->post].desc.kind != POP_HH) {
+            d->channel < 0 || d->channel > 1 || net->pops[d->post].desc.kind == POP_SOURCE) {
             oracle_net_destroy(net); return NULL;
         }
         double gs;
@@ -336,7 +376,8 @@ static void hh_substep(const oracle_pop* d, double hs, double I_in,
     *V += hs * dV; *m += hs * dm; *h += hs * dh; *n += hs * dn;
 }
 
-/* One time step of dt, in this order:
+/* One time step of dt, in this order (Izhikevich populations: see the
+ * comment in their branch; their synaptic input is the current g0 + g1):
  *   1. Poisson sources draw their spikes;
  *   2. driven HH neurons draw a drive event and add drive_amp to I_ext;
  *   3. I_syn = sum_c g_c (E_c - V) from step-start state;
@@ -356,6 +397,35 @@ void oracle_net_step(oracle_net* net)
             for (int i = 0; i < d->n; ++i) {
                 uint32_t u = draw_u32(net->seed, (uint32_t)i, t, P->tag, STREAM_SOURCE, 0);
                 if ((uint64_t)u < P->thr_src) P->spk[P->nspk++] = i;
+            }
+            P->spike_count += P->nspk;
+            continue;
+        }
+        if (d->kind == POP_IZH) {
+            for (int i = 0; i < d->n; ++i) {
+                /* Ref. [9]: v' = 0.04 v^2 + 5 v + 140 - u + I, u' = a (b v - u);
+                 * v >= v_thresh (30 mV) fires and resets v <- c, u <- u + d.
+                 * v takes n_sub Euler substeps of dt / n_sub, then u one step
+                 * of dt with the new v, as in the model's published scheme. */
+                const double r = P->h[i];
+                const double a = d->izh[0] + d->izh[1] * r, b = d->izh[2] + d->izh[3] * r;
+                const double c = d->izh[4] + d->izh[5] * r * r, dd = d->izh[6] + d->izh[7] * r * r;
+                const double isyn = P->g[0][i] + P->g[1][i];
+                const double I = d->bias + d->noise_sigma * oracle_izh_noise(net->seed, P->tag, t, (uint32_t)i) + isyn;
+                P->isyn[i] = isyn;
+                double v = P->V[i], u = P->m[i];
+                for (int s = 0; s < net->n_sub; ++s) v += hs * (0.04 * v * v + 5.0 * v + 140.0 - u + I);
+                u += net->dt * a * (b * v - u);
+                if (v >= d->v_thresh) {
+                    P->spk[P->nspk++] = i;
+                    v = c;
+                    u += dd;
+                }
+                if (isnan(v)) P->nan_count++;
+                P->V[i] = v;
+                P->m[i] = u;
+                P->g[0][i] *= P->dec[0];
+                P->g[1][i] *= P->dec[1];
             }
             P->spike_count += P->nspk;
             continue;

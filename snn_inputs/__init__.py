@@ -45,6 +45,24 @@ def hh_pop(n, *, v0_range=(-62.0, -58.0), drive=None, E_syn=(E_EXC, E_INH), tau_
                 E_syn=tuple(E_syn), tau_syn=tuple(tau_syn), v_thresh=v_thresh)
 
 
+# Cortical neurons of the paper's first network (Sec. 5.1, ref. [9]): with one
+# uniform r per neuron, excitatory a = 0.02, b = 0.2, c = -65 + 15 r^2,
+# d = 8 - 6 r^2; inhibitory a = 0.02 + 0.08 r, b = 0.25 - 0.05 r, c = -65,
+# d = 2; thalamic input noise of standard deviation 5 (excitatory) / 2
+# (inhibitory) per 1 ms step; peak 30 mV.
+IZH_EXC = dict(a0=0.02, a1=0.0, b0=0.2, b1=0.0, c0=-65.0, c2=15.0, d0=8.0, d2=-6.0, noise=5.0, bias=0.0)
+IZH_INH = dict(a0=0.02, a1=0.08, b0=0.25, b1=-0.05, c0=-65.0, c2=0.0, d0=2.0, d2=0.0, noise=2.0, bias=0.0)
+
+
+def izh_pop(n, *, excitatory=True, v0=-65.0, **overrides):
+    """An Izhikevich population; synaptic input is a current pulse (the
+    channels clear every step), v starts at v0 and u at b v."""
+    izh = dict(IZH_EXC if excitatory else IZH_INH)
+    izh.update(overrides)
+    return dict(kind="izh", n=int(n), izh=izh, v0_range=(float(v0), float(v0)), E_syn=(0.0, 0.0),
+                tau_syn=(0.0, 0.0), v_thresh=30.0)
+
+
 def source_pop(n, rate_hz):
     return dict(kind="source", n=int(n), rate_hz=float(rate_hz))
 
@@ -165,9 +183,11 @@ def v0(spec, pop):
     """Initial membrane potentials of population `pop`: uniform in its
     v0_range, drawn in FP64 and rounded to FP32 (both sides read these bits)."""
     d = spec["pops"][pop]
-    if d["kind"] != "hh":
+    if d["kind"] not in ("hh", "izh"):
         return None
     lo, hi = d["v0_range"]
+    if lo == hi:
+        return np.full(d["n"], lo, np.float32)
     rng = np.random.default_rng([spec["seed"], _V0, spec["instance"], pop])
     return rng.uniform(lo, hi, d["n"]).astype(np.float32)
 
