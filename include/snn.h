@@ -48,7 +48,7 @@ typedef enum snn_status {
     SNN_ERR_SIZE = 8         /* a destination buffer is too small */
 } snn_status;
 
-enum { SNN_POP_HH = 0, SNN_POP_SOURCE = 1 };
+enum { SNN_POP_HH = 0, SNN_POP_SOURCE = 1, SNN_POP_IZH = 2 };
 enum { SNN_LAYOUT_CSR = 0, SNN_LAYOUT_DENSE = 1 };
 enum { SNN_SYN_EXP = 0, SNN_SYN_GRADED = 1 };
 
@@ -97,7 +97,17 @@ enum {
 };
 
 /* A population.  kind SNN_POP_HH: Traub-Miles HH neurons with the given
- * conductances; kind SNN_POP_SOURCE: Poisson spike sources at src_rate_hz. */
+ * conductances; kind SNN_POP_SOURCE: Poisson spike sources at src_rate_hz;
+ * kind SNN_POP_IZH: the cortical neurons of the paper's first network (Sec.
+ * 5.1, its ref. [9]): v' = 0.04 v^2 + 5 v + 140 - u + I, u' = a (b v - u),
+ * spike and reset v <- c, u <- u + d when v >= v_thresh; v takes n_substeps
+ * Euler substeps per dt, u one step of dt with the new v.  Per neuron one
+ * uniform r (drawn from the seed) gives a = izh[0] + izh[1] r,
+ * b = izh[2] + izh[3] r, c = izh[4] + izh[5] r^2, d = izh[6] + izh[7] r^2.
+ * I = bias + noise_sigma * z + g0 + g1: z is the per-step Irwin-Hall normal
+ * draw (12 uniforms of 20 bits from the seed, minus 6), and the synaptic
+ * input is the current g0 + g1 (E_syn unused; tau_syn 0 makes every event a
+ * one-step pulse).  u starts at b v0; v0 as for HH. */
 typedef struct snn_pop_desc {
     int32_t kind;
     int32_t n;                 /* neurons, 0 <= n < 2^30 */
@@ -112,6 +122,9 @@ typedef struct snn_pop_desc {
     const float* v0;           /* n initial potentials; NULL = EL.  Gating starts at steady state. */
     int32_t v0_on_device;      /* 1 if v0 is a device pointer */
     int32_t reserved;
+    double izh[8];             /* SNN_POP_IZH: a0, a1, b0, b1, c0, c2, d0, d2 (see above) */
+    double noise_sigma;        /* SNN_POP_IZH: standard deviation of the per-step input current */
+    double bias;               /* SNN_POP_IZH: constant input current */
 } snn_pop_desc;
 
 /* A projection from population `pre` to `post`.  Input connectivity is either

@@ -15,7 +15,7 @@ LIB_PATH = Path(__file__).resolve().parent / "_build" / "libsnn.so"
 SNN_OK = 0
 STATUS = {0: "SNN_OK", 1: "SNN_ERR_INVALID_ARG", 2: "SNN_ERR_CSR", 3: "SNN_ERR_GSCALE", 4: "SNN_ERR_OOM",
           5: "SNN_ERR_CUDA", 6: "SNN_ERR_TIMEOUT", 7: "SNN_ERR_STATE", 8: "SNN_ERR_SIZE"}
-POP_HH, POP_SOURCE = 0, 1
+POP_HH, POP_SOURCE, POP_IZH = 0, 1, 2
 LAYOUT_CSR, LAYOUT_DENSE = 0, 1
 SYN_EXP, SYN_GRADED = 0, 1
 FIELD = {"V": 0, "m": 1, "h": 2, "n": 3, "g0": 4, "g1": 5, "iext": 6, "isyn": 7, "spikes": 8, "nspk": 9,
@@ -33,6 +33,7 @@ class PopDesc(C.Structure):
         ("src_rate_hz", C.c_double), ("drive_rate_hz", C.c_double), ("drive_amp", C.c_double),
         ("drive_tau", C.c_double),
         ("v0", C.c_void_p), ("v0_on_device", C.c_int32), ("reserved", C.c_int32),
+        ("izh", C.c_double * 8), ("noise_sigma", C.c_double), ("bias", C.c_double),
     ]
 
 

@@ -93,7 +93,8 @@ bool finite_pos(double x) { return std::isfinite(x) && x > 0.0; }
 
 snn_status check_pop(const snn_pop_desc& d, int k) {
     const std::string at = "population " + std::to_string(k) + ": ";
-    if (d.kind != SNN_POP_HH && d.kind != SNN_POP_SOURCE) return fail(SNN_ERR_INVALID_ARG, at + "bad kind");
+    if (d.kind != SNN_POP_HH && d.kind != SNN_POP_SOURCE && d.kind != SNN_POP_IZH)
+        return fail(SNN_ERR_INVALID_ARG, at + "bad kind");
     if (d.n < 0 || d.n >= (1 << 30)) return fail(SNN_ERR_INVALID_ARG, at + "n out of range");
     if (d.kind == SNN_POP_HH) {
         if (!finite_pos(d.C)) return fail(SNN_ERR_INVALID_ARG, at + "C must be > 0");
@@ -103,6 +104,11 @@ snn_status check_pop(const snn_pop_desc& d, int k) {
             if (!std::isfinite(x)) return fail(SNN_ERR_INVALID_ARG, at + "non-finite parameter");
         if (d.drive_rate_hz < 0 || !std::isfinite(d.drive_rate_hz))
             return fail(SNN_ERR_INVALID_ARG, at + "drive rate must be >= 0");
+    } else if (d.kind == SNN_POP_IZH) {
+        for (double x : d.izh)
+            if (!std::isfinite(x)) return fail(SNN_ERR_INVALID_ARG, at + "non-finite Izhikevich parameter");
+        if (!std::isfinite(d.noise_sigma) || d.noise_sigma < 0 || !std::isfinite(d.bias) || !std::isfinite(d.v_thresh))
+            return fail(SNN_ERR_INVALID_ARG, at + "bad Izhikevich input or threshold");
     } else if (d.src_rate_hz < 0 || !std::isfinite(d.src_rate_hz)) {
         return fail(SNN_ERR_INVALID_ARG, at + "source rate must be >= 0");
     }
@@ -335,7 +341,9 @@ snn_status create_impl(const snn_pop_desc* pops, int32_t n_pops, const snn_proj_
         const std::string at = "projection " + std::to_string(q) + ": ";
         if (d.pre < 0 || d.pre >= n_pops || d.post < 0 || d.post >= n_pops)
             return fail(SNN_ERR_INVALID_ARG, at + "pre/post out of range");
-        if (pops[d.post].kind != SNN_POP_HH) return fail(SNN_ERR_INVALID_ARG, at + "post must be HH");
+        if (pops[d.post].kind == SNN_POP_SOURCE) return fail(SNN_ERR_INVALID_ARG, at + "post must not be a source");
+        if (d.synapse == SNN_SYN_GRADED && pops[d.post].kind != SNN_POP_HH)
+            return fail(SNN_ERR_INVALID_ARG, at + "graded synapses target HH populations");
         if (d.channel != 0 && d.channel != 1) return fail(SNN_ERR_INVALID_ARG, at + "channel must be 0 or 1");
         if (d.layout != SNN_LAYOUT_CSR && d.layout != SNN_LAYOUT_DENSE)
             return fail(SNN_ERR_INVALID_ARG, at + "bad layout");
@@ -422,7 +430,7 @@ snn_status create_impl(const snn_pop_desc* pops, int32_t n_pops, const snn_proj_
     for (int k = 0; k < n_pops; ++k) {
         const PopHost& P = net->pops[k];
         const snn_pop_desc& d = P.d;
-        if (d.kind == SNN_POP_HH) {
+        if (d.kind != SNN_POP_SOURCE) {
             if (d.v0 && !d.v0_on_device) std::memcpy(&v0[P.offset], d.v0, sizeof(float) * d.n);
             else std::fill(v0.begin() + P.offset, v0.begin() + P.offset + d.n, (float)d.EL);
         }
@@ -450,11 +458,15 @@ snn_status create_impl(const snn_pop_desc* pops, int32_t n_pops, const snn_proj_
         q.spike_count = net->counters + 2 * k;
         q.nan_count = net->counters + 2 * k + 1;
         q.neuron_spikes = net->nrn_count + P.offset;
+        for (int j = 0; j < 8; ++j) q.izh[j] = (float)d.izh[j];
+        q.noise = (float)d.noise_sigma;
+        q.bias = (float)d.bias;
+        q.dt = (float)dt;
     }
     CK(cudaMemcpyAsync(net->V, v0.data(), NT * sizeof(float), cudaMemcpyHostToDevice, s), "upload V0");
     for (int k = 0; k < n_pops; ++k) {
         const PopHost& P = net->pops[k];
-        if (P.d.kind == SNN_POP_HH && P.d.v0 && P.d.v0_on_device && P.d.n > 0)
+        if (P.d.kind != SNN_POP_SOURCE && P.d.v0 && P.d.v0_on_device && P.d.n > 0)
             CK(cudaMemcpyAsync(net->V + P.offset, P.d.v0, sizeof(float) * P.d.n, cudaMemcpyDeviceToDevice, s),
                "copy V0");
     }
@@ -463,7 +475,7 @@ snn_status create_impl(const snn_pop_desc* pops, int32_t n_pops, const snn_proj_
     CK(cudaMemcpyAsync(net->d_pops, dp.data(), dp.size() * sizeof(DevPop), cudaMemcpyHostToDevice, s),
        "upload population descriptors");
     CK(launch_init_state(net->d_pops, n_pops, net->tile_pop, net->num_tiles, net->V, net->m, net->h, net->n,
-                         net->g0, net->g1, net->iext, s),
+                         net->g0, net->g1, net->iext, seed, s),
        "initialise state");
 
     // ---- projections: copy, validate, measure ----

@@ -183,7 +183,7 @@ __global__ void __launch_bounds__(kCT, 1) k_step_cluster(const PersistArgs A, in
                 live[u] = true;
                 pop_of[u] = p - p_lo;
                 local_of[u] = local;
-                if (P.kind == SNN_POP_HH)
+                if (P.kind != SNN_POP_SOURCE)
                     st[u] = NeuronState{a.V[idx], a.m[idx], a.h[idx], a.n[idx], a.g0[idx], a.g1[idx], a.iext[idx]};
             }
         }
@@ -255,7 +255,7 @@ __global__ void __launch_bounds__(kCT, 1) k_step_cluster(const PersistArgs A, in
             bool spike = false;
             if (live[u]) {
                 const DevPop& P = s_pops[pop_of[u]];
-                if (P.kind == SNN_POP_HH) {
+                if (P.kind != SNN_POP_SOURCE) {
                     st[u].g0 += acc[off];
                     st[u].g1 += acc[per_cta + off];
                     acc[off] = 0.0f;
@@ -263,7 +263,7 @@ __global__ void __launch_bounds__(kCT, 1) k_step_cluster(const PersistArgs A, in
                 }
                 float isyn;
                 spike = neuron_step(P, key, t, local_of[u], a.hs, a.n_sub, st[u], &isyn);
-                if (P.kind == SNN_POP_HH) {
+                if (P.kind != SNN_POP_SOURCE) {
                     if (isnan(st[u].V)) atomicAdd(P.nan_count, 1ull);
                     if (a.isyn_rec) a.isyn_rec[idx] = isyn;
                 }
@@ -295,7 +295,7 @@ __global__ void __launch_bounds__(kCT, 1) k_step_cluster(const PersistArgs A, in
         if (!live[u]) continue;
         const DevPop& P = s_pops[pop_of[u]];
         if (n_spk[u]) P.neuron_spikes[local_of[u]] += n_spk[u];
-        if (P.kind != SNN_POP_HH) continue;
+        if (P.kind == SNN_POP_SOURCE) continue;
         const int off = threadIdx.x + u * kCT;
         const int idx = base + off;
         st[u].g0 += acc[off];

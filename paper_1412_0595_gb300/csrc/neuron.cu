@@ -54,11 +54,11 @@ __global__ void __launch_bounds__(kTile, 6) k_neuron_step(const NeuronArgs a) {
         bool spike = false, is_nan = false;
         if (active) {
             NeuronState s{};
-            if (P.kind == SNN_POP_HH)
+            if (P.kind != SNN_POP_SOURCE)
                 s = NeuronState{a.V[idx], a.m[idx], a.h[idx], a.n[idx], a.g0[idx], a.g1[idx], a.iext[idx]};
             float isyn;
             spike = neuron_step(P, key, t, local, a.hs, a.n_sub, s, &isyn);
-            if (P.kind == SNN_POP_HH) {
+            if (P.kind != SNN_POP_SOURCE) {
                 is_nan = isnan(s.V);
                 a.V[idx] = s.V; a.m[idx] = s.m; a.h[idx] = s.h; a.n[idx] = s.n;
                 a.g0[idx] = s.g0; a.g1[idx] = s.g1; a.iext[idx] = s.ie;
@@ -79,13 +79,17 @@ __global__ void __launch_bounds__(kTile, 6) k_neuron_step(const NeuronArgs a) {
 }
 
 __global__ void k_init_state(const DevPop* pops, const int32_t* tile_pop, float* V, float* m,
-                             float* h, float* n, float* g0, float* g1, float* iext) {
+                             float* h, float* n, float* g0, float* g1, float* iext, PhiloxKey key) {
     const int tile = blockIdx.x;
     const DevPop& P = pops[tile_pop[tile]];
     const int local = (tile - P.first_tile) * kTile + (int)threadIdx.x;
     const int idx = P.offset + local;
     float v = V[idx], mm = 0.f, hh = 0.f, nn = 0.f;
     if (local < P.n && P.kind == SNN_POP_HH) hh_steady(v, mm, hh, nn);
+    if (local < P.n && P.kind == SNN_POP_IZH) {
+        hh = izh_r(key, (uint32_t)local, P.tag);          // the neuron's parameter draw r
+        mm = fmaf(P.izh[3], hh, P.izh[2]) * v;             // u = b v
+    }
     m[idx] = mm;
     h[idx] = hh;
     n[idx] = nn;
@@ -122,9 +126,10 @@ cudaError_t launch_neuron_step(const NeuronArgs& a, cudaStream_t s) {
 
 cudaError_t launch_init_state(const DevPop* pops, int, const int32_t* tile_pop, int num_tiles,
                               float* V, float* m, float* h, float* n, float* g0, float* g1,
-                              float* iext, cudaStream_t s) {
+                              float* iext, uint64_t seed, cudaStream_t s) {
     if (num_tiles == 0) return cudaSuccess;
-    k_init_state<<<num_tiles, kTile, 0, s>>>(pops, tile_pop, V, m, h, n, g0, g1, iext);
+    k_init_state<<<num_tiles, kTile, 0, s>>>(pops, tile_pop, V, m, h, n, g0, g1, iext,
+                                             PhiloxKey{(uint32_t)seed, (uint32_t)(seed >> 32)});
     return cudaGetLastError();
 }
 

@@ -98,7 +98,7 @@ __global__ void __launch_bounds__(kTile, 6) k_step_persistent(const PersistArgs 
         const DevPop& P = a.pops[a.tile_pop[my_tile]];
         const int local = (my_tile - P.first_tile) * kTile + (int)threadIdx.x;
         const int idx = P.offset + local;
-        if (local < P.n && P.kind == SNN_POP_HH)
+        if (local < P.n && P.kind != SNN_POP_SOURCE)
             rs = NeuronState{a.V[idx], a.m[idx], a.h[idx], a.n[idx], a.g0[idx], a.g1[idx], a.iext[idx]};
     }
 
@@ -121,7 +121,7 @@ __global__ void __launch_bounds__(kTile, 6) k_step_persistent(const PersistArgs 
             bool spike = false, is_nan = false;
             if (active) {
                 NeuronState s{};
-                if (P.kind == SNN_POP_HH) {
+                if (P.kind != SNN_POP_SOURCE) {
                     if (kResident) s = rs;
                     else s = NeuronState{a.V[idx], a.m[idx], a.h[idx], a.n[idx], __ldcg(a.g0 + idx),
                                          __ldcg(a.g1 + idx), a.iext[idx]};
@@ -133,7 +133,7 @@ __global__ void __launch_bounds__(kTile, 6) k_step_persistent(const PersistArgs 
                 }
                 float isyn;
                 spike = neuron_step(P, key, t, local, a.hs, a.n_sub, s, &isyn);
-                if (P.kind == SNN_POP_HH) {
+                if (P.kind != SNN_POP_SOURCE) {
                     is_nan = isnan(s.V);
                     if (kResident) {
                         rs = s;
@@ -182,7 +182,7 @@ __global__ void __launch_bounds__(kTile, 6) k_step_persistent(const PersistArgs 
     for (int tile = blockIdx.x; tile < a.num_tiles; tile += gridDim.x) {
         const DevPop& P = a.pops[a.tile_pop[tile]];
         const int local = (tile - P.first_tile) * kTile + (int)threadIdx.x;
-        if (local >= P.n || P.kind != SNN_POP_HH) continue;
+        if (local >= P.n || P.kind == SNN_POP_SOURCE) continue;
         const int idx = P.offset + local;
         NeuronState s = rs;
         if (!kResident) s.g0 = __ldcg(a.g0 + idx), s.g1 = __ldcg(a.g1 + idx);

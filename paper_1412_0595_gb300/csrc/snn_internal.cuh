@@ -25,6 +25,8 @@ constexpr uint32_t kDevErrCsr = 2u;
 constexpr uint32_t kStreamSource = 1u;
 constexpr uint32_t kStreamDrive = 2u;
 constexpr uint32_t kStreamCsr = 3u;
+constexpr uint32_t kStreamIzhParam = 5u;        // per-neuron parameter draw r
+constexpr uint32_t kStreamIzhNoise = 6u;        // 6, 7, 8: the 12 words of the input noise
 
 
 struct DevPop {
@@ -48,6 +50,9 @@ struct DevPop {
     unsigned long long* nan_count;
     int32_t* neuron_spikes;        // per-neuron spike counts of this population
     float rel_thr, rel_inv_slope;  // graded release of this population's neurons
+    float izh[8];                  // Izhikevich: a0, a1, b0, b1, c0, c2, d0, d2
+    float noise, bias;             // Izhikevich input: bias + noise * z
+    float dt;                      // step length (ms), for u
 };
 
 struct DevProj {
@@ -307,7 +312,7 @@ snn_status cuda_fail(cudaError_t e, const char* what);
 cudaError_t launch_neuron_step(const NeuronArgs& a, cudaStream_t s);
 cudaError_t launch_init_state(const DevPop* pops, int n_pops_total, const int32_t* tile_pop,
                               int num_tiles, float* V, float* m, float* h, float* n, float* g0,
-                              float* g1, float* iext, cudaStream_t s);
+                              float* g1, float* iext, uint64_t seed, cudaStream_t s);
 cudaError_t launch_propagate(const PropArgs& a, int blocks, cudaStream_t s);
 int dense_rows_per_item();
 int dense_posts_per_item();

@@ -75,7 +75,7 @@ def _descs(pops, projs, device, keep):
     P = (L.PopDesc * len(pops))()
     for k, d in enumerate(pops):
         p = P[k]
-        p.kind = L.POP_SOURCE if d["kind"] == "source" else L.POP_HH
+        p.kind = {"source": L.POP_SOURCE, "hh": L.POP_HH, "izh": L.POP_IZH}[d["kind"]]
         p.n = int(d["n"])
         for f, v in (d.get("hh") or {}).items():
             setattr(p, f, float(v))
@@ -89,8 +89,14 @@ def _descs(pops, projs, device, keep):
         p.drive_rate_hz = float(drv.get("rate_hz", 0.0))
         p.drive_amp = float(drv.get("amp", 0.0))
         p.drive_tau = float(drv.get("tau", 0.0))
+        izh = d.get("izh")
+        if izh is not None:
+            for j, f in enumerate(("a0", "a1", "b0", "b1", "c0", "c2", "d0", "d2")):
+                p.izh[j] = float(izh[f])
+            p.noise_sigma = float(izh.get("noise", 0.0))
+            p.bias = float(izh.get("bias", 0.0))
         v0 = d.get("v0")
-        if v0 is not None and p.kind == L.POP_HH:
+        if v0 is not None and p.kind != L.POP_SOURCE:
             t = _dev(v0, torch.float32, device)
             assert t.numel() == p.n
             keep.append(t)

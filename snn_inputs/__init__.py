@@ -107,6 +107,26 @@ def config_four_pop(steps=10000, n_in=100, n_mid=10000, n_out=100, n_inh=20, p_m
                name=f"four_pop_in{n_in}_mid{n_mid}_out{n_out}_inh{n_inh}_p{p_mid}_{mid_layout}")
 
 
+def config_izhikevich(n_conn=1000, gscale=1.0, steps=1000, n=1000, layout=None, seed=SEED, instance=0):
+    """The paper's first network (Sec. 5.1): n cortical neurons, excitatory to
+    inhibitory 4 : 1, every neuron receiving nConn inputs on average (one
+    Bernoulli(nConn / n) draw per ordered pair, self-pairs included), weights
+    U(0, 0.5) from excitatory and U(-1, 0) from inhibitory neurons (the
+    synaptic input is a current), all scaled by gScale; dt = 1 ms, v in two
+    substeps of 0.5 ms, 1000 steps = 1 s."""
+    ne = n * 4 // 5
+    ni = n - ne
+    p = min(1.0, n_conn / n)
+    layout = layout or ("dense" if p >= 0.5 else "csr")
+    pops = [izh_pop(ne, excitatory=True), izh_pop(ni, excitatory=False)]
+    k = (0.0, 0.0, 1.0)
+    w_e, w_i = ("uniform", 0.0, 0.5), ("uniform", -1.0, 0.0)
+    projs = [proj(0, 0, layout, p, w_e, k=k, user_scale=gscale), proj(0, 1, layout, p, w_e, k=k, user_scale=gscale),
+             proj(1, 0, layout, p, w_i, k=k, user_scale=gscale), proj(1, 1, layout, p, w_i, k=k, user_scale=gscale)]
+    return net(pops, projs, dt=1.0, n_sub=2, steps=steps, seed=seed, instance=instance,
+               name=f"izhikevich_n{n}_nconn{n_conn}_gscale{gscale:.4g}")
+
+
 SWEEP_N_MID = (1_000, 10_000, 100_000, 1_000_000)
 SWEEP_P = (0.01, 0.05, 0.2, 0.5)
 
