@@ -308,6 +308,35 @@ def _gscale_procedure(dev, steps=5000):
             "nan_runs": int(sum(r["sum_nans"] > 0 for r in recs))}
 
 
+# Table 1 of the paper: the law fitted on its Izhikevich network
+TABLE1_IZHIKEVICH = (1.318e3, 1.099e2, -2.800e-1)
+
+
+def _gscale_procedure_izhikevich(dev, steps=1000):
+    """Fig. 1's procedure on the paper's cortical network (Table 1, Fig. 2):
+    nConn 100..1000 step 50 x gScale 2^(k/8), k = -8..32, reference (1000,
+    1.0), 1 s per run; the fitted law next to Table 1's at nConn 100, 500,
+    1000 (the paper's runs and raw numbers are not available; its constants
+    are context, not a target)."""
+    from paper_1412_0595_gb300 import gscale as G
+    import torch
+    n_conn = list(range(100, 1001, 50))
+    grid = [2.0 ** (k / 8.0) for k in range(-8, 33)]
+    specs, keys = G.izhikevich_sweep_specs(n_conn, grid, steps=steps)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    recs = G.run_sweep(specs, keys, device=dev)
+    t_run = time.perf_counter() - t0
+    x, y, target = G.select(recs, 1000.0, 1.0)
+    (k1, k2, k3), mape = G.fit(x, y)
+    at = {str(n): {"fit": G.law(n, k1, k2, k3), "table1": G.law(n, *TABLE1_IZHIKEVICH)} for n in (100, 500, 1000)}
+    return {"runs": len(recs), "neurons_per_run": 1000, "steps": steps, "seconds_incl_build": t_run,
+            "reference_avg_spike": target, "k1": k1, "k2": k2, "k3": k3, "mape_percent": mape,
+            "table1": dict(zip(("k1", "k2", "k3"), TABLE1_IZHIKEVICH)), "gscale_at": at,
+            "selected": {str(int(a)): float(b) for a, b in zip(x, y)},
+            "nan_runs": int(sum(r["sum_nans"] > 0 for r in recs))}
+
+
 def _cpu_baseline(sim_steps):
     """The FP64 oracle, as it stands, on a bounded sample (single thread)."""
     import oracle
@@ -549,9 +578,10 @@ def run_ours(a):
     differentiable = None
     if not a.no_graded and rank == 0:
         differentiable = _differentiable(snn, torch, dev)
-    gscale_fit = None
+    gscale_fit = gscale_izh = None
     if not a.no_gscale and rank == 0:
         gscale_fit = _gscale_procedure(dev)
+        gscale_izh = _gscale_procedure_izhikevich(dev)
 
     cpu = None
     if rank == 0 and world == 1 and not a.no_cpu_baseline:
@@ -579,6 +609,7 @@ def run_ours(a):
                 "batched": batched,
                 "differentiable": differentiable,
                 "gscale_fit": gscale_fit,
+                "gscale_fit_izhikevich": gscale_izh,
                 "gpu_launches": a.steps * ((-(-a.sim_steps // 1000)) + 2 if multi
                                            else 2 * a.sim_steps + 2),
                 "clocks": clk.summary()}

@@ -1,4 +1,5 @@
-"""The paper's conductance-scale procedure (Sec. 5.1, Fig. 1) on the batched GPU form.
+"""The paper's conductance-scale procedure (Sec. 5.1, Fig. 1) on the batched GPU form,
+for the HH network and for the Izhikevich cortical network (Table 1, Fig. 2).
 
 1. Sweep: one network instance per (nConn, gScale) pair, all run in one
    batched network object (every simulation step runs in the CUDA library).
@@ -42,9 +43,27 @@ def sweep_specs(n_conn_values, gscale_values, n_src=1000, n_hh=1000, rate_hz=20.
     return specs, keys
 
 
+def izhikevich_sweep_specs(n_conn_values, gscale_values, steps=1000, n=1000, seed=None):
+    """Instances of the sweep on the paper's cortical network (Sec. 5.1,
+    Table 1 / Fig. 2): n Izhikevich neurons, 4 : 1 excitatory : inhibitory,
+    nConn inputs per neuron, all weights times gScale."""
+    import snn_inputs as I
+    seed = I.SEED if seed is None else seed
+    specs, keys = [], []
+    b = 0
+    for nc in n_conn_values:
+        for gs in gscale_values:
+            specs.append(I.config_izhikevich(n_conn=nc, gscale=float(gs), steps=steps, n=n, seed=seed, instance=b))
+            keys.append((float(nc), float(gs)))
+            b += 1
+    return specs, keys
+
+
 def run_sweep(specs, keys, device=None, engine=None):
     """Runs every instance in one batched network; returns one record per run
-    with avgSpike (spikes per HH neuron over the run) and sumNANs."""
+    with avgSpike (spikes per neuron of the instance's spiking model
+    populations, sources excluded, over the run) and sumNANs (NaN
+    neuron-steps of those populations)."""
     from .network import Network
     net = Network.from_specs(specs, device=device)
     if engine is not None:
@@ -54,8 +73,13 @@ def run_sweep(specs, keys, device=None, engine=None):
     out = []
     for b, ((nc, gs), sp) in enumerate(zip(keys, specs)):
         o = net.pop_offsets[b]
-        count, nans = net.counters(o + 1)
-        out.append({"n_conn": nc, "gscale": gs, "avg_spike": count / sp["pops"][1]["n"], "sum_nans": nans})
+        count = nans = n = 0
+        for k, pop in enumerate(sp["pops"]):
+            if pop["kind"] == "source":
+                continue
+            c, z = net.counters(o + k)
+            count, nans, n = count + c, nans + z, n + pop["n"]
+        out.append({"n_conn": nc, "gscale": gs, "avg_spike": count / n, "sum_nans": nans})
     net.close()
     return out
 

@@ -67,3 +67,31 @@ def test_batched_sweep_matches_standalone_runs_and_oracle(gpu):
     # more conductance, more spikes
     a = {k: r["avg_spike"] for k, r in zip(keys, recs)}
     assert a[(100.0, 2.0)] >= a[(100.0, 0.5)] and a[(300.0, 2.0)] >= a[(300.0, 0.5)]
+
+
+def test_izhikevich_sweep_specs_shape():
+    G = _gs()
+    specs, keys = G.izhikevich_sweep_specs([100, 1000], [0.5, 1.0], steps=10, n=200)
+    assert len(specs) == 4 and keys[3] == (1000.0, 1.0)
+    assert [p["kind"] for p in specs[0]["pops"]] == ["izh", "izh"]
+    assert [p["n"] for p in specs[0]["pops"]] == [160, 40]
+    assert specs[0]["projs"][0]["p"] == pytest.approx(0.5) and specs[0]["projs"][0]["layout"] == "dense"
+    assert specs[3]["projs"][2]["user_scale"] == 1.0 and specs[3]["instance"] == 3
+
+
+@pytest.mark.gpu
+def test_izhikevich_sweep_matches_oracle(gpu):
+    # batched Izhikevich runs: avgSpike over the whole network within the
+    # rounding sensitivity of the network (2 % of the count plus one spike)
+    import oracle
+    from paper_1412_0595_gb300 import gscale as G
+    specs, keys = G.izhikevich_sweep_specs([100, 400], [0.5, 2.0], steps=600, n=300)
+    recs = G.run_sweep(specs, keys)
+    for r, sp in zip(recs, specs):
+        ref = oracle.from_spec(sp)
+        ref.step(sp["steps"])
+        count = sum(ref.counters(p)[0] for p in (0, 1))
+        assert count / 300 == pytest.approx(r["avg_spike"], abs=0.03 * r["avg_spike"] + 1 / 300), (r, count)
+        assert r["sum_nans"] == 0
+    a = {k: r["avg_spike"] for k, r in zip(keys, recs)}
+    assert a[(100.0, 2.0)] >= a[(100.0, 0.5)] and a[(400.0, 2.0)] >= a[(400.0, 0.5)]
