@@ -338,17 +338,39 @@ def _gscale_procedure_izhikevich(dev, steps=1000):
 
 
 def _cpu_baseline(sim_steps):
-    """The FP64 oracle, as it stands, on a bounded sample (single thread)."""
+    """The FP64 oracle, as it stands, on a bounded sample: all host cores
+    (its threaded step) and one thread."""
     import oracle
     spec = I.config_four_pop(steps=sim_steps)
-    ref = oracle.from_spec(spec)
-    t0 = time.perf_counter()
-    ref.step(sim_steps)
-    dt = time.perf_counter() - t0
     n_neurons = sum(p["n"] for p in spec["pops"])
-    return {"value": ref.events / dt, "unit": "synaptic events/s", "cores": 1, "kind": "oracle",
-            "sample": f"{sim_steps} of the 10,000 time steps of the same network, FP64, 1 thread",
-            "neuron_steps_per_s": n_neurons * sim_steps / dt, "seconds": dt}
+    cores = os.cpu_count() or 1
+    out = {}
+    for threads in (cores, 1):
+        oracle.set_threads(threads)
+        ref = oracle.from_spec(spec)
+        t0 = time.perf_counter()
+        ref.step(sim_steps)
+        out[threads] = (ref.events / (time.perf_counter() - t0), time.perf_counter() - t0)
+    oracle.set_threads(1)
+    return {"value": out[cores][0], "unit": "synaptic events/s", "cores": cores, "kind": "oracle",
+            "sample": f"{sim_steps} of the 10,000 time steps of the same network, FP64, {cores} threads "
+                      "(neurons and post ranges in parallel)",
+            "seconds": out[cores][1], "neuron_steps_per_s": n_neurons * sim_steps / out[cores][1],
+            "single_thread": {"value": out[1][0], "seconds": out[1][1]}}
+
+
+def reduce_over_ranks(total_ms, events, device):
+    """Whole-job figures of replicas: the slowest rank's time (every rank ran
+    the same work, so the job ends with the slowest) and the sum of the
+    ranks' events.  Needs an initialised process group; `device` is where
+    the backend reduces (CUDA for NCCL, CPU for gloo)."""
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(total_ms)], device=device, dtype=torch.float64)
+    e = torch.tensor([float(events)], device=device, dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    dist.all_reduce(e, op=dist.ReduceOp.SUM)
+    return float(t.item()), float(e.item())
 
 
 def run_reference(a):
@@ -358,6 +380,8 @@ def run_reference(a):
     import oracle
     spec = I.config_four_pop(steps=a.cpu_steps)
     n_neurons = sum(p["n"] for p in spec["pops"])
+    cores = os.cpu_count() or 1
+    oracle.set_threads(cores)
     times, events = [], 0
     for k in range(a.warmup + a.steps):
         ref = oracle.from_spec(spec)
@@ -376,8 +400,8 @@ def run_reference(a):
             "config": {"workload": spec["name"], "sim_steps_per_step": a.cpu_steps, "dt_ms": spec["dt"],
                        "substeps": spec["n_sub"]},
             "neuron_steps_per_s": n_neurons * a.cpu_steps * a.steps / total,
-            "cpu_baseline": {"value": value, "unit": "synaptic events/s", "cores": 1, "kind": "oracle",
-                             "sample": f"{a.cpu_steps} time steps of the same network per step"},
+            "cpu_baseline": {"value": value, "unit": "synaptic events/s", "cores": cores, "kind": "oracle",
+                             "sample": f"{a.cpu_steps} time steps of the same network per step, {cores} threads"},
             "e2e": {"value": value, "unit": "synaptic events/s", "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
@@ -481,11 +505,7 @@ def run_ours(a):
     wall = time.perf_counter() - wall0
     total_ms = sum(ms)
     if world > 1:
-        t = torch.tensor([total_ms], device=dev, dtype=torch.float64)
-        e = torch.tensor([events], device=dev, dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        dist.all_reduce(e, op=dist.ReduceOp.SUM)
-        total_ms, events = float(t.item()), float(e.item())
+        total_ms, events = reduce_over_ranks(total_ms, events, dev)
     value = events / (total_ms * 1e-3)
     neuron_steps = world * n_neurons * a.sim_steps * a.steps / (total_ms * 1e-3)
 

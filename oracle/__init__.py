@@ -35,15 +35,16 @@ FIELD = {"V": 0, "m": 1, "h": 2, "n": 3, "g0": 4, "g1": 5, "iext": 6, "isyn": 7}
 
 
 def build(force: bool = False) -> Path:
-    """Compile the oracle with gcc (no FMA contraction, so x86 and Arm agree)."""
+    """Compile the oracle with gcc (no FMA contraction, so x86 and Arm agree;
+    OpenMP for the optional multi-threaded step used only for timing)."""
     _BUILD.mkdir(exist_ok=True)
     srcs = [s for s in _SOURCES if s.exists()]
     newest = max(s.stat().st_mtime for s in srcs)
     if not force and _LIB_PATH.exists() and _LIB_PATH.stat().st_mtime >= newest:
         return _LIB_PATH
     tmp = _LIB_PATH.with_suffix(f".so.tmp{os.getpid()}")
-    cmd = ["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fno-fast-math", "-fPIC", "-shared", f"-I{_HERE}",
-           *map(str, srcs), "-o", str(tmp), "-lm"]
+    cmd = ["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fno-fast-math", "-fopenmp", "-fPIC", "-shared",
+           f"-I{_HERE}", *map(str, srcs), "-o", str(tmp), "-lm"]
     subprocess.run(cmd, check=True)
     os.replace(tmp, _LIB_PATH)
     return _LIB_PATH
@@ -119,6 +120,8 @@ def lib():
         L.oracle_source_spike.argtypes = [C.c_uint64, C.c_uint32, C.c_uint32, C.c_uint32,
                                           C.c_double, C.c_double]
         L.oracle_source_spike.restype = C.c_int
+        L.oracle_set_threads.argtypes = [C.c_int]
+        L.oracle_get_threads.restype = C.c_int
         L.oracle_izh_r.argtypes = [C.c_uint64, C.c_uint32, C.c_uint32]
         L.oracle_izh_r.restype = C.c_double
         L.oracle_izh_noise.argtypes = [C.c_uint64, C.c_uint32, C.c_uint32, C.c_uint32]
@@ -198,6 +201,15 @@ def event_list(row_ptr, col, w, spk):
 
 def source_spike(seed, tag, t, i, rate_hz, dt):
     return int(lib().oracle_source_spike(seed, tag, t, i, rate_hz, dt))
+
+
+def set_threads(n):
+    """Threads of the network step (timing only; 1 = the sequential step)."""
+    lib().oracle_set_threads(int(n))
+
+
+def get_threads():
+    return int(lib().oracle_get_threads())
 
 
 def izh_r(seed, tag, i):

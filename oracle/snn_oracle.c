@@ -29,6 +29,9 @@
  *     round(p * 2^32), so CPU and GPU draw identical bits.
  */
 #include <math.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
 #include <stdint.h>
 #include <stdlib.h>
 #include <string.h>
@@ -376,8 +379,73 @@ static void hh_substep(const oracle_pop* d, double hs, double I_in,
     *V += hs * dV; *m += hs * dm; *h += hs * dh; *n += hs * dn;
 }
 
-/* One time step of dt, in this order (Izhikevich populations: see the
- * comment in their branch; their synaptic input is the current g0 + g1):
+/* Threads of oracle_net_step (timing only; default 1).  With one thread the
+ * step is the plain sequential loop.  With more, neurons are updated in a
+ * parallel loop (each neuron's arithmetic unchanged, spike lists compacted
+ * in index order afterwards), dense rows are delivered by post ranges (the
+ * per-post summation order unchanged) and compressed rows by spike ranges
+ * into per-thread accumulators added in thread order, which changes the
+ * order of the floating-point sums of compressed-row events. */
+static int g_threads = 1;
+void oracle_set_threads(int n) { g_threads = n < 1 ? 1 : n; }
+int oracle_get_threads(void) { return g_threads; }
+
+/* The per-neuron update of population P at step t; returns 1 on a spike
+ * and sets *nan when V ends as NaN. */
+static int neuron_update(const oracle_net* net, opop* P, int i, uint32_t t, double hs, int* nan)
+{
+    const oracle_pop* d = &P->desc;
+    *nan = 0;
+    if (d->kind == POP_SOURCE) {
+        uint32_t u = draw_u32(net->seed, (uint32_t)i, t, P->tag, STREAM_SOURCE, 0);
+        return (uint64_t)u < P->thr_src;
+    }
+    if (d->kind == POP_IZH) {
+        /* Ref. [9]: v' = 0.04 v^2 + 5 v + 140 - u + I, u' = a (b v - u);
+         * v >= v_thresh (30 mV) fires and resets v <- c, u <- u + d.
+         * v takes n_sub Euler substeps of dt / n_sub, then u one step of dt
+         * with the new v, as in the model's published scheme. */
+        const double r = P->h[i];
+        const double a = d->izh[0] + d->izh[1] * r, b = d->izh[2] + d->izh[3] * r;
+        const double c = d->izh[4] + d->izh[5] * r * r, dd = d->izh[6] + d->izh[7] * r * r;
+        const double isyn = P->g[0][i] + P->g[1][i];
+        const double I = d->bias + d->noise_sigma * oracle_izh_noise(net->seed, P->tag, t, (uint32_t)i) + isyn;
+        P->isyn[i] = isyn;
+        double v = P->V[i], u = P->m[i];
+        for (int s = 0; s < net->n_sub; ++s) v += hs * (0.04 * v * v + 5.0 * v + 140.0 - u + I);
+        u += net->dt * a * (b * v - u);
+        int spike = 0;
+        if (v >= d->v_thresh) {
+            spike = 1;
+            v = c;
+            u += dd;
+        }
+        *nan = isnan(v) ? 1 : 0;
+        P->V[i] = v;
+        P->m[i] = u;
+        P->g[0][i] *= P->dec[0];
+        P->g[1][i] *= P->dec[1];
+        return spike;
+    }
+    if (P->thr_drive) {
+        uint32_t u = draw_u32(net->seed, (uint32_t)i, t, P->tag, STREAM_DRIVE, 0);
+        if ((uint64_t)u < P->thr_drive) P->iext[i] += d->drive_amp;
+    }
+    double V0 = P->V[i];
+    double isyn = P->g[0][i] * (d->E_syn[0] - V0) + P->g[1][i] * (d->E_syn[1] - V0);
+    P->isyn[i] = isyn;
+    double V = V0, m = P->m[i], h = P->h[i], n = P->n[i];
+    for (int s = 0; s < net->n_sub; ++s) hh_substep(d, hs, isyn + P->iext[i], &V, &m, &h, &n);
+    P->V[i] = V; P->m[i] = m; P->h[i] = h; P->n[i] = n;
+    *nan = isnan(V) ? 1 : 0;
+    P->g[0][i] *= P->dec[0];
+    P->g[1][i] *= P->dec[1];
+    P->iext[i] *= P->dec_drive;
+    return V0 < d->v_thresh && V >= d->v_thresh;
+}
+
+/* One time step of dt, in this order (Izhikevich populations: see
+ * neuron_update; their synaptic input is the current g0 + g1):
  *   1. Poisson sources draw their spikes;
  *   2. driven HH neurons draw a drive event and add drive_amp to I_ext;
  *   3. I_syn = sum_c g_c (E_c - V) from step-start state;
@@ -389,63 +457,30 @@ void oracle_net_step(oracle_net* net)
 {
     const uint32_t t = net->t;
     const double hs = net->dt / net->n_sub;
+    const int nt = g_threads;
     for (int p = 0; p < net->n_pops; ++p) {
         opop* P = &net->pops[p];
-        const oracle_pop* d = &P->desc;
+        const int n = P->desc.n;
         P->nspk = 0;
-        if (d->kind == POP_SOURCE) {
-            for (int i = 0; i < d->n; ++i) {
-                uint32_t u = draw_u32(net->seed, (uint32_t)i, t, P->tag, STREAM_SOURCE, 0);
-                if ((uint64_t)u < P->thr_src) P->spk[P->nspk++] = i;
+        if (nt == 1) {
+            for (int i = 0; i < n; ++i) {
+                int nan;
+                if (neuron_update(net, P, i, t, hs, &nan)) P->spk[P->nspk++] = i;
+                P->nan_count += nan;
             }
-            P->spike_count += P->nspk;
-            continue;
-        }
-        if (d->kind == POP_IZH) {
-            for (int i = 0; i < d->n; ++i) {
-                /* Ref. [9]: v' = 0.04 v^2 + 5 v + 140 - u + I, u' = a (b v - u);
-                 * v >= v_thresh (30 mV) fires and resets v <- c, u <- u + d.
-                 * v takes n_sub Euler substeps of dt / n_sub, then u one step
-                 * of dt with the new v, as in the model's published scheme. */
-                const double r = P->h[i];
-                const double a = d->izh[0] + d->izh[1] * r, b = d->izh[2] + d->izh[3] * r;
-                const double c = d->izh[4] + d->izh[5] * r * r, dd = d->izh[6] + d->izh[7] * r * r;
-                const double isyn = P->g[0][i] + P->g[1][i];
-                const double I = d->bias + d->noise_sigma * oracle_izh_noise(net->seed, P->tag, t, (uint32_t)i) + isyn;
-                P->isyn[i] = isyn;
-                double v = P->V[i], u = P->m[i];
-                for (int s = 0; s < net->n_sub; ++s) v += hs * (0.04 * v * v + 5.0 * v + 140.0 - u + I);
-                u += net->dt * a * (b * v - u);
-                if (v >= d->v_thresh) {
-                    P->spk[P->nspk++] = i;
-                    v = c;
-                    u += dd;
-                }
-                if (isnan(v)) P->nan_count++;
-                P->V[i] = v;
-                P->m[i] = u;
-                P->g[0][i] *= P->dec[0];
-                P->g[1][i] *= P->dec[1];
+        } else {
+            /* flags in the spike-list buffer (1 spike, 2 NaN), compacted after */
+            int64_t nans = 0;
+            #pragma omp parallel for num_threads(nt) schedule(static) reduction(+:nans)
+            for (int i = 0; i < n; ++i) {
+                int nan;
+                const int s = neuron_update(net, P, i, t, hs, &nan);
+                P->spk[i] = s;
+                nans += nan;
             }
-            P->spike_count += P->nspk;
-            continue;
-        }
-        for (int i = 0; i < d->n; ++i) {
-            if (P->thr_drive) {
-                uint32_t u = draw_u32(net->seed, (uint32_t)i, t, P->tag, STREAM_DRIVE, 0);
-                if ((uint64_t)u < P->thr_drive) P->iext[i] += d->drive_amp;
-            }
-            double V0 = P->V[i];
-            double isyn = P->g[0][i] * (d->E_syn[0] - V0) + P->g[1][i] * (d->E_syn[1] - V0);
-            P->isyn[i] = isyn;
-            double V = V0, m = P->m[i], h = P->h[i], n = P->n[i];
-            for (int s = 0; s < net->n_sub; ++s) hh_substep(d, hs, isyn + P->iext[i], &V, &m, &h, &n);
-            P->V[i] = V; P->m[i] = m; P->h[i] = h; P->n[i] = n;
-            if (V0 < d->v_thresh && V >= d->v_thresh) P->spk[P->nspk++] = i;
-            if (isnan(V)) P->nan_count++;
-            P->g[0][i] *= P->dec[0];
-            P->g[1][i] *= P->dec[1];
-            P->iext[i] *= P->dec_drive;
+            for (int i = 0; i < n; ++i)
+                if (P->spk[i]) P->spk[P->nspk++] = i;
+            P->nan_count += nans;
         }
         P->spike_count += P->nspk;
     }
@@ -454,16 +489,49 @@ void oracle_net_step(oracle_net* net)
         const opop* pre = &net->pops[Q->desc.pre];
         double* g = net->pops[Q->desc.post].g[Q->desc.channel];
         int64_t n_post = net->pops[Q->desc.post].desc.n;
-        for (int s = 0; s < pre->nspk; ++s) {
-            int64_t i = pre->spk[s];
-            if (Q->desc.dense) {
-                for (int64_t j = 0; j < n_post; ++j) g[j] += Q->scale * Q->w[i * n_post + j];
-                net->events += n_post;
+        if (Q->desc.dense) {
+            if (nt == 1) {
+                for (int s = 0; s < pre->nspk; ++s) {
+                    const int64_t i = pre->spk[s];
+                    for (int64_t j = 0; j < n_post; ++j) g[j] += Q->scale * Q->w[i * n_post + j];
+                }
             } else {
-                for (int64_t k = Q->row_ptr[i]; k < Q->row_ptr[i + 1]; ++k)
-                    g[Q->col[k]] += Q->scale * Q->w[k];
-                net->events += Q->row_ptr[i + 1] - Q->row_ptr[i];
+                #pragma omp parallel for num_threads(nt) schedule(static)
+                for (int64_t j = 0; j < n_post; ++j)
+                    for (int s = 0; s < pre->nspk; ++s)
+                        g[j] += Q->scale * Q->w[(int64_t)pre->spk[s] * n_post + j];
             }
+            net->events += (int64_t)pre->nspk * n_post;
+        } else {
+            int64_t ev = 0;
+            for (int s = 0; s < pre->nspk; ++s) ev += Q->row_ptr[pre->spk[s] + 1] - Q->row_ptr[pre->spk[s]];
+            if (nt == 1 || ev < 4096) {
+                for (int s = 0; s < pre->nspk; ++s) {
+                    const int64_t i = pre->spk[s];
+                    for (int64_t k = Q->row_ptr[i]; k < Q->row_ptr[i + 1]; ++k) g[Q->col[k]] += Q->scale * Q->w[k];
+                }
+            } else {
+                double* buf = (double*)xcalloc((size_t)(nt * n_post), sizeof(double));
+                #pragma omp parallel num_threads(nt)
+                {
+                    int th = 0;
+#ifdef _OPENMP
+                    th = omp_get_thread_num();
+#endif
+                    double* mine = buf + (size_t)th * n_post;
+                    #pragma omp for schedule(static)
+                    for (int s = 0; s < pre->nspk; ++s) {
+                        const int64_t i = pre->spk[s];
+                        for (int64_t k = Q->row_ptr[i]; k < Q->row_ptr[i + 1]; ++k)
+                            mine[Q->col[k]] += Q->scale * Q->w[k];
+                    }
+                    #pragma omp for schedule(static)
+                    for (int64_t j = 0; j < n_post; ++j)
+                        for (int u = 0; u < nt; ++u) g[j] += buf[(size_t)u * n_post + j];
+                }
+                free(buf);
+            }
+            net->events += ev;
         }
     }
     net->t = t + 1;

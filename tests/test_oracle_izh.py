@@ -125,3 +125,28 @@ def test_excitatory_inhibitory_parameters():
     r = np.array([oracle.izh_r(spec["seed"], 0, i) for i in range(50)])
     assert np.allclose(net.get(0, "m"), (0.25 - 0.05 * r) * -65.0, rtol=0, atol=1e-12)
     assert np.allclose(net.get(0, "h"), r, rtol=0, atol=0)
+
+
+def test_threaded_step_matches_sequential():
+    # the multi-threaded step (used for the all-core timing) gives the same
+    # spikes; neuron states are bit-identical, conductances equal to rounding
+    import snn_inputs as I2
+    spec = I2.config_four_pop(steps=200, n_mid=2000)
+    a = oracle.from_spec(spec)
+    oracle.set_threads(4)
+    try:
+        b = oracle.from_spec(spec)
+        for t in range(200):
+            oracle.set_threads(1)
+            a.step()
+            oracle.set_threads(4)
+            b.step()
+            for p in range(4):
+                assert np.array_equal(a.spikes(p), b.spikes(p)), (t, p)
+        for p in range(4):
+            assert np.allclose(a.get(p, "V"), b.get(p, "V"), rtol=0, atol=1e-9)
+            assert np.allclose(a.get(p, "g0"), b.get(p, "g0"), rtol=1e-12, atol=1e-15)
+            assert a.counters(p) == b.counters(p)
+        assert a.events == b.events
+    finally:
+        oracle.set_threads(1)
