@@ -29,6 +29,7 @@ namespace snn {
 namespace {
 
 constexpr int kThreads = 256;
+constexpr int kNeuronThreads = 64;     // per-neuron kernels: small CTAs, so 20,000 neurons reach every SM
 
 __device__ __forceinline__ float release(float V, float thr, float inv_slope) {
     return 1.0f / (1.0f + __expf((thr - V) * inv_slope));
@@ -85,28 +86,83 @@ __device__ __forceinline__ float graded_isyn(const GradedArgs& a, int pop, int l
     return isyn;
 }
 
+constexpr int kStagedThreads = 1024;              // staged kernels: one CTA per SM
+constexpr size_t kStageMaxBytes = 200 * 1024;      // largest gathered vector held in shared memory
+
+// x[i]: from shared memory when the gathered vector is staged there (its
+// random reads then cost bank conflicts instead of one L1 wavefront each),
+// else through the read-only path.
+template <bool kShared>
+__device__ __forceinline__ float gather(const float* x, int32_t i) {
+    if constexpr (kShared) return x[i];
+    else return __ldg(x + i);
+}
+
+// sum over k in [b, e) of w[k] x[idx[k]] by one warp: 16-byte loads of 4
+// consecutive synapses per lane, four 128-synapse blocks in flight per
+// iteration (128 B per lane), one partial sum per block.  w and idx are
+// padded so loads that start before e stay inside the allocation; the
+// synapse arrays are streamed (evict-first).  The order of the sums is fixed,
+// so a recomputed step is bit-identical.
+template <bool kShared>
+__device__ __forceinline__ float lane_dot(const float* w, const int32_t* idx, const float* x, int64_t b,
+                                          int64_t e, int lane) {
+    float acc[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+    for (int64_t k0 = (b & ~int64_t(3)) + 4 * lane; k0 < e; k0 += 512) {
+        float4 wv[4];
+        int4 iv[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const int64_t k = k0 + 128 * u;
+            if (k < e) {
+                wv[u] = __ldcs(reinterpret_cast<const float4*>(w + k));
+                iv[u] = __ldcs(reinterpret_cast<const int4*>(idx + k));
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const int64_t k = k0 + 128 * u;
+            if (k < e) {
+                if (k >= b) acc[u] = fmaf(wv[u].x, gather<kShared>(x, iv[u].x), acc[u]);
+                if (k + 1 >= b && k + 1 < e) acc[u] = fmaf(wv[u].y, gather<kShared>(x, iv[u].y), acc[u]);
+                if (k + 2 >= b && k + 2 < e) acc[u] = fmaf(wv[u].z, gather<kShared>(x, iv[u].z), acc[u]);
+                if (k + 3 >= b && k + 3 < e) acc[u] = fmaf(wv[u].w, gather<kShared>(x, iv[u].w), acc[u]);
+            }
+        }
+    }
+    return (acc[0] + acc[1]) + (acc[2] + acc[3]);
+}
+
 }  // namespace
 
-__global__ void __launch_bounds__(kThreads) k_graded_spmv(const GradedArgs a) {
+// One warp per post neuron.  kShared: the releases of the whole network
+// (n_total floats) are first copied into shared memory.
+template <bool kShared>
+__global__ void __launch_bounds__(kShared ? kStagedThreads : kThreads, kShared ? 1 : 4) k_graded_spmv(const GradedArgs a) {
+    extern __shared__ float s_x[];
+    const float* x = a.r;
+    if constexpr (kShared) {
+        for (int i = threadIdx.x; i < a.n_total; i += blockDim.x) s_x[i] = a.r[i];
+        __syncthreads();
+        x = s_x;
+    }
     const int lane = threadIdx.x & 31;
-    const int64_t warp = (int64_t)blockIdx.x * (kThreads / 32) + (threadIdx.x >> 5);
-    const int64_t warps = (int64_t)gridDim.x * (kThreads / 32);
+    const int64_t warp = (int64_t)blockIdx.x * (blockDim.x / 32) + (threadIdx.x >> 5);
+    const int64_t warps = (int64_t)gridDim.x * (blockDim.x / 32);
     for (int64_t w = warp; w < a.total_posts; w += warps) {
         int q = 0;
         while (a.gprojs[q].g_off + a.gprojs[q].n_post <= w) ++q;
         const GradProj& Q = a.gprojs[q];
         const int j = (int)(w - Q.g_off);
-        const int64_t b = Q.csc_ptr[j], e = Q.csc_ptr[j + 1];
-        float acc = 0.0f;
-        for (int64_t k = b + lane; k < e; k += 32) acc = fmaf(Q.csc_w[k], a.r[Q.pre_off + Q.csc_pre[k]], acc);
+        float acc = lane_dot<kShared>(Q.csc_w, Q.csc_pre, x + Q.pre_off, Q.csc_ptr[j], Q.csc_ptr[j + 1], lane);
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
         if (lane == 0) a.G[w] = acc;
     }
 }
 
-__global__ void __launch_bounds__(kThreads) k_graded_neuron(const GradedArgs a) {
-    const int idx_t = blockIdx.x * kThreads + threadIdx.x;     // tile-major over the SoA
+__global__ void __launch_bounds__(kNeuronThreads) k_graded_neuron(const GradedArgs a) {
+    const int idx_t = blockIdx.x * kNeuronThreads + threadIdx.x;     // tile-major over the SoA
     if (idx_t >= a.n_total) return;
     const int tile = idx_t / kTile;
     const int pop = a.tile_pop[tile];
@@ -169,11 +225,11 @@ __global__ void k_graded_release_init(const GradedArgs a) {
 // the step (lV includes the pre-synaptic gather of the later step), writes the
 // local part of the adjoint of the state before it, dL/dG per incoming
 // projection (per-step slice and time-contiguous copy) and dL/ds partials.
-__global__ void __launch_bounds__(kThreads) k_graded_reverse(const GradedArgs a, const AdjArgs b) {
+__global__ void __launch_bounds__(kNeuronThreads) k_graded_reverse(const GradedArgs a, const AdjArgs b) {
     __shared__ double s_gs[kMaxGradedProjs];
-    for (int k = threadIdx.x; k < a.n_gprojs; k += kThreads) s_gs[k] = 0.0;
+    for (int k = threadIdx.x; k < a.n_gprojs; k += kNeuronThreads) s_gs[k] = 0.0;
     __syncthreads();
-    const int idx_t = blockIdx.x * kThreads + threadIdx.x;
+    const int idx_t = blockIdx.x * kNeuronThreads + threadIdx.x;
     bool active = idx_t < a.n_total;
     int pop = 0, local = 0, idx = 0;
     const DevPop* Pp = nullptr;
@@ -246,11 +302,13 @@ __global__ void __launch_bounds__(kThreads) k_graded_reverse(const GradedArgs a,
         }
     }
     __syncthreads();
-    for (int k = threadIdx.x; k < a.n_gprojs; k += kThreads)
+    for (int k = threadIdx.x; k < a.n_gprojs; k += kNeuronThreads)
         if (s_gs[k] != 0.0) atomicAdd(b.grad_scale + k, s_gs[k]);
 }
 
 // dL/dV_i = local part + r'_i sum over outgoing rows of w * dL/dG (one warp per neuron).
+// One warp per pre-synaptic neuron; the dL/dG vector is gathered through L1
+// (it fits there, and a shared-memory copy would take the L1's space).
 __global__ void __launch_bounds__(kThreads) k_graded_gather(const GradedArgs a, const AdjArgs b) {
     const int lane = threadIdx.x & 31;
     const int64_t warp = (int64_t)blockIdx.x * (kThreads / 32) + (threadIdx.x >> 5);
@@ -327,14 +385,28 @@ static int grid_warps(int64_t warps) {
     return (int)b;
 }
 
+// Staged launch: one 1024-thread CTA per SM with `bytes` of shared memory.
+template <typename K, typename... Args>
+static cudaError_t launch_staged(K kernel, size_t bytes, cudaStream_t s, Args... args) {
+    int dev = 0, sms = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+    if (e != cudaSuccess) return e;
+    kernel<<<sms, kStagedThreads, bytes, s>>>(args...);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_graded_spmv(const GradedArgs& a, cudaStream_t s) {
     if (a.total_posts == 0) return cudaSuccess;
-    k_graded_spmv<<<grid_warps(a.total_posts), kThreads, 0, s>>>(a);
+    const size_t bytes = sizeof(float) * (size_t)a.n_total;
+    if (bytes <= kStageMaxBytes) return launch_staged(k_graded_spmv<true>, bytes, s, a);
+    k_graded_spmv<false><<<grid_warps(a.total_posts), kThreads, 0, s>>>(a);
     return cudaGetLastError();
 }
 
 cudaError_t launch_graded_neuron(const GradedArgs& a, cudaStream_t s) {
-    k_graded_neuron<<<(a.n_total + kThreads - 1) / kThreads, kThreads, 0, s>>>(a);
+    k_graded_neuron<<<(a.n_total + kNeuronThreads - 1) / kNeuronThreads, kNeuronThreads, 0, s>>>(a);
     return cudaGetLastError();
 }
 
@@ -344,7 +416,7 @@ cudaError_t launch_graded_release_init(const GradedArgs& a, cudaStream_t s) {
 }
 
 cudaError_t launch_graded_reverse(const GradedArgs& a, const AdjArgs& b, cudaStream_t s) {
-    k_graded_reverse<<<(a.n_total + kThreads - 1) / kThreads, kThreads, 0, s>>>(a, b);
+    k_graded_reverse<<<(a.n_total + kNeuronThreads - 1) / kNeuronThreads, kNeuronThreads, 0, s>>>(a, b);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     k_graded_gather<<<grid_warps(a.n_total), kThreads, 0, s>>>(a, b);

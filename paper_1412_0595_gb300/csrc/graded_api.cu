@@ -142,8 +142,13 @@ snn_status graded_setup(snn_net* net, cudaStream_t s) {
                 perm[k] = e;
             }
         SNN_TRY(net_alloc(net, &P.csc_ptr, (size_t)n_post + 1, "transposed row starts"));
-        SNN_TRY(net_alloc(net, &P.csc_pre, std::max<size_t>(1, (size_t)P.nnz), "transposed indices"));
-        SNN_TRY(net_alloc(net, &P.csc_w, std::max<size_t>(1, (size_t)P.nnz), "transposed weights"));
+        // padded to a multiple of 4 plus 4 zeros, so 16-byte loads that start
+        // at or before a column's end stay inside the allocation
+        const size_t padded = (size_t)((P.nnz + 3) / 4 * 4 + 4);
+        SNN_TRY(net_alloc(net, &P.csc_pre, padded, "transposed indices"));
+        SNN_TRY(net_alloc(net, &P.csc_w, padded, "transposed weights"));
+        SNN_CK(cudaMemsetAsync(P.csc_pre, 0, padded * sizeof(int32_t), s), "clear");
+        SNN_CK(cudaMemsetAsync(P.csc_w, 0, padded * sizeof(float), s), "clear");
         SNN_TRY(net_alloc(net, &P.csc_perm, std::max<size_t>(1, (size_t)P.nnz), "transposed positions"));
         SNN_CK(cudaMemcpyAsync(P.csc_ptr, cp.data(), cp.size() * sizeof(int64_t), cudaMemcpyHostToDevice, s), "upload");
         if (P.nnz) {
