@@ -66,6 +66,8 @@ def _args():
     ap.add_argument("--batch-steps", type=int, default=5000)
     ap.add_argument("--no-graded", action="store_true", help="skip the differentiable-form measurement")
     ap.add_argument("--no-gscale", action="store_true", help="skip the gScale sweep and fit")
+    ap.add_argument("--no-dense-batch", action="store_true",
+                    help="skip the tensor-core dense delivery for batched instances")
     ap.add_argument("--no-occupancy", action="store_true",
                     help="skip the occupancy-rule baseline (the paper's block sizing) beside the autotuned run")
     ap.add_argument("--no-scale-point", action="store_true",
@@ -285,6 +287,47 @@ def _differentiable(snn, torch, dev, steps=2000, K=100):
            "finite": bool(torch.isfinite(gs).all() and all(torch.isfinite(g).all() for g in gw))}
     net.close()
     return out
+
+
+def _dense_batch(snn, torch, dev, reps=20):
+    """Dense delivery for B instances sharing one projection: tensor cores
+    (tcgen05, three BF16 parts of W, FP32 accumulation) against the CUDA-core
+    rows, per step, at several activity levels.  Tensor work counts the
+    padded product the MMAs execute: 3 x 2 x Bp x Kp x Np FLOP."""
+    peaks, src = _peaks()
+    bf16 = float(peaks.get("bf16_tflops", 1900.0))
+    rng = np.random.default_rng(11)
+    out = []
+    for B, n_pre, n_post in ((512, 1000, 1000), (1024, 4096, 4096)):
+        W = torch.from_numpy(rng.lognormal(-3.0, 0.5, (n_pre, n_post)).astype(np.float32))
+        h = snn.DenseBatch(W, device=dev)
+        scale = torch.ones(B, dtype=torch.float32, device=dev)
+        G = torch.zeros((B, n_post), dtype=torch.float32, device=dev)
+        for frac in (0.01, 0.1, 0.5):
+            spikes = [np.sort(rng.choice(n_pre, max(1, int(frac * n_pre)), replace=False)) for _ in range(B)]
+            lens = [len(x) for x in spikes]
+            off = torch.tensor(np.concatenate([[0], np.cumsum(lens)]), dtype=torch.int32, device=dev)
+            idx = torch.tensor(np.concatenate(spikes), dtype=torch.int32, device=dev)
+            row = {"B": B, "n_pre": n_pre, "n_post": n_post, "activity": frac}
+            for eng in ("cuda", "tensor"):
+                h.deliver((off, idx), scale, G, engine=eng)
+                torch.cuda.synchronize()
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record()
+                for _ in range(reps):
+                    h.deliver((off, idx), scale, G, engine=eng)
+                e1.record()
+                e1.synchronize()
+                row[eng + "_us"] = 1e3 * e0.elapsed_time(e1) / reps
+            h.check()
+            bp, kp, np_ = -(-B // 128) * 128, -(-n_pre // 64) * 64, -(-n_post // 128) * 128
+            flops = 3 * 2 * bp * kp * np_
+            row["tensor_tflops"] = flops / (row["tensor_us"] * 1e-6) / 1e12
+            row["tensor_frac_bf16_peak"] = row["tensor_tflops"] / bf16
+            row["speedup_tensor_over_cuda"] = row["cuda_us"] / row["tensor_us"]
+            out.append(row)
+        h.close()
+    return {"rows": out, "peak_bf16_tflops": bf16, "peak_source": f"bf16_tflops ({src})"}
 
 
 def _gscale_procedure(dev, steps=5000):
@@ -598,6 +641,9 @@ def run_ours(a):
     differentiable = None
     if not a.no_graded and rank == 0:
         differentiable = _differentiable(snn, torch, dev)
+    dense_batch = None
+    if not a.no_dense_batch and rank == 0:
+        dense_batch = _dense_batch(snn, torch, dev)
     gscale_fit = gscale_izh = None
     if not a.no_gscale and rank == 0:
         gscale_fit = _gscale_procedure(dev)
@@ -628,6 +674,7 @@ def run_ours(a):
                 "occupancy_baseline": occupancy,
                 "batched": batched,
                 "differentiable": differentiable,
+                "dense_batch": dense_batch,
                 "gscale_fit": gscale_fit,
                 "gscale_fit_izhikevich": gscale_izh,
                 "gpu_launches": a.steps * ((-(-a.sim_steps // 1000)) + 2 if multi

@@ -318,6 +318,42 @@ snn_status snn_csr_bernoulli_fill(uint64_t seed, uint32_t tag, int64_t n_pre, in
 snn_status snn_csr_bernoulli_rows_noalloc(uint64_t seed, uint32_t tag, int64_t n_pre, int64_t n_post,
                                           double p, int64_t* row_ptr, int64_t* nnz, void* stream);
 
+/* ---- dense delivery for batched instances, on the tensor cores ------------ */
+/* Many network instances that share one dense projection W (Eq. 2 storage)
+ * receive, per step, G[b][j] += s_b * sum over the spikes i of instance b of
+ * W[i][j].  On the tensor cores that is one product of the spike matrix S
+ * (B x n_pre, 0/1, exact in BF16) with W, which is split once into three BF16
+ * parts W = hi + mid + lo (each the BF16 rounding of what the previous parts
+ * left, together W's 24 significant bits); the three products accumulate in
+ * FP32 in tensor memory (tcgen05), so the result has FP32-sum accuracy. */
+typedef struct snn_dense_batch snn_dense_batch;
+
+/* Copies W (n_pre x n_post row-major FP32, host or device) and prepares its
+ * parts.  Device memory through `alloc` (may be NULL: cudaMalloc).
+ * SNN_ERR_INVALID_ARG for sizes < 1 or n_pre * n_post > 2^31.  Synchronises
+ * `stream`. */
+snn_status snn_dense_batch_create(const float* W, int32_t n_pre, int32_t n_post, int32_t w_on_device,
+                                  const snn_allocator* alloc, void* stream, snn_dense_batch** out);
+
+/* Frees the handle and its device memory (synchronises the device). */
+snn_status snn_dense_batch_destroy(snn_dense_batch* h);
+
+/* Delivers one step for B instances; all pointers are device pointers:
+ * spk_off[B + 1] int32 offsets into spk (pre indices of each instance's
+ * spikes), scale[B], G rows of n_post floats with a stride of ldg floats
+ * (ldg >= n_post), accumulated.  engine 0: CUDA cores (each thread sums its
+ * four posts over the instance's spike rows); engine 1: tensor cores (S is
+ * built in device scratch owned by the handle, then one 128 x 128 output
+ * tile per CTA).  Enqueued on `stream`; errors of the kernels (a spike index
+ * outside [0, n_pre), a bounded wait that ran out) are reported by
+ * snn_dense_batch_check. */
+snn_status snn_dense_batch_deliver(snn_dense_batch* h, int32_t B, const int32_t* spk_off, const int32_t* spk,
+                                   const float* scale, float* G, int64_t ldg, int32_t engine, void* stream);
+
+/* Synchronises `stream` and reports a sticky kernel error of the handle:
+ * SNN_ERR_INVALID_ARG (spike index out of range) or SNN_ERR_TIMEOUT. */
+snn_status snn_dense_batch_check(snn_dense_batch* h, void* stream);
+
 /* ---- parameters ----------------------------------------------------------- */
 /* Replaces the conductance scale s of projection `proj` (rounded to FP32). */
 snn_status snn_set_scale(snn_net* net, int32_t proj, double scale);

@@ -203,6 +203,18 @@ def source_spike(seed, tag, t, i, rate_hz, dt):
     return int(lib().oracle_source_spike(seed, tag, t, i, rate_hz, dt))
 
 
+def dense_batch_deliver(W, spikes, scale, G0):
+    """Dense delivery for B instances sharing W (Sec. 3, Eq. 2 storage), the
+    plain definition in FP64: G[b, j] = G0[b, j] + scale[b] * sum over the
+    spikes i of instance b of W[i, j], i.e. G0 + diag(scale) S W with S the
+    0/1 spike matrix (a library matrix product as one step)."""
+    W = np.asarray(W, np.float64)
+    S = np.zeros((len(spikes), W.shape[0]))
+    for b, spk in enumerate(spikes):
+        S[b, np.asarray(spk, np.int64)] = 1.0
+    return np.asarray(G0, np.float64) + np.asarray(scale, np.float64)[:, None] * (S @ W)
+
+
 def set_threads(n):
     """Threads of the network step (timing only; 1 = the sequential step)."""
     lib().oracle_set_threads(int(n))

@@ -105,6 +105,10 @@ def _load():
         "snn_load_state": [vp, vp, sz, i32, vp],
         "snn_autotune": [vp, i32, P(Tuning), vp],
         "snn_occupancy_config": [vp, i32, P(Tuning), vp],
+        "snn_dense_batch_create": [vp, i32, i32, i32, P(Allocator), vp, P(vp)],
+        "snn_dense_batch_destroy": [vp],
+        "snn_dense_batch_deliver": [vp, i32, vp, vp, vp, vp, i64, i32, vp],
+        "snn_dense_batch_check": [vp, vp],
     }
     for name, args in sig.items():
         f = getattr(L, name)

@@ -1,0 +1,442 @@
+// Dense spike delivery for many network instances that share one dense
+// projection (Sec. 3, Eq. 2 storage), on the tensor cores.
+//
+// For B instances, G[b][j] += s_b * sum_i S[b][i] W[i][j] with S the 0/1
+// spike matrix of the step: one matrix product per step instead of one row
+// read per spike and instance.  S is exact in BF16.  W is split once into
+// three BF16 parts, W = hi + mid + lo (each part the BF16 rounding of what
+// the previous parts left), which carry W's 24 significant bits, and the
+// three products accumulate in FP32 in tensor memory: the result has the
+// accuracy of an FP32 sum.
+//
+// Layout: operands are stored K-major in the tensor core's canonical
+// no-swizzle form, tile by tile (128 rows x 64 K-elements = 16 KiB, core
+// matrices of 8 rows x 16 bytes, 8 of them along K per 8-row group), so each
+// tile is one contiguous bulk copy into shared memory.
+//
+// Kernel (one CTA of 128 threads per 128 x 128 output tile): one thread
+// streams the K tiles of S and of the three W parts into two shared-memory
+// stages with cp.async.bulk (completion on an mbarrier) and issues the
+// tcgen05.mma chain (M = 128, N = 128, K = 16 per instruction; 12 per K tile)
+// into a 128-column FP32 accumulator in tensor memory; tcgen05.commit
+// releases a stage when its MMAs are done.  The four warps then read the
+// accumulator with tcgen05.ld (warp w owns lanes 32w..32w+31 = 32 instances)
+// and add s_b times it to G.  Every wait is bounded: a wait that runs out sets
+// the sticky timeout bit, and the CTA still waits (bounded) for its copies
+// and MMAs and frees its tensor memory before it leaves.
+#include <algorithm>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include <cuda_bf16.h>
+
+#include "snn_internal.cuh"
+
+namespace {
+
+constexpr int kTM = 128;              // output rows (instances) per tile
+constexpr int kTN = 128;              // output columns (posts) per tile
+constexpr int kTK = 64;               // K elements (pre neurons) per tile
+constexpr int kTileElems = kTM * kTK; // 8192 BF16 = 16 KiB (same for the W tiles: kTN = kTM)
+constexpr int kStageBytes = 4 * kTileElems * 2;   // S tile + three W-part tiles
+constexpr int kThreadsMma = 128;
+
+static_assert(kTN == kTM, "S and W tiles share one tile shape");
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+// Element offset of (row, k) inside the tiled K-major layout with `kt` K tiles per row band.
+__host__ __device__ __forceinline__ int64_t tiled_offset(int64_t row, int64_t k, int64_t kt) {
+    const int64_t tile = (row / kTM) * kt + k / kTK;
+    const int r = (int)(row % kTM), c = (int)(k % kTK);
+    return tile * kTileElems + ((r >> 3) * (kTK / 8) + (c >> 3)) * 64 + (r & 7) * 8 + (c & 7);
+}
+
+__device__ __forceinline__ uint16_t bf16_rn(float x) {
+    return __bfloat16_as_ushort(__float2bfloat16_rn(x));
+}
+
+__device__ __forceinline__ float bf16_to_f(uint16_t h) { return __bfloat162float(__ushort_as_bfloat16(h)); }
+
+// W (n_pre x n_post, row-major FP32) -> three BF16 parts of W^T (post-major),
+// tiled; zero padding up to (np, kp).
+__global__ void k_split_weights(const float* W, int32_t n_pre, int32_t n_post, int64_t np, int64_t kp,
+                                uint16_t* parts) {
+    const int64_t total = np * kp, kt = kp / kTK;
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t n = e / kp, k = e % kp;
+        const float w = (n < n_post && k < n_pre) ? W[k * n_post + n] : 0.0f;
+        const uint16_t hi = bf16_rn(w);
+        const float r1 = w - bf16_to_f(hi);
+        const uint16_t mid = bf16_rn(r1);
+        const uint16_t lo = bf16_rn(r1 - bf16_to_f(mid));
+        const int64_t o = tiled_offset(n, k, kt);
+        parts[o] = hi;
+        parts[total + o] = mid;
+        parts[2 * total + o] = lo;
+    }
+}
+
+// S (bp x kp, tiled): zero, then 1.0 at every (instance, spike).
+__global__ void k_zero_u16(uint16_t* p, int64_t n) {
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x)
+        p[e] = 0;
+}
+
+__global__ void k_fill_spikes(const int32_t* spk_off, const int32_t* spk, int32_t B, int32_t n_pre, int64_t kp,
+                              uint16_t* S, uint32_t* error) {
+    const int b = blockIdx.x;
+    if (b >= B) return;
+    const int32_t beg = spk_off[b], end = spk_off[b + 1];
+    for (int32_t s = beg + threadIdx.x; s < end; s += blockDim.x) {
+        const int32_t i = spk[s];
+        if (i < 0 || i >= n_pre) {
+            atomicOr(error, snn::kDevErrCsr);     // an index outside the pre population
+            continue;
+        }
+        S[tiled_offset(b, i, kp / kTK)] = 0x3F80;   // BF16 1.0
+    }
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
+    uint32_t done;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(done) : "r"(bar), "r"(parity) : "memory");
+    return done != 0;
+}
+
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, uint32_t limit) {
+    for (uint32_t it = 0; it < limit; ++it)
+        if (mbar_try_wait(bar, parity)) return true;
+    return false;
+}
+
+__device__ __forceinline__ void bulk_copy(void* dst, const void* src, uint32_t bytes, uint32_t bar) {
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+                 ::"r"(smem_u32(dst)), "l"(src), "r"(bytes), "r"(bar) : "memory");
+}
+
+// Shared-memory matrix descriptor, K-major, no swizzle: start address, the
+// byte distance between core matrices along K (leading) and along M/N
+// (stride), descriptor version 1.
+__device__ __forceinline__ uint64_t smem_desc(uint32_t addr, uint32_t lbo, uint32_t sbo) {
+    return (uint64_t)((addr >> 4) & 0x3FFFu) | ((uint64_t)((lbo >> 4) & 0x3FFFu) << 16) |
+           ((uint64_t)((sbo >> 4) & 0x3FFFu) << 32) | (1ull << 46);
+}
+
+// Instruction descriptor of kind::f16: FP32 accumulator, BF16 A and B, both
+// K-major, N = 128, M = 128.
+constexpr uint32_t kIdesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(kTN >> 3) << 17) |
+                            ((uint32_t)(kTM >> 4) << 24);
+
+__device__ __forceinline__ void mma_bf16(uint32_t tmem, uint64_t a, uint64_t b, uint32_t accumulate) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "setp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}"
+        ::"r"(tmem), "l"(a), "l"(b), "r"(kIdesc), "r"(accumulate) : "memory");
+}
+
+__device__ __forceinline__ void mma_commit(uint32_t bar) {
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar) : "memory");
+}
+
+__global__ void __launch_bounds__(kThreadsMma, 1)
+    k_dense_batch_mma(const uint16_t* __restrict__ S, const uint16_t* __restrict__ parts, int64_t np, int64_t kp,
+                      int32_t B, int32_t n_post, const float* __restrict__ scale, float* G, int64_t ldg,
+                      uint32_t* error, uint32_t spin_limit) {
+    extern __shared__ __align__(1024) unsigned char s_raw[];
+    __shared__ __align__(8) unsigned long long s_full[2], s_done[2];
+    __shared__ uint32_t s_tmem;
+    __shared__ int s_fail;
+    const int nt = blockIdx.x, mt = blockIdx.y;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int64_t kt = kp / kTK;
+    const int64_t part_elems = np * kp;
+
+    if (warp == 0) {
+        // 128 FP32 accumulator columns x 128 lanes
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 128;" ::"r"(smem_u32(&s_tmem))
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    if (threadIdx.x == 0) {
+        for (int i = 0; i < 2; ++i) {
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&s_full[i])) : "memory");
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&s_done[i])) : "memory");
+        }
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        s_fail = 0;
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const uint32_t tmem = s_tmem;
+
+    if (threadIdx.x == 0) {
+        auto stage_ptr = [&](int st, int part) { return s_raw + (size_t)st * kStageBytes + (size_t)part * kTileElems * 2; };
+        auto issue = [&](int kc) {
+            const int st = kc & 1;
+            const uint32_t bar = smem_u32(&s_full[st]);
+            asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"((uint32_t)kStageBytes)
+                         : "memory");
+            bulk_copy(stage_ptr(st, 0), S + ((int64_t)mt * kt + kc) * kTileElems, kTileElems * 2, bar);
+            for (int p = 0; p < 3; ++p)
+                bulk_copy(stage_ptr(st, 1 + p), parts + p * part_elems + ((int64_t)nt * kt + kc) * kTileElems,
+                          kTileElems * 2, bar);
+        };
+        bool ok = true;
+        issue(0);
+        for (int kc = 0; kc < kt && ok; ++kc) {
+            if (kc + 1 < kt) {
+                const int st1 = (kc + 1) & 1;
+                // the stage is free once the MMAs of K tile kc - 1 have completed
+                if (kc + 1 >= 2 && !mbar_wait(smem_u32(&s_done[st1]), ((kc + 1) / 2 - 1) & 1, spin_limit)) {
+                    ok = false;
+                    break;
+                }
+                issue(kc + 1);
+            }
+            const int st = kc & 1;
+            if (!mbar_wait(smem_u32(&s_full[st]), (kc / 2) & 1, spin_limit)) {
+                ok = false;
+                break;
+            }
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            const uint32_t a0 = smem_u32(stage_ptr(st, 0));
+            for (int ks = 0; ks < kTK / 16; ++ks)          // K = 16 per MMA: two core matrices
+                for (int p = 0; p < 3; ++p) {
+                    const uint64_t da = smem_desc(a0 + ks * 256, 128, 1024);
+                    const uint64_t db = smem_desc(smem_u32(stage_ptr(st, 1 + p)) + ks * 256, 128, 1024);
+                    mma_bf16(tmem, da, db, (kc | ks | p) != 0);
+                }
+            mma_commit(smem_u32(&s_done[st]));
+        }
+        // the accumulator is complete when the last K tile's MMAs are
+        if (ok && !mbar_wait(smem_u32(&s_done[(kt - 1) & 1]), ((kt - 1) / 2) & 1, spin_limit)) ok = false;
+        if (!ok) {
+            atomicOr(error, snn::kDevErrTimeout);
+            s_fail = 1;
+            // wait (bounded) for whatever is still in flight into this CTA
+            for (int st = 0; st < 2; ++st) {
+                mbar_wait(smem_u32(&s_full[st]), 0, spin_limit);
+                mbar_wait(smem_u32(&s_done[st]), 0, spin_limit);
+            }
+        }
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+
+    __syncwarp();                                         // tcgen05.ld is warp-collective
+    if (!s_fail) {
+        // warp w reads lanes 32w .. 32w + 31: instance b = 128 mt + 32 w + lane
+        const int b = mt * kTM + warp * 32 + lane;
+        const float sb = b < B ? scale[b] : 0.0f;
+        for (int c0 = 0; c0 < kTN; c0 += 32) {
+            uint32_t v[32];
+            const uint32_t taddr = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0;
+            asm volatile(
+                "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
+                "{%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, "
+                "%16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
+                : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
+                  "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]),
+                  "=r"(v[15]), "=r"(v[16]), "=r"(v[17]), "=r"(v[18]), "=r"(v[19]), "=r"(v[20]), "=r"(v[21]),
+                  "=r"(v[22]), "=r"(v[23]), "=r"(v[24]), "=r"(v[25]), "=r"(v[26]), "=r"(v[27]), "=r"(v[28]),
+                  "=r"(v[29]), "=r"(v[30]), "=r"(v[31])
+                : "r"(taddr));
+            asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+            if (b < B) {
+                float* g = G + (int64_t)b * ldg + (int64_t)nt * kTN + c0;
+                const int lim = min(32, n_post - (nt * kTN + c0));
+                for (int j = 0; j < lim; ++j) g[j] += sb * __uint_as_float(v[j]);
+            }
+        }
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    if (warp == 0) {
+        __syncwarp();
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 128;" ::"r"(tmem) : "memory");
+    }
+}
+
+// CUDA-core delivery (the plain path for comparison): one CTA per (instance,
+// 1024 posts); each thread sums its four posts over the instance's spikes.
+__global__ void __launch_bounds__(256) k_dense_batch_rows(const float* __restrict__ W, int32_t n_post,
+                                                          const int32_t* spk_off, const int32_t* spk,
+                                                          const float* scale, float* G, int64_t ldg) {
+    const int b = blockIdx.y;
+    const int j = (blockIdx.x * 256 + threadIdx.x) * 4;
+    if (j >= n_post) return;
+    float a0 = 0.f, a1 = 0.f, a2 = 0.f, a3 = 0.f;
+    const bool vec = (n_post & 3) == 0;
+    for (int32_t s = spk_off[b]; s < spk_off[b + 1]; ++s) {
+        const float* row = W + (int64_t)spk[s] * n_post + j;
+        if (vec) {
+            const float4 w = __ldg(reinterpret_cast<const float4*>(row));
+            a0 += w.x; a1 += w.y; a2 += w.z; a3 += w.w;
+        } else {
+            a0 += row[0];
+            if (j + 1 < n_post) a1 += row[1];
+            if (j + 2 < n_post) a2 += row[2];
+            if (j + 3 < n_post) a3 += row[3];
+        }
+    }
+    float* g = G + (int64_t)b * ldg + j;
+    const float sb = scale[b];
+    g[0] += sb * a0;
+    if (j + 1 < n_post) g[1] += sb * a1;
+    if (j + 2 < n_post) g[2] += sb * a2;
+    if (j + 3 < n_post) g[3] += sb * a3;
+}
+
+}  // namespace
+
+struct snn_dense_batch {
+    snn::Alloc mem;
+    std::vector<void*> owned;      // device allocations, freed by snn_dense_batch_destroy
+    int32_t n_pre = 0, n_post = 0;
+    int64_t np = 0, kp = 0;
+    uint16_t* parts = nullptr;     // 3 x np x kp BF16, tiled
+    float* W = nullptr;            // n_pre x n_post FP32 (CUDA-core path)
+    uint16_t* S = nullptr;         // spike matrix, bp_cap x kp BF16, tiled
+    int64_t bp_cap = 0;
+    uint32_t* error = nullptr;
+    uint32_t spin_limit = 1u << 22;
+    int sm_count = 0;
+};
+
+using snn::fail;
+
+namespace {
+
+template <typename T>
+snn_status dalloc(snn_dense_batch* h, T** p, size_t n, const char* what) {
+    *p = static_cast<T*>(h->mem.get(sizeof(T) * std::max<size_t>(n, 1)));
+    if (!*p) return fail(SNN_ERR_OOM, std::string("device allocation failed: ") + what);
+    h->owned.push_back(*p);
+    return SNN_OK;
+}
+
+void release(snn_dense_batch* h) {
+    cudaDeviceSynchronize();
+    for (void* p : h->owned) h->mem.put(p);
+    h->owned.clear();
+}
+
+snn_status cuda(cudaError_t e, const char* what) {
+    return e == cudaSuccess ? SNN_OK : snn::cuda_fail(e, what);
+}
+
+snn_status check_error(snn_dense_batch* h, cudaStream_t s) {
+    uint32_t err = 0;
+    snn_status st = cuda(cudaMemcpyAsync(&err, h->error, sizeof(err), cudaMemcpyDeviceToHost, s), "read error word");
+    if (st == SNN_OK) st = cuda(cudaStreamSynchronize(s), "synchronize");
+    if (st != SNN_OK) return st;
+    if (err & snn::kDevErrTimeout) return fail(SNN_ERR_TIMEOUT, "tensor-core delivery: a bounded wait ran out");
+    if (err & snn::kDevErrCsr) return fail(SNN_ERR_INVALID_ARG, "spike index outside the pre population");
+    return SNN_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+snn_status snn_dense_batch_create(const float* W, int32_t n_pre, int32_t n_post, int32_t w_on_device,
+                                  const snn_allocator* alloc, void* stream, snn_dense_batch** out) {
+    if (!out || !W || n_pre < 1 || n_post < 1 || (int64_t)n_pre * n_post > (int64_t(1) << 31))
+        return fail(SNN_ERR_INVALID_ARG, "dense batch: bad weights or sizes");
+    cudaStream_t s = (cudaStream_t)stream;
+    auto* h = new (std::nothrow) snn_dense_batch();
+    if (!h) return fail(SNN_ERR_OOM, "host allocation failed");
+    if (alloc) {
+        h->mem.a = *alloc;
+        h->mem.have = true;
+    }
+    h->mem.stream = stream;
+    h->n_pre = n_pre;
+    h->n_post = n_post;
+    h->np = (n_post + kTN - 1) / kTN * kTN;
+    h->kp = (n_pre + kTK - 1) / kTK * kTK;
+    int dev = 0;
+    snn_status st = cuda(cudaGetDevice(&dev), "get device");
+    if (st == SNN_OK) st = cuda(cudaDeviceGetAttribute(&h->sm_count, cudaDevAttrMultiProcessorCount, dev), "SMs");
+    if (st == SNN_OK) st = dalloc(h, &h->parts, (size_t)(3 * h->np * h->kp), "weight parts");
+    if (st == SNN_OK) st = dalloc(h, &h->W, (size_t)n_pre * n_post + 4, "weights");
+    if (st == SNN_OK) st = dalloc(h, &h->error, 1, "error word");
+    if (st == SNN_OK)
+        st = cuda(cudaMemcpyAsync(h->W, W, sizeof(float) * (size_t)n_pre * n_post,
+                                  w_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, s), "copy weights");
+    if (st == SNN_OK) st = cuda(cudaMemsetAsync(h->error, 0, sizeof(uint32_t), s), "clear");
+    if (st == SNN_OK) {
+        const int64_t total = h->np * h->kp;
+        k_split_weights<<<(int)std::min<int64_t>((total + 255) / 256, 8192), 256, 0, s>>>(h->W, n_pre, n_post, h->np,
+                                                                                         h->kp, h->parts);
+        st = cuda(cudaGetLastError(), "split weights");
+    }
+    if (st == SNN_OK) st = cuda(cudaStreamSynchronize(s), "synchronize");
+    if (st != SNN_OK) {
+        release(h);
+        delete h;
+        return st;
+    }
+    *out = h;
+    return SNN_OK;
+}
+
+snn_status snn_dense_batch_destroy(snn_dense_batch* h) {
+    if (!h) return SNN_OK;
+    release(h);
+    delete h;
+    return SNN_OK;
+}
+
+snn_status snn_dense_batch_deliver(snn_dense_batch* h, int32_t B, const int32_t* spk_off, const int32_t* spk,
+                                   const float* scale, float* G, int64_t ldg, int32_t engine, void* stream) {
+    if (!h || B < 0 || !spk_off || !scale || !G || ldg < h->n_post || (engine != 0 && engine != 1))
+        return fail(SNN_ERR_INVALID_ARG, "dense batch: bad arguments");
+    if (B == 0) return SNN_OK;
+    cudaStream_t s = (cudaStream_t)stream;
+    snn_status st = SNN_OK;
+    if (engine == 0) {
+        const dim3 grid((unsigned)((h->n_post + 1023) / 1024), (unsigned)B);
+        k_dense_batch_rows<<<grid, 256, 0, s>>>(h->W, h->n_post, spk_off, spk, scale, G, ldg);
+        return cuda(cudaGetLastError(), "CUDA-core delivery");
+    }
+    const int64_t bp = (int64_t)(B + kTM - 1) / kTM * kTM;
+    if (bp > h->bp_cap) {
+        if (h->S) {
+            if ((st = cuda(cudaStreamSynchronize(s), "synchronize")) != SNN_OK) return st;
+            h->owned.erase(std::find(h->owned.begin(), h->owned.end(), (void*)h->S));
+            h->mem.put(h->S);
+        }
+        h->S = nullptr;
+        if ((st = dalloc(h, &h->S, (size_t)(bp * h->kp), "spike matrix")) != SNN_OK) return st;
+        h->bp_cap = bp;
+    }
+    const int64_t n_s = bp * h->kp;
+    k_zero_u16<<<(int)std::min<int64_t>((n_s + 255) / 256, 8192), 256, 0, s>>>(h->S, n_s);
+    k_fill_spikes<<<B, 128, 0, s>>>(spk_off, spk, B, h->n_pre, h->kp, h->S, h->error);
+    const size_t smem = 2 * (size_t)kStageBytes;
+    if ((st = cuda(cudaFuncSetAttribute(k_dense_batch_mma, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem),
+                   "shared memory")) != SNN_OK)
+        return st;
+    const dim3 grid((unsigned)(h->np / kTN), (unsigned)(bp / kTM));
+    k_dense_batch_mma<<<grid, kThreadsMma, smem, s>>>(h->S, h->parts, h->np, h->kp, B, h->n_post, scale, G, ldg,
+                                                      h->error, h->spin_limit);
+    if ((st = cuda(cudaGetLastError(), "tensor-core delivery")) != SNN_OK) return st;
+    return SNN_OK;
+}
+
+snn_status snn_dense_batch_check(snn_dense_batch* h, void* stream) {
+    if (!h) return fail(SNN_ERR_INVALID_ARG, "dense batch is NULL");
+    return check_error(h, (cudaStream_t)stream);
+}
+
+}  // extern "C"

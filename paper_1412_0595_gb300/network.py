@@ -462,3 +462,58 @@ class SNNFunction(torch.autograd.Function):
         g = grad_out.to(torch.float32)
         return (None, None, None, None, None, (g * gs).to(torch.float64) if gs.dtype != torch.float64 else g * gs,
                 *[g * x for x in gw])
+
+
+class DenseBatch:
+    """A dense projection W (n_pre x n_post) shared by many network instances,
+    delivered for all of them at once (``snn_dense_batch_*``): engine
+    "tensor" multiplies the step's 0/1 spike matrix with W on the tensor cores
+    (W split into three BF16 parts, FP32 accumulation), engine "cuda" sums the
+    spike rows on the CUDA cores."""
+
+    ENGINES = {"cuda": 0, "tensor": 1}
+
+    def __init__(self, W, device=None, stream=None):
+        self.device = torch.device("cuda") if device is None else torch.device(device)
+        w = _dev(W, torch.float32, self.device)
+        assert w.dim() == 2
+        self.n_pre, self.n_post = int(w.shape[0]), int(w.shape[1])
+        self._alloc = TorchAllocator(self.device.index)
+        h = C.c_void_p()
+        check(L.lib.snn_dense_batch_create(w.data_ptr(), self.n_pre, self.n_post, 1, self._alloc.ref(),
+                                           _stream(stream), C.byref(h)))
+        self.h = h
+
+    def deliver(self, spikes, scale, G, engine="tensor", stream=None):
+        """G[b] += scale[b] * W[spikes[b]].sum(0) for every instance b; `spikes`
+        is a list of index arrays (or (offsets, indices) tensors), G a CUDA
+        tensor of shape (B, >= n_post) whose rows are contiguous."""
+        if isinstance(spikes, tuple):
+            off, idx = spikes
+        else:
+            lens = [len(s) for s in spikes]
+            off = torch.tensor(np.concatenate([[0], np.cumsum(lens)]), dtype=torch.int32)
+            idx = torch.tensor(np.concatenate([np.asarray(s, np.int64) for s in spikes]) if sum(lens) else [0],
+                               dtype=torch.int32)
+        off = off.to(self.device, torch.int32).contiguous()
+        idx = idx.to(self.device, torch.int32).contiguous()
+        sc = _dev(scale, torch.float32, self.device)
+        assert G.is_cuda and G.dtype == torch.float32 and G.stride(1) == 1
+        check(L.lib.snn_dense_batch_deliver(self.h, int(G.shape[0]), off.data_ptr(), idx.data_ptr(), sc.data_ptr(),
+                                            G.data_ptr(), int(G.stride(0)), self.ENGINES[engine], _stream(stream)))
+        self._keep = (off, idx, sc)
+
+    def check(self, stream=None):
+        check(L.lib.snn_dense_batch_check(self.h, _stream(stream)))
+
+    def close(self):
+        if getattr(self, "h", None):
+            L.lib.snn_dense_batch_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+

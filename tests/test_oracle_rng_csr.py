@@ -129,3 +129,26 @@ def test_event_list_matches_row_concatenation():
     assert np.array_equal(post, want_post) and np.array_equal(wv, want_w)
     post0, _ = oracle.event_list(rp, col, w, np.zeros(0, np.int32))
     assert len(post0) == 0
+
+
+def test_dense_batch_oracle_matches_per_instance_delivery():
+    # the batched dense definition (a matrix product) against the network
+    # oracle's own dense delivery loop, one instance at a time
+    import snn_inputs as I
+    rng = np.random.default_rng(5)
+    n_pre, n_post, B = 30, 17, 4
+    W = rng.uniform(0, 1, (n_pre, n_post)).astype(np.float32).astype(np.float64)
+    spikes = [np.sort(rng.choice(n_pre, k, replace=False)) for k in (0, 1, 7, 30)]
+    scale = rng.uniform(0.5, 2.0, B)
+    G0 = rng.uniform(0, 1, (B, n_post))
+    G = oracle.dense_batch_deliver(W, spikes, scale, G0)
+    for b in range(B):
+        spec = I.net([I.source_pop(n_pre, 0.0), I.hh_pop(n_post)],
+                     [I.proj(0, 1, "dense", 1.0, ("uniform", 0.0, 1.0), k=(0.0, 0.0, 1.0), user_scale=scale[b])],
+                     dt=0.1, steps=1)
+        pops = [dict(spec["pops"][0], v0=None), dict(spec["pops"][1], v0=None)]
+        proj = dict(spec["projs"][0], w=W.ravel(), n_conn=n_pre)
+        net = oracle.OracleNet(pops, [proj], 0.1, 4, 1)
+        net.set(1, "g0", G0[b])
+        net.deliver(0, spikes[b].astype(np.int32))
+        assert np.allclose(net.get(1, "g0"), G[b], rtol=1e-14, atol=1e-14)
