@@ -12,16 +12,20 @@
 // Layout: operands are stored K-major in the tensor core's canonical
 // no-swizzle form, tile by tile (128 rows x 64 K-elements = 16 KiB, core
 // matrices of 8 rows x 16 bytes, 8 of them along K per 8-row group), so each
-// tile is one contiguous bulk copy into shared memory.
+// tile is one contiguous bulk copy into shared memory.  (Measured: 64-wide K
+// tiles in two stages beat 32-wide tiles in four by 15 % at 1024 x 4096 x 4096.)
 //
-// Kernel (one CTA of 128 threads per 128 x 128 output tile): one thread
-// streams the K tiles of S and of the three W parts into two shared-memory
-// stages with cp.async.bulk (completion on an mbarrier) and issues the
-// tcgen05.mma chain (M = 128, N = 128, K = 16 per instruction; 12 per K tile)
-// into a 128-column FP32 accumulator in tensor memory; tcgen05.commit
-// releases a stage when its MMAs are done.  The four warps then read the
-// accumulator with tcgen05.ld (warp w owns lanes 32w..32w+31 = 32 instances)
-// and add s_b times it to G.  Every wait is bounded: a wait that runs out sets
+// Kernel (one CTA of 256 threads per 256 x 128 output tile and K range):
+// one thread streams the K tiles of two 128-row S tiles and of the three W
+// parts into two shared-memory stages with cp.async.bulk (completion on an
+// mbarrier) and issues the tcgen05.mma chain (M = 128, N = 128, K = 16 per
+// instruction; 24 per K tile: 4 K steps x 3 parts x 2 row tiles, the W
+// tiles shared by both) into two 128-column FP32 accumulators in tensor
+// memory; tcgen05.commit releases a stage when its MMAs are done.  The eight
+// warps then read the accumulators with tcgen05.ld (warp w owns lanes
+// 32 (w % 4) .. + 31 of accumulator w / 4) and add s_b times them to G.  When
+// the output has few tiles the K range is split over CTAs (split-K), which
+// then add with atomics.  Every wait is bounded: a wait that runs out sets
 // the sticky timeout bit, and the CTA still waits (bounded) for its copies
 // and MMAs and frees its tensor memory before it leaves.
 #include <algorithm>
@@ -39,8 +43,10 @@ constexpr int kTM = 128;              // output rows (instances) per tile
 constexpr int kTN = 128;              // output columns (posts) per tile
 constexpr int kTK = 64;               // K elements (pre neurons) per tile
 constexpr int kTileElems = kTM * kTK; // 8192 BF16 = 16 KiB (same for the W tiles: kTN = kTM)
-constexpr int kStageBytes = 4 * kTileElems * 2;   // S tile + three W-part tiles
-constexpr int kThreadsMma = 128;
+constexpr int kStages = 2;            // shared-memory stages of the operand pipeline (2 x 80 KiB)
+constexpr uint32_t kSbo = (kTK / 8) * 128;   // bytes between 8-row groups of core matrices
+constexpr int kStageBytes = 5 * kTileElems * 2;   // two S tiles + three W-part tiles
+constexpr int kThreadsMma = 256;
 
 static_assert(kTN == kTM, "S and W tiles share one tile shape");
 
@@ -78,15 +84,16 @@ __global__ void k_split_weights(const float* W, int32_t n_pre, int32_t n_post, i
     }
 }
 
-// S (bp x kp, tiled): zero, then 1.0 at every (instance, spike).
-__global__ void k_zero_u16(uint16_t* p, int64_t n) {
-    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x)
-        p[e] = 0;
-}
-
-__global__ void k_fill_spikes(const int32_t* spk_off, const int32_t* spk, int32_t B, int32_t n_pre, int64_t kp,
-                              uint16_t* S, uint32_t* error) {
+// Row b of S (bp x kp, tiled), one CTA per row: zero (16-byte stores of 8
+// consecutive K elements, which are contiguous in the tiled layout), then
+// 1.0 at every spike of instance b (rows b >= B stay zero).
+__global__ void k_build_spikes(const int32_t* spk_off, const int32_t* spk, int32_t B, int32_t n_pre, int64_t kp,
+                               uint16_t* S, uint32_t* error) {
     const int b = blockIdx.x;
+    const int64_t kt = kp / kTK;
+    for (int64_t k8 = threadIdx.x; k8 < kp / 8; k8 += blockDim.x)
+        *reinterpret_cast<uint4*>(S + tiled_offset(b, 8 * k8, kt)) = make_uint4(0u, 0u, 0u, 0u);
+    __syncthreads();
     if (b >= B) return;
     const int32_t beg = spk_off[b], end = spk_off[b + 1];
     for (int32_t s = beg + threadIdx.x; s < end; s += blockDim.x) {
@@ -95,7 +102,7 @@ __global__ void k_fill_spikes(const int32_t* spk_off, const int32_t* spk, int32_
             atomicOr(error, snn::kDevErrCsr);     // an index outside the pre population
             continue;
         }
-        S[tiled_offset(b, i, kp / kTK)] = 0x3F80;   // BF16 1.0
+        S[tiled_offset(b, i, kt)] = 0x3F80;   // BF16 1.0
     }
 }
 
@@ -148,24 +155,27 @@ __device__ __forceinline__ void mma_commit(uint32_t bar) {
 __global__ void __launch_bounds__(kThreadsMma, 1)
     k_dense_batch_mma(const uint16_t* __restrict__ S, const uint16_t* __restrict__ parts, int64_t np, int64_t kp,
                       int32_t B, int32_t n_post, const float* __restrict__ scale, float* G, int64_t ldg,
-                      uint32_t* error, uint32_t spin_limit) {
+                      uint32_t* error, uint32_t spin_limit, int32_t k_per_cta) {
     extern __shared__ __align__(1024) unsigned char s_raw[];
-    __shared__ __align__(8) unsigned long long s_full[2], s_done[2];
+    __shared__ __align__(8) unsigned long long s_full[kStages], s_done[kStages];
     __shared__ uint32_t s_tmem;
     __shared__ int s_fail;
-    const int nt = blockIdx.x, mt = blockIdx.y;
+    const int nt = blockIdx.x, mt2 = blockIdx.y;      // row tiles 2 mt2 and 2 mt2 + 1
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int64_t kt = kp / kTK;
+    const int k0 = blockIdx.z * k_per_cta;
+    const int k1 = min((int)kt, k0 + k_per_cta);
+    const bool split = gridDim.z > 1;
     const int64_t part_elems = np * kp;
 
     if (warp == 0) {
-        // 128 FP32 accumulator columns x 128 lanes
-        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 128;" ::"r"(smem_u32(&s_tmem))
+        // two accumulators of 128 FP32 columns x 128 lanes
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 256;" ::"r"(smem_u32(&s_tmem))
                      : "memory");
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
     }
     if (threadIdx.x == 0) {
-        for (int i = 0; i < 2; ++i) {
+        for (int i = 0; i < kStages; ++i) {
             asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&s_full[i])) : "memory");
             asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&s_done[i])) : "memory");
         }
@@ -179,50 +189,54 @@ __global__ void __launch_bounds__(kThreadsMma, 1)
 
     if (threadIdx.x == 0) {
         auto stage_ptr = [&](int st, int part) { return s_raw + (size_t)st * kStageBytes + (size_t)part * kTileElems * 2; };
-        auto issue = [&](int kc) {
-            const int st = kc & 1;
+        auto issue = [&](int i) {                     // i-th K tile of this CTA's range
+            const int kc = k0 + i, st = i % kStages;
             const uint32_t bar = smem_u32(&s_full[st]);
             asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"((uint32_t)kStageBytes)
                          : "memory");
-            bulk_copy(stage_ptr(st, 0), S + ((int64_t)mt * kt + kc) * kTileElems, kTileElems * 2, bar);
+            for (int h = 0; h < 2; ++h)
+                bulk_copy(stage_ptr(st, h), S + ((int64_t)(2 * mt2 + h) * kt + kc) * kTileElems, kTileElems * 2, bar);
             for (int p = 0; p < 3; ++p)
-                bulk_copy(stage_ptr(st, 1 + p), parts + p * part_elems + ((int64_t)nt * kt + kc) * kTileElems,
+                bulk_copy(stage_ptr(st, 2 + p), parts + p * part_elems + ((int64_t)nt * kt + kc) * kTileElems,
                           kTileElems * 2, bar);
         };
+        const int n_k = k1 - k0;
         bool ok = true;
-        issue(0);
-        for (int kc = 0; kc < kt && ok; ++kc) {
-            if (kc + 1 < kt) {
-                const int st1 = (kc + 1) & 1;
-                // the stage is free once the MMAs of K tile kc - 1 have completed
-                if (kc + 1 >= 2 && !mbar_wait(smem_u32(&s_done[st1]), ((kc + 1) / 2 - 1) & 1, spin_limit)) {
+        for (int i = 0; i < kStages - 1 && i < n_k; ++i) issue(i);
+        for (int i = 0; i < n_k && ok; ++i) {
+            const int nx = i + kStages - 1;              // the tile that refills the stage tile i - 1 used
+            if (nx < n_k) {
+                // that stage is free once the MMAs of tile i - 1 have completed
+                if (i >= 1 && !mbar_wait(smem_u32(&s_done[nx % kStages]), ((i - 1) / kStages) & 1, spin_limit)) {
                     ok = false;
                     break;
                 }
-                issue(kc + 1);
+                issue(nx);
             }
-            const int st = kc & 1;
-            if (!mbar_wait(smem_u32(&s_full[st]), (kc / 2) & 1, spin_limit)) {
+            const int st = i % kStages;
+            if (!mbar_wait(smem_u32(&s_full[st]), (i / kStages) & 1, spin_limit)) {
                 ok = false;
                 break;
             }
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-            const uint32_t a0 = smem_u32(stage_ptr(st, 0));
             for (int ks = 0; ks < kTK / 16; ++ks)          // K = 16 per MMA: two core matrices
                 for (int p = 0; p < 3; ++p) {
-                    const uint64_t da = smem_desc(a0 + ks * 256, 128, 1024);
-                    const uint64_t db = smem_desc(smem_u32(stage_ptr(st, 1 + p)) + ks * 256, 128, 1024);
-                    mma_bf16(tmem, da, db, (kc | ks | p) != 0);
+                    const uint64_t db = smem_desc(smem_u32(stage_ptr(st, 2 + p)) + ks * 256, 128, kSbo);
+                    for (int h = 0; h < 2; ++h) {
+                        const uint64_t da = smem_desc(smem_u32(stage_ptr(st, h)) + ks * 256, 128, kSbo);
+                        mma_bf16(tmem + (uint32_t)(h * kTN), da, db, (i | ks | p) != 0);
+                    }
                 }
             mma_commit(smem_u32(&s_done[st]));
         }
-        // the accumulator is complete when the last K tile's MMAs are
-        if (ok && !mbar_wait(smem_u32(&s_done[(kt - 1) & 1]), ((kt - 1) / 2) & 1, spin_limit)) ok = false;
+        // the accumulators are complete when the range's last tile's MMAs are
+        if (ok && !mbar_wait(smem_u32(&s_done[(n_k - 1) % kStages]), ((n_k - 1) / kStages) & 1, spin_limit))
+            ok = false;
         if (!ok) {
             atomicOr(error, snn::kDevErrTimeout);
             s_fail = 1;
             // wait (bounded) for whatever is still in flight into this CTA
-            for (int st = 0; st < 2; ++st) {
+            for (int st = 0; st < kStages; ++st) {
                 mbar_wait(smem_u32(&s_full[st]), 0, spin_limit);
                 mbar_wait(smem_u32(&s_done[st]), 0, spin_limit);
             }
@@ -234,12 +248,14 @@ __global__ void __launch_bounds__(kThreadsMma, 1)
 
     __syncwarp();                                         // tcgen05.ld is warp-collective
     if (!s_fail) {
-        // warp w reads lanes 32w .. 32w + 31: instance b = 128 mt + 32 w + lane
-        const int b = mt * kTM + warp * 32 + lane;
+        // warp w reads lanes 32 (w % 4) .. + 31 of accumulator w / 4:
+        // instance b = 128 (2 mt2 + w / 4) + 32 (w % 4) + lane
+        const int q = warp & 3, h = warp >> 2;
+        const int b = (2 * mt2 + h) * kTM + q * 32 + lane;
         const float sb = b < B ? scale[b] : 0.0f;
         for (int c0 = 0; c0 < kTN; c0 += 32) {
             uint32_t v[32];
-            const uint32_t taddr = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0;
+            const uint32_t taddr = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(h * kTN + c0);
             asm volatile(
                 "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
                 "{%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, "
@@ -254,7 +270,10 @@ __global__ void __launch_bounds__(kThreadsMma, 1)
             if (b < B) {
                 float* g = G + (int64_t)b * ldg + (int64_t)nt * kTN + c0;
                 const int lim = min(32, n_post - (nt * kTN + c0));
-                for (int j = 0; j < lim; ++j) g[j] += sb * __uint_as_float(v[j]);
+                if (split)
+                    for (int j = 0; j < lim; ++j) atomicAdd(g + j, sb * __uint_as_float(v[j]));
+                else
+                    for (int j = 0; j < lim; ++j) g[j] += sb * __uint_as_float(v[j]);
             }
         }
     }
@@ -262,7 +281,7 @@ __global__ void __launch_bounds__(kThreadsMma, 1)
     __syncthreads();
     if (warp == 0) {
         __syncwarp();
-        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 128;" ::"r"(tmem) : "memory");
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 256;" ::"r"(tmem) : "memory");
     }
 }
 
@@ -310,6 +329,7 @@ struct snn_dense_batch {
     uint32_t* error = nullptr;
     uint32_t spin_limit = 1u << 22;
     int sm_count = 0;
+    bool smem_set = false;
 };
 
 using snn::fail;
@@ -409,7 +429,7 @@ snn_status snn_dense_batch_deliver(snn_dense_batch* h, int32_t B, const int32_t*
         k_dense_batch_rows<<<grid, 256, 0, s>>>(h->W, h->n_post, spk_off, spk, scale, G, ldg);
         return cuda(cudaGetLastError(), "CUDA-core delivery");
     }
-    const int64_t bp = (int64_t)(B + kTM - 1) / kTM * kTM;
+    const int64_t bp = (int64_t)(B + 2 * kTM - 1) / (2 * kTM) * (2 * kTM);   // whole pairs of row tiles
     if (bp > h->bp_cap) {
         if (h->S) {
             if ((st = cuda(cudaStreamSynchronize(s), "synchronize")) != SNN_OK) return st;
@@ -420,16 +440,22 @@ snn_status snn_dense_batch_deliver(snn_dense_batch* h, int32_t B, const int32_t*
         if ((st = dalloc(h, &h->S, (size_t)(bp * h->kp), "spike matrix")) != SNN_OK) return st;
         h->bp_cap = bp;
     }
-    const int64_t n_s = bp * h->kp;
-    k_zero_u16<<<(int)std::min<int64_t>((n_s + 255) / 256, 8192), 256, 0, s>>>(h->S, n_s);
-    k_fill_spikes<<<B, 128, 0, s>>>(spk_off, spk, B, h->n_pre, h->kp, h->S, h->error);
-    const size_t smem = 2 * (size_t)kStageBytes;
-    if ((st = cuda(cudaFuncSetAttribute(k_dense_batch_mma, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem),
-                   "shared memory")) != SNN_OK)
-        return st;
-    const dim3 grid((unsigned)(h->np / kTN), (unsigned)(bp / kTM));
+    k_build_spikes<<<(unsigned)bp, 128, 0, s>>>(spk_off, spk, B, h->n_pre, h->kp, h->S, h->error);
+    const size_t smem = kStages * (size_t)kStageBytes;
+    if (!h->smem_set) {
+        if ((st = cuda(cudaFuncSetAttribute(k_dense_batch_mma, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem),
+                       "shared memory")) != SNN_OK)
+            return st;
+        h->smem_set = true;
+    }
+    // split the K range when the output has fewer tiles than SMs
+    const int64_t tiles = (h->np / kTN) * (bp / (2 * kTM)), kt = h->kp / kTK;
+    int64_t ksplit = std::min<int64_t>(kt, std::max<int64_t>(1, (h->sm_count + tiles - 1) / tiles));
+    const int k_per = (int)((kt + ksplit - 1) / ksplit);
+    ksplit = (kt + k_per - 1) / k_per;
+    const dim3 grid((unsigned)(h->np / kTN), (unsigned)(bp / (2 * kTM)), (unsigned)ksplit);
     k_dense_batch_mma<<<grid, kThreadsMma, smem, s>>>(h->S, h->parts, h->np, h->kp, B, h->n_post, scale, G, ldg,
-                                                      h->error, h->spin_limit);
+                                                      h->error, h->spin_limit, k_per);
     if ((st = cuda(cudaGetLastError(), "tensor-core delivery")) != SNN_OK) return st;
     return SNN_OK;
 }
