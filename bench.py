@@ -72,7 +72,7 @@ def _args():
                     help="skip the occupancy-rule baseline (the paper's block sizing) beside the autotuned run")
     ap.add_argument("--no-scale-point", action="store_true",
                     help="skip the forced-activity propagation measurement at 100 x 1,000,000, p = 0.5")
-    ap.add_argument("--profile", choices=["cluster", "tiled", "dense", "neuron", "graded"],
+    ap.add_argument("--profile", choices=["cluster", "tiled", "dense", "neuron", "graded", "dense_batch"],
                     help="run a few launches of one kernel on its workload and exit (a target for ncu)")
     ap.add_argument("--record-traffic", nargs=3, metavar=("KERNEL", "BYTES", "COMMAND"),
                     help="store an ncu DRAM byte count per launch of KERNEL (with a hash of its sources) in "
@@ -785,7 +785,9 @@ def run_profile(a):
       dense:   the same with dense rows;
       neuron:  8,000,000 HH neurons, one neuron phase per launch;
       graded:  the differentiable workload (20,000 middle neurons), 200 steps
-               recorded forward and the adjoint."""
+               recorded forward and the adjoint;
+      dense_batch: tensor-core delivery for 1024 instances sharing a 4096 x 4096
+               dense projection, half of the pre neurons spiking, three launches."""
     import torch
 
     import paper_1412_0595_gb300 as snn
@@ -801,6 +803,18 @@ def run_profile(a):
         flush = _flush_buffers(torch, dev)
         _forced_propagation(snn, torch, dev, 1_000_000, 0.5, "csr" if a.profile == "tiled" else a.profile, reps=3,
                             flush=flush)
+        return
+    elif a.profile == "dense_batch":
+        rng = np.random.default_rng(11)
+        W = torch.from_numpy(rng.lognormal(-3.0, 0.5, (4096, 4096)).astype(np.float32))
+        h = snn.DenseBatch(W, device=dev)
+        spikes = [np.sort(rng.choice(4096, 2048, replace=False)) for _ in range(1024)]
+        G = torch.zeros((1024, 4096), dtype=torch.float32, device=dev)
+        scale = torch.ones(1024, dtype=torch.float32, device=dev)
+        for _ in range(3):
+            h.deliver(spikes, scale, G, engine="tensor")
+        h.check()
+        h.close()
         return
     elif a.profile == "neuron":
         net = snn.Network.from_spec(I.net([I.hh_pop(8_000_000)], [], dt=0.1, steps=1), device=dev)
