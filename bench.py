@@ -320,7 +320,7 @@ def _dense_batch(snn, torch, dev, reps=20):
                 e1.synchronize()
                 row[eng + "_us"] = 1e3 * e0.elapsed_time(e1) / reps
             h.check()
-            bp, kp, np_ = -(-B // 128) * 128, -(-n_pre // 64) * 64, -(-n_post // 128) * 128
+            bp, kp, np_ = -(-B // 256) * 256, -(-n_pre // 48) * 48, -(-n_post // 128) * 128   # the kernel's padding
             flops = 3 * 2 * bp * kp * np_
             row["tensor_tflops"] = flops / (row["tensor_us"] * 1e-6) / 1e12
             row["tensor_frac_bf16_peak"] = row["tensor_tflops"] / bf16

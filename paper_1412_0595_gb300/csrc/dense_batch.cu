@@ -12,16 +12,16 @@
 // Layout: operands are stored K-major in the tensor core's canonical
 // no-swizzle form, tile by tile (128 rows x 64 K-elements = 16 KiB, core
 // matrices of 8 rows x 16 bytes, 8 of them along K per 8-row group), so each
-// tile is one contiguous bulk copy into shared memory.  (Measured: 64-wide K
-// tiles in two stages beat 32-wide tiles in four by 15 % at 1024 x 4096 x 4096.)
+// tile is one contiguous bulk copy into shared memory.
 //
 // Kernel (one CTA of 256 threads per 256 x 128 output tile and K range):
-// one thread streams the K tiles of two 128-row S tiles and of the three W
-// parts into two shared-memory stages with cp.async.bulk (completion on an
-// mbarrier) and issues the tcgen05.mma chain (M = 128, N = 128, K = 16 per
-// instruction; 24 per K tile: 4 K steps x 3 parts x 2 row tiles, the W
-// tiles shared by both) into two 128-column FP32 accumulators in tensor
-// memory; tcgen05.commit releases a stage when its MMAs are done.  The eight
+// one thread (warp 0) streams the K tiles of two 128-row S tiles and of the
+// three W parts into three shared-memory stages with cp.async.bulk
+// (completion on an mbarrier); another (warp 1) issues, as each stage lands,
+// its tcgen05.mma chain (M = 128, N = 128, K = 16 per instruction; 18 per K
+// tile: 3 K steps x 3 parts x 2 row tiles, the W tiles shared by both) into
+// two 128-column FP32 accumulators in tensor memory; tcgen05.commit
+// releases a stage when its MMAs are done.  The eight
 // warps then read the accumulators with tcgen05.ld (warp w owns lanes
 // 32 (w % 4) .. + 31 of accumulator w / 4) and add s_b times them to G.  When
 // the output has few tiles the K range is split over CTAs (split-K), which
@@ -41,9 +41,9 @@ namespace {
 
 constexpr int kTM = 128;              // output rows (instances) per tile
 constexpr int kTN = 128;              // output columns (posts) per tile
-constexpr int kTK = 64;               // K elements (pre neurons) per tile
-constexpr int kTileElems = kTM * kTK; // 8192 BF16 = 16 KiB (same for the W tiles: kTN = kTM)
-constexpr int kStages = 2;            // shared-memory stages of the operand pipeline (2 x 80 KiB)
+constexpr int kTK = 48;               // K elements (pre neurons) per tile
+constexpr int kTileElems = kTM * kTK; // 6144 BF16 = 12 KiB (same for the W tiles: kTN = kTM)
+constexpr int kStages = 3;            // shared-memory stages of the operand pipeline (3 x 60 KiB)
 constexpr uint32_t kSbo = (kTK / 8) * 128;   // bytes between 8-row groups of core matrices
 constexpr int kStageBytes = 5 * kTileElems * 2;   // two S tiles + three W-part tiles
 constexpr int kThreadsMma = 256;
@@ -187,10 +187,19 @@ __global__ void __launch_bounds__(kThreadsMma, 1)
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     const uint32_t tmem = s_tmem;
 
+    auto stage_ptr = [&](int st, int part) { return s_raw + (size_t)st * kStageBytes + (size_t)part * kTileElems * 2; };
+    const int n_k = k1 - k0;
     if (threadIdx.x == 0) {
-        auto stage_ptr = [&](int st, int part) { return s_raw + (size_t)st * kStageBytes + (size_t)part * kTileElems * 2; };
-        auto issue = [&](int i) {                     // i-th K tile of this CTA's range
-            const int kc = k0 + i, st = i % kStages;
+        // producer: tile i goes into stage i % kStages once the MMAs of tile
+        // i - kStages (the stage's previous use) have completed
+        for (int i = 0; i < n_k; ++i) {
+            const int st = i % kStages;
+            if (i >= kStages && !mbar_wait(smem_u32(&s_done[st]), (i / kStages - 1) & 1, spin_limit)) {
+                atomicOr(error, snn::kDevErrTimeout);
+                s_fail = 1;
+                break;
+            }
+            const int kc = k0 + i;
             const uint32_t bar = smem_u32(&s_full[st]);
             asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"((uint32_t)kStageBytes)
                          : "memory");
@@ -199,20 +208,11 @@ __global__ void __launch_bounds__(kThreadsMma, 1)
             for (int p = 0; p < 3; ++p)
                 bulk_copy(stage_ptr(st, 2 + p), parts + p * part_elems + ((int64_t)nt * kt + kc) * kTileElems,
                           kTileElems * 2, bar);
-        };
-        const int n_k = k1 - k0;
+        }
+    } else if (threadIdx.x == 32) {
+        // MMA issuer: as soon as a stage has landed, its 3 x 2 x kTK / 16 MMAs
         bool ok = true;
-        for (int i = 0; i < kStages - 1 && i < n_k; ++i) issue(i);
-        for (int i = 0; i < n_k && ok; ++i) {
-            const int nx = i + kStages - 1;              // the tile that refills the stage tile i - 1 used
-            if (nx < n_k) {
-                // that stage is free once the MMAs of tile i - 1 have completed
-                if (i >= 1 && !mbar_wait(smem_u32(&s_done[nx % kStages]), ((i - 1) / kStages) & 1, spin_limit)) {
-                    ok = false;
-                    break;
-                }
-                issue(nx);
-            }
+        for (int i = 0; i < n_k; ++i) {
             const int st = i % kStages;
             if (!mbar_wait(smem_u32(&s_full[st]), (i / kStages) & 1, spin_limit)) {
                 ok = false;
@@ -235,12 +235,17 @@ __global__ void __launch_bounds__(kThreadsMma, 1)
         if (!ok) {
             atomicOr(error, snn::kDevErrTimeout);
             s_fail = 1;
-            // wait (bounded) for whatever is still in flight into this CTA
-            for (int st = 0; st < kStages; ++st) {
-                mbar_wait(smem_u32(&s_full[st]), 0, spin_limit);
-                mbar_wait(smem_u32(&s_done[st]), 0, spin_limit);
-            }
         }
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    if (s_fail && threadIdx.x == 0) {
+        // wait (bounded) for whatever may still be in flight into this CTA
+        for (int st = 0; st < kStages; ++st)
+            for (uint32_t par = 0; par < 2; ++par) {
+                mbar_wait(smem_u32(&s_full[st]), par, spin_limit);
+                mbar_wait(smem_u32(&s_done[st]), par, spin_limit);
+            }
     }
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
@@ -448,7 +453,9 @@ snn_status snn_dense_batch_deliver(snn_dense_batch* h, int32_t B, const int32_t*
             return st;
         h->smem_set = true;
     }
-    // split the K range when the output has fewer tiles than SMs
+    // split the K range when the output has fewer tiles than SMs (a finer
+    // split to even out the waves measured slower: its atomic epilogue and
+    // the repeated W reads cost more than the idle SMs of the last wave)
     const int64_t tiles = (h->np / kTN) * (bp / (2 * kTM)), kt = h->kp / kTK;
     int64_t ksplit = std::min<int64_t>(kt, std::max<int64_t>(1, (h->sm_count + tiles - 1) / tiles));
     const int k_per = (int)((kt + ksplit - 1) / ksplit);
