@@ -453,11 +453,11 @@ snn_status snn_dense_batch_deliver(snn_dense_batch* h, int32_t B, const int32_t*
             return st;
         h->smem_set = true;
     }
-    // split the K range when the output has fewer tiles than SMs (a finer
-    // split to even out the waves measured slower: its atomic epilogue and
-    // the repeated W reads cost more than the idle SMs of the last wave)
+    // split the K range only when the output has fewer than half as many
+    // tiles as SMs (measured: a split that only evens out the waves costs
+    // more in its atomic epilogue than the idle SMs of the last wave)
     const int64_t tiles = (h->np / kTN) * (bp / (2 * kTM)), kt = h->kp / kTK;
-    int64_t ksplit = std::min<int64_t>(kt, std::max<int64_t>(1, (h->sm_count + tiles - 1) / tiles));
+    int64_t ksplit = tiles * 2 > h->sm_count ? 1 : std::min<int64_t>(kt, (h->sm_count + tiles - 1) / tiles);
     const int k_per = (int)((kt + ksplit - 1) / ksplit);
     ksplit = (kt + k_per - 1) / k_per;
     const dim3 grid((unsigned)(h->np / kTN), (unsigned)(bp / (2 * kTM)), (unsigned)ksplit);
