@@ -327,7 +327,9 @@ def _dense_batch(snn, torch, dev, reps=20):
             row["speedup_tensor_over_cuda"] = row["cuda_us"] / row["tensor_us"]
             out.append(row)
         h.close()
-    return {"rows": out, "peak_bf16_tflops": bf16, "peak_source": f"bf16_tflops ({src})"}
+    # DRAM bytes of the 1024 x 4096 x 4096 launch at 50 % activity (the ncu capture of --profile dense_batch)
+    return {"rows": out, "peak_bf16_tflops": bf16, "peak_source": f"bf16_tflops ({src})",
+            "traffic_1024x4096x4096": _traffic("k_dense_batch_mma")}
 
 
 def _gscale_procedure(dev, steps=5000):
@@ -837,6 +839,7 @@ _KERNEL_SOURCES = {
     "k_neuron_step": ["neuron.cu", "neuron_update.cuh", "device_math.cuh", "compaction.cuh", "snn_internal.cuh"],
     "k_propagate_tiled": ["propagate_tiled.cu", "snn_internal.cuh"],
     "k_propagate": ["propagate.cu", "snn_internal.cuh"],
+    "k_dense_batch_mma": ["dense_batch.cu", "snn_internal.cuh"],
 }
 
 
