@@ -1,7 +1,7 @@
 // Cluster step engine: a whole small network advanced by one thread-block
 // cluster (up to 16 CTAs of 1024 threads on 16 SMs) for many steps per launch.
 //
-// Each CTA owns a contiguous, tile-aligned slice of the structure-of-arrays
+// Each CTA owns a contiguous, warp-aligned slice of the structure-of-arrays
 // neurons and keeps their state in registers for the whole launch.  Spikes
 // are exchanged through distributed shared memory: every warp writes the
 // ballot word of its 32 neurons into a spike bitmask held by every CTA (plain
@@ -93,7 +93,7 @@ template <int NPT>
 __global__ void __launch_bounds__(kCT, 1) k_step_cluster(const PersistArgs A, int per_cta) {
     extern __shared__ float s_mem[];
     // spike words [2 parities][n_words] (8-byte aligned at the start), then the
-    // accumulators [channel 0/1][per_cta]
+    // accumulators [step parity][channel 0/1][per_cta]
     unsigned long long* bits = reinterpret_cast<unsigned long long*>(s_mem);
     const int n_words = A.n.num_tiles * (kTile / 32);
     float* acc = reinterpret_cast<float*>(bits + 2 * n_words);
@@ -119,7 +119,7 @@ __global__ void __launch_bounds__(kCT, 1) k_step_cluster(const PersistArgs A, in
     const int p_lo = base < n_soa ? a.tile_pop[base / kTile] : 0;
     const int p_hi = last_idx >= base ? a.tile_pop[last_idx / kTile] : p_lo - 1;
     for (int p = p_lo; p <= p_hi; ++p) copy_pop(s_pops + (p - p_lo), a.pops + p);
-    for (int j = threadIdx.x; j < 2 * per_cta; j += kCT) acc[j] = 0.0f;
+    for (int j = threadIdx.x; j < 4 * per_cta; j += kCT) acc[j] = 0.0f;
     for (int j = threadIdx.x; j < 2 * n_words; j += kCT) bits[j] = 0ull;
     for (int p = threadIdx.x; p < kMaxSlicePops; p += kCT) s_pop_spikes[p] = 0ull;
     for (int tl = threadIdx.x; tl < a.num_tiles; tl += kCT) {
@@ -201,6 +201,9 @@ __global__ void __launch_bounds__(kCT, 1) k_step_cluster(const PersistArgs A, in
     for (int k = 0; k <= A.n_steps; ++k) {
         const unsigned long long e64 = epoch0 + (unsigned long long)k;
         const int slot = (int)(e64 & 1ull);
+        // the accumulators alternate by step, so a step's clearing and the
+        // next-but-one step's adds are ordered by the CTA barrier between them
+        float* acc_k = acc + (k & 1) * 2 * per_cta;
         // ---- pull: the previous step's spikes, my slice of their rows --------
         // Light rows: each lane reads one word; the warp then adds, spike by
         // spike, this CTA's segment of each row.  Heavy rows: every warp reads
@@ -220,7 +223,7 @@ __global__ void __launch_bounds__(kCT, 1) k_step_cluster(const PersistArgs A, in
                         const int bit = __ffs(mm) - 1;
                         mm &= mm - 1u;
                         pull_row(A, s_tile_pop, s_tile_local, s_out_begin, (w0 + l) * 32 + bit, rank, n_ranks, base,
-                                 per_cta, acc, 0, 1, lane);
+                                 per_cta, acc_k, 0, 1, lane);
                     }
                 }
             }
@@ -238,16 +241,17 @@ __global__ void __launch_bounds__(kCT, 1) k_step_cluster(const PersistArgs A, in
                         const int bit = __ffs(mm) - 1;
                         mm &= mm - 1u;
                         pull_row(A, s_tile_pop, s_tile_local, s_out_begin, wd * 32 + bit, rank, n_ranks, base,
-                                 per_cta, acc, warp, kCT / 32, lane);
+                                 per_cta, acc_k, warp, kCT / 32, lane);
                     }
                 }
             }
-            __syncthreads();                                // events in acc
+            __syncthreads();                                // events in acc_k
         }
         if (k == A.n_steps) break;                         // the last pull folds into g below
         const uint32_t t = (uint32_t)(e64 - ebase);
         const bool last = k == A.n_steps - 1;
         unsigned long long* cur = bits + slot * n_words;
+        bool wrote = false;                                // this warp stored spike words
 #pragma unroll
         for (int u = 0; u < NPT; ++u) {
             const int off = threadIdx.x + u * kCT;
@@ -256,10 +260,10 @@ __global__ void __launch_bounds__(kCT, 1) k_step_cluster(const PersistArgs A, in
             if (live[u]) {
                 const DevPop& P = s_pops[pop_of[u]];
                 if (P.kind != SNN_POP_SOURCE) {
-                    st[u].g0 += acc[off];
-                    st[u].g1 += acc[per_cta + off];
-                    acc[off] = 0.0f;
-                    acc[per_cta + off] = 0.0f;
+                    st[u].g0 += acc_k[off];
+                    st[u].g1 += acc_k[per_cta + off];
+                    acc_k[off] = 0.0f;
+                    acc_k[per_cta + off] = 0.0f;
                 }
                 float isyn;
                 spike = neuron_step(P, key, t, local_of[u], a.hs, a.n_sub, st[u], &isyn);
@@ -271,6 +275,7 @@ __global__ void __launch_bounds__(kCT, 1) k_step_cluster(const PersistArgs A, in
             }
             const unsigned ballot = __ballot_sync(0xffffffffu, spike);
             if (ballot && off < per_cta) {
+                wrote = true;
                 // the warp's 32 neurons are one word of every CTA's spike words
                 const int wd = (base + u * kCT + warp * 32) / 32;
                 if (lane < n_ranks) st_cluster_u64(cur + wd, lane, ((unsigned long long)(uint32_t)e64 << 32) | ballot);
@@ -285,8 +290,15 @@ __global__ void __launch_bounds__(kCT, 1) k_step_cluster(const PersistArgs A, in
                 }
             }
         }
-        cluster.sync();                                    // this step's spikes are in every CTA's words
+        // End of step: only warps that stored spike words need release
+        // ordering (a cluster-scope fence); the barrier itself is relaxed and
+        // its wait acquires.  Shared accumulators need no cluster ordering
+        // (see acc_k above), so a step without spikes runs no fence.
+        if (wrote) asm volatile("fence.acq_rel.cluster;" ::: "memory");
+        asm volatile("barrier.cluster.arrive.relaxed.aligned;" ::: "memory");
+        asm volatile("barrier.cluster.wait.acquire.aligned;" ::: "memory");
     }
+    const float* acc_end = acc + (A.n_steps & 1) * 2 * per_cta;
 
     // fold the last step's events (pulled above), write the state and the
     // launch's spike counts back
@@ -298,8 +310,8 @@ __global__ void __launch_bounds__(kCT, 1) k_step_cluster(const PersistArgs A, in
         if (P.kind == SNN_POP_SOURCE) continue;
         const int off = threadIdx.x + u * kCT;
         const int idx = base + off;
-        st[u].g0 += acc[off];
-        st[u].g1 += acc[per_cta + off];
+        st[u].g0 += acc_end[off];
+        st[u].g1 += acc_end[per_cta + off];
         a.V[idx] = st[u].V; a.m[idx] = st[u].m; a.h[idx] = st[u].h; a.n[idx] = st[u].n;
         a.g0[idx] = st[u].g0; a.g1[idx] = st[u].g1; a.iext[idx] = st[u].ie;
     }
@@ -330,7 +342,7 @@ __global__ void k_cluster_splits(const int64_t* row_ptr, const int32_t* col, int
 }
 
 size_t cluster_smem(int per_cta, int num_tiles) {
-    return sizeof(unsigned long long) * 2 * (size_t)num_tiles * (kTile / 32) + sizeof(float) * 2 * (size_t)per_cta;
+    return sizeof(unsigned long long) * 2 * (size_t)num_tiles * (kTile / 32) + sizeof(float) * 4 * (size_t)per_cta;
 }
 
 template <int NPT>
@@ -363,9 +375,9 @@ cudaError_t launch_npt(const PersistArgs& a, int cl, int per_cta, cudaStream_t s
 // or 0 when it does not fit one cluster (16 CTAs x 1024 threads x 4 neurons).
 int cluster_plan(int n_total, int n_pops, int* per_cta) {
     if (n_pops > kMaxClusterTiles) return 0;
-    const int tiles = (n_total + kTile - 1) / kTile;
+    const int warps = (n_total + 31) / 32;
     for (int cl : {16, 8}) {
-        const int pc = (tiles + cl - 1) / cl * kTile;       // whole tiles per CTA
+        const int pc = (warps + cl - 1) / cl * 32;          // whole warps per CTA
         if (pc <= 4 * kCT) {
             *per_cta = pc;
             return cl;

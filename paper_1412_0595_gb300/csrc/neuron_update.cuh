@@ -84,7 +84,12 @@ __device__ __forceinline__ bool neuron_step(const DevPop& P, PhiloxKey key, uint
     const float I_syn = s.g0 * (P.E0 - V0) + s.g1 * (P.E1 - V0);
     const float I_in = I_syn + s.ie;
     const HHCell cell{P.gNa, P.ENa, P.gK, P.EK, P.gL, P.EL};
-    for (int k = 0; k < n_sub; ++k) hh_substep(cell, hs, P.hs_over_C, I_in, s.V, s.m, s.h, s.n);
+    if (n_sub == 4) {                                  // the usual count, unrolled so substeps overlap
+#pragma unroll
+        for (int k = 0; k < 4; ++k) hh_substep(cell, hs, P.hs_over_C, I_in, s.V, s.m, s.h, s.n);
+    } else {
+        for (int k = 0; k < n_sub; ++k) hh_substep(cell, hs, P.hs_over_C, I_in, s.V, s.m, s.h, s.n);
+    }
     s.g0 *= P.d0;
     s.g1 *= P.d1;
     s.ie *= P.drive_dec;

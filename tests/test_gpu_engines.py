@@ -30,7 +30,7 @@ def test_engine_choice(gpu):
 
 def test_options_read_back(gpu):
     net = gpu.Network.from_spec(I.config_four_pop(steps=1))
-    # 43 tiles of 256 neurons over 16 CTAs: 3 tiles (768 neurons) per CTA
+    # 43 tiles of 256 neurons (344 warps) over 16 CTAs: 22 warps (704 neurons) per CTA
     assert net.cluster_size == 16
     for name, value in (("persist_steps", 250), ("chunk", 512), ("graph_steps", 7), ("engine", 1), ("tiled", 0)):
         net.set_option(name, value)
