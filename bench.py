@@ -65,6 +65,8 @@ def _args():
     ap.add_argument("--batch-instances", type=int, default=512)
     ap.add_argument("--batch-steps", type=int, default=5000)
     ap.add_argument("--no-graded", action="store_true", help="skip the differentiable-form measurement")
+    ap.add_argument("--no-graded-dense", action="store_true",
+                    help="skip the differentiable form with dense storage and the rank-K weight-gradient update")
     ap.add_argument("--no-gscale", action="store_true", help="skip the gScale sweep and fit")
     ap.add_argument("--no-dense-batch", action="store_true",
                     help="skip the tensor-core dense delivery for batched instances")
@@ -72,7 +74,8 @@ def _args():
                     help="skip the occupancy-rule baseline (the paper's block sizing) beside the autotuned run")
     ap.add_argument("--no-scale-point", action="store_true",
                     help="skip the forced-activity propagation measurement at 100 x 1,000,000, p = 0.5")
-    ap.add_argument("--profile", choices=["cluster", "tiled", "dense", "neuron", "graded", "dense_batch"],
+    ap.add_argument("--profile", choices=["cluster", "tiled", "dense", "neuron", "graded", "dense_batch", "dense_grad",
+                                          "graded_dense"],
                     help="run a few launches of one kernel on its workload and exit (a target for ncu)")
     ap.add_argument("--record-traffic", nargs=3, metavar=("KERNEL", "BYTES", "COMMAND"),
                     help="store an ncu DRAM byte count per launch of KERNEL (with a hash of its sources) in "
@@ -287,6 +290,96 @@ def _differentiable(snn, torch, dev, steps=2000, K=100):
            "finite": bool(torch.isfinite(gs).all() and all(torch.isfinite(g).all() for g in gw))}
     net.close()
     return out
+
+
+def _differentiable_dense(snn, torch, dev, steps=2000, K=100):
+    """Differentiable form with dense storage (Eq. 2) of the middle
+    population's projections: In 100 -> Mid 4096 (compressed rows, p = 0.05),
+    Mid -> Mid and Mid -> Out dense.  Recorded forward, adjoint with the
+    weight gradient on the tensor cores and on the CUDA cores, and the 6
+    forward runs of a central difference over the 3 scales."""
+    spec = I.config_graded_dense(steps=steps)
+    net = snn.GradedNetwork.from_spec(spec, device=dev)
+    n_out = spec["pops"][-1]["n"]
+    target = torch.from_numpy(I.target_trace(spec, steps, n_out)).to(dev)
+    net.forward_record(target, checkpoint_every=K)
+    net.backward()
+    torch.cuda.synchronize()
+
+    def timed(fn):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        r = fn()
+        e1.record()
+        e1.synchronize()
+        return e0.elapsed_time(e1), r
+
+    t_f, loss = timed(lambda: net.forward_record(target, checkpoint_every=K))
+    net.set_option("dense_grad", 1)
+    t_bt, (gs, gw) = timed(net.backward)
+    net.set_option("dense_grad", 0)
+    net.forward_record(target, checkpoint_every=K)
+    t_bc, (gs_c, gw_c) = timed(net.backward)
+    net.set_option("dense_grad", 1)
+    t_fd, _ = timed(lambda: [net.forward_record(target, checkpoint_every=K) for _ in range(6)])
+    n_mid = spec["pops"][1]["n"]
+    dense_w = n_mid * n_mid + n_mid * n_out
+    peaks, _ = _peaks()
+    hbm = float(peaks.get("hbm_gbs", 6800.0))
+    fwd_gbs = 4.0 * dense_w * steps / (t_f * 1e-3) / 1e9
+    rel = [float(torch.linalg.norm(a - b) / torch.linalg.norm(b).clamp_min(1e-30)) for a, b in zip(gw, gw_c)]
+    out = {"workload": f"graded HH, dense storage: In 100 -> Mid {n_mid} (p = 0.05), Mid -> Mid and Mid -> Out dense, "
+                       f"{steps} steps of 0.05 ms",
+           "dense_weights": dense_w, "checkpoint_every": K, "loss": loss,
+           "forward_ms": t_f, "backward_tensor_ms": t_bt, "backward_cuda_core_ms": t_bc,
+           "six_forward_runs_ms": t_fd, "adjoint_vs_fd_speedup": t_fd / (t_f + t_bt),
+           "forward_dense_weight_stream_gbs": fwd_gbs, "forward_frac_hbm": fwd_gbs / hbm,
+           "weight_grad_rel_diff_tensor_vs_cuda_core": rel,
+           "finite": bool(torch.isfinite(gs).all() and all(torch.isfinite(g).all() for g in gw))}
+    net.close()
+    return out
+
+
+def _dense_grad(snn, torch, dev, reps=20):
+    """Rank-K weight-gradient update D += R^T N (one checkpoint segment of a
+    dense projection) on the tensor cores (three BF16 parts per operand, six
+    products) and on the CUDA cores.  Useful work 2 m n K FLOP; the tensor
+    cores execute 6 x 2 x mp x np x kp (padded to 128 / 128 / 32).  Bytes:
+    D read and written (8 m n) plus the operands (4 K (m + n))."""
+    peaks, src = _peaks()
+    bf16 = float(peaks.get("bf16_tflops", 1900.0))
+    hbm = float(peaks.get("hbm_gbs", 6800.0))
+    rng = np.random.default_rng(12)
+    out = []
+    for K, m, n in ((100, 4096, 4096), (512, 4096, 4096), (100, 20000, 100)):
+        R = torch.from_numpy(rng.uniform(0, 1, (K, m)).astype(np.float32)).to(dev)
+        N = torch.from_numpy(rng.normal(0, 1, (n, K)).astype(np.float32)).to(dev)
+        D = torch.zeros((m, n), dtype=torch.float32, device=dev)
+        h = snn.DenseGrad(device=dev)
+        row = {"K": K, "m": m, "n": n}
+        for eng in ("cuda", "tensor"):
+            h.run(R, N, D, engine=eng)
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            for _ in range(reps):
+                h.run(R, N, D, engine=eng)
+            e1.record()
+            e1.synchronize()
+            row[eng + "_us"] = 1e3 * e0.elapsed_time(e1) / reps
+        h.check()
+        h.close()
+        mp, np_, kp = -(-m // 128) * 128, -(-n // 128) * 128, -(-K // 32) * 32
+        row["tensor_executed_tflops"] = 6 * 2 * mp * np_ * kp / (row["tensor_us"] * 1e-6) / 1e12
+        row["tensor_frac_bf16_peak"] = row["tensor_executed_tflops"] / bf16
+        nbytes = 8.0 * m * n + 4.0 * K * (m + n)
+        row["tensor_gbs"] = nbytes / (row["tensor_us"] * 1e-6) / 1e9
+        row["tensor_frac_hbm"] = row["tensor_gbs"] / hbm
+        row["cuda_core_useful_tflops"] = 2.0 * m * n * K / (row["cuda_us"] * 1e-6) / 1e12
+        row["speedup_tensor_over_cuda"] = row["cuda_us"] / row["tensor_us"]
+        out.append(row)
+    return {"rows": out, "peak_bf16_tflops": bf16, "peak_hbm_gbs": hbm, "peak_source": src,
+            "traffic_4096x4096_K100": _traffic("k_dense_grad_mma")}
 
 
 def _dense_batch(snn, torch, dev, reps=20):
@@ -646,6 +739,10 @@ def run_ours(a):
     dense_batch = None
     if not a.no_dense_batch and rank == 0:
         dense_batch = _dense_batch(snn, torch, dev)
+    graded_dense = dense_grad = None
+    if not a.no_graded_dense and rank == 0:
+        graded_dense = _differentiable_dense(snn, torch, dev)
+        dense_grad = _dense_grad(snn, torch, dev)
     gscale_fit = gscale_izh = None
     if not a.no_gscale and rank == 0:
         gscale_fit = _gscale_procedure(dev)
@@ -677,6 +774,8 @@ def run_ours(a):
                 "batched": batched,
                 "differentiable": differentiable,
                 "dense_batch": dense_batch,
+                "differentiable_dense": graded_dense,
+                "dense_grad": dense_grad,
                 "gscale_fit": gscale_fit,
                 "gscale_fit_izhikevich": gscale_izh,
                 "gpu_launches": a.steps * ((-(-a.sim_steps // 1000)) + 2 if multi
@@ -789,7 +888,11 @@ def run_profile(a):
       graded:  the differentiable workload (20,000 middle neurons), 200 steps
                recorded forward and the adjoint;
       dense_batch: tensor-core delivery for 1024 instances sharing a 4096 x 4096
-               dense projection, half of the pre neurons spiking, three launches."""
+               dense projection, half of the pre neurons spiking, three launches;
+      dense_grad: the tensor-core rank-100 weight-gradient update of a 4096 x 4096
+               dense projection, three launches;
+      graded_dense: the dense differentiable workload (4096 middle neurons), 200
+               steps recorded forward and the adjoint."""
     import torch
 
     import paper_1412_0595_gb300 as snn
@@ -818,6 +921,23 @@ def run_profile(a):
         h.check()
         h.close()
         return
+    elif a.profile == "dense_grad":
+        rng = np.random.default_rng(12)
+        R = torch.from_numpy(rng.uniform(0, 1, (100, 4096)).astype(np.float32)).to(dev)
+        N = torch.from_numpy(rng.normal(0, 1, (4096, 100)).astype(np.float32)).to(dev)
+        D = torch.zeros((4096, 4096), dtype=torch.float32, device=dev)
+        h = snn.DenseGrad(device=dev)
+        for _ in range(3):
+            h.run(R, N, D, engine="tensor")
+        h.check()
+        h.close()
+        return
+    elif a.profile == "graded_dense":
+        spec = I.config_graded_dense(steps=200)
+        net = snn.GradedNetwork.from_spec(spec, device=dev)
+        target = torch.from_numpy(I.target_trace(spec, 200, spec["pops"][-1]["n"])).to(dev)
+        net.forward_record(target, checkpoint_every=100)
+        net.backward()
     elif a.profile == "neuron":
         net = snn.Network.from_spec(I.net([I.hh_pop(8_000_000)], [], dt=0.1, steps=1), device=dev)
         net.set_option("engine", 0)
@@ -839,7 +959,8 @@ _KERNEL_SOURCES = {
     "k_neuron_step": ["neuron.cu", "neuron_update.cuh", "device_math.cuh", "compaction.cuh", "snn_internal.cuh"],
     "k_propagate_tiled": ["propagate_tiled.cu", "snn_internal.cuh"],
     "k_propagate": ["propagate.cu", "snn_internal.cuh"],
-    "k_dense_batch_mma": ["dense_batch.cu", "snn_internal.cuh"],
+    "k_dense_batch_mma": ["dense_batch.cu", "tc_common.cuh", "snn_internal.cuh"],
+    "k_dense_grad_mma": ["graded_dense.cu", "tc_common.cuh", "snn_internal.cuh"],
 }
 
 

@@ -90,6 +90,9 @@ enum {
                                   recovers the network */
     SNN_OPT_CLUSTER_CTAS = 9,  /* read only (snn_get_option): CTAs of the cluster engine's plan,
                                   0 when the network does not fit one cluster */
+    SNN_OPT_DENSE_GRAD = 10,   /* weight gradient of dense graded projections in snn_backward:
+                                  0 CUDA cores (FP32 products), 1 tensor cores (default; three
+                                  BF16 parts of each operand, six products, FP32 accumulation) */
     SNN_OPT_TILED = 7          /* compressed-row propagation of the plain engine: 0 one warp per
                                   row chunk with global atomics, 1 post-tiled through shared
                                   memory, 2 choose (default: post-tiled when a row has
@@ -354,12 +357,44 @@ snn_status snn_dense_batch_deliver(snn_dense_batch* h, int32_t B, const int32_t*
  * SNN_ERR_INVALID_ARG (spike index out of range) or SNN_ERR_TIMEOUT. */
 snn_status snn_dense_batch_check(snn_dense_batch* h, void* stream);
 
+/* ---- weight gradient of a dense projection: rank-K update ---------------- */
+/* D[i][j] += sum over t < K of R[t][i] N[j][t] (i < m, j < n): the adjoint
+ * weight gradient of a dense graded projection (Eq. 2 storage) over one
+ * checkpoint segment of K steps, with R the segment's releases of the pre
+ * population (step-major) and N the segment's dL/dG of the posts
+ * (time-contiguous per post); snn_backward runs it for every dense
+ * projection.  On the tensor cores both operands are split into three BF16
+ * parts and the six products whose weight reaches 2^-24 of the result
+ * accumulate in FP32 in tensor memory (tcgen05), so D receives an FP32-
+ * accurate sum; the CUDA-core engine forms FP32 products directly. */
+typedef struct snn_dense_grad snn_dense_grad;
+
+/* A handle owning the operand-part scratch (grown on demand) and an error
+ * word; device memory through `alloc` (may be NULL: cudaMalloc). */
+snn_status snn_dense_grad_create(const snn_allocator* alloc, void* stream, snn_dense_grad** out);
+
+/* Frees the handle and its device memory (synchronises the device). */
+snn_status snn_dense_grad_destroy(snn_dense_grad* h);
+
+/* Enqueues one update on `stream`.  Device pointers: R[t * ldr + i]
+ * (ldr >= m), N[j * ldn + t] (ldn >= K), D[i * ldd + j] (ldd >= n),
+ * accumulated.  engine 0: CUDA cores, 1: tensor cores.  m, n >= 0,
+ * 0 <= K <= 512; SNN_ERR_INVALID_ARG otherwise.  A bounded wait that ran out
+ * is reported by snn_dense_grad_check. */
+snn_status snn_dense_grad_run(snn_dense_grad* h, const float* R, int64_t ldr, const float* N, int64_t ldn,
+                              int32_t m, int32_t n, int32_t K, float* D, int64_t ldd, int32_t engine, void* stream);
+
+/* Synchronises `stream` and reports a sticky kernel error of the handle
+ * (SNN_ERR_TIMEOUT). */
+snn_status snn_dense_grad_check(snn_dense_grad* h, void* stream);
+
 /* ---- parameters ----------------------------------------------------------- */
 /* Replaces the conductance scale s of projection `proj` (rounded to FP32). */
 snn_status snn_set_scale(snn_net* net, int32_t proj, double scale);
 
-/* Replaces the nnz weights (nS, compressed-row order) of projection `proj`
- * (compressed-row storage only), host or device.  Synchronises `stream`. */
+/* Replaces the weights of projection `proj`, host or device: the nnz weights
+ * (nS) in compressed-row order, or for dense storage the n_pre x n_post
+ * matrix in row-major order.  Synchronises `stream`. */
 snn_status snn_set_weights(snn_net* net, int32_t proj, const float* w, int32_t on_device, void* stream);
 
 /* ---- differentiable form (graded synapses) ---------------------------------

@@ -215,6 +215,16 @@ def dense_batch_deliver(W, spikes, scale, G0):
     return np.asarray(G0, np.float64) + np.asarray(scale, np.float64)[:, None] * (S @ W)
 
 
+def dense_grad_update(R, N, D0):
+    """Rank-K update of a dense weight gradient over a checkpoint segment, the
+    plain definition in FP64: D[i, j] = D0[i, j] + sum_t R[t, i] N[j, t]
+    (R: K x m releases, N: n x K dL/dG), i.e. D0 + R^T N^T (a library matrix
+    product as one step)."""
+    R = np.asarray(R, np.float64)
+    N = np.asarray(N, np.float64)
+    return np.asarray(D0, np.float64) + R.T @ N.T
+
+
 def set_threads(n):
     """Threads of the network step (timing only; 1 = the sequential step)."""
     lib().oracle_set_threads(int(n))

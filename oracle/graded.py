@@ -54,7 +54,8 @@ def hh_rate_derivs(V):
 
 class GradedOracle:
     """FP64 graded-synapse network: forward(T, target) -> loss, backward() ->
-    (dL/ds per projection, [dL/dw per projection in compressed-row order])."""
+    (dL/ds per projection, [dL/dw per projection in compressed-row order;
+    row-major n_pre x n_post for a dense projection])."""
 
     def __init__(self, spec, out_pop=None, tau_f=None, instance=None):
         import snn_inputs as I
@@ -83,8 +84,23 @@ class GradedOracle:
         self.rows = []
         for q, d in enumerate(spec["projs"]):
             n_pre, n_post = I.n_pre_post(spec, q)
-            rp, col = csr_bernoulli(spec["seed"], I.rng_tag(inst, q), n_pre, n_post, d["p"])
-            w = I.weights(spec, q, len(col)).astype(np.float64)
+            if d["layout"] == "dense":
+                # Eq. 2 storage: every (pre, post) pair is a weight, in row-major
+                # order (absent synapses of a thinned matrix are zeros); written
+                # as compressed rows that hold all pairs
+                if d["p"] >= 1.0:
+                    W = I.weights(spec, q, n_pre * n_post).astype(np.float64)
+                else:
+                    rp, col = csr_bernoulli(spec["seed"], I.rng_tag(inst, q), n_pre, n_post, d["p"])
+                    Wm = np.zeros((n_pre, n_post))
+                    Wm[np.repeat(np.arange(n_pre), np.diff(rp)), col] = I.weights(spec, q, len(col))
+                    W = Wm.ravel()
+                rp = np.arange(n_pre + 1, dtype=np.int64) * n_post
+                col = np.tile(np.arange(n_post, dtype=np.int32), n_pre)
+                w = np.ascontiguousarray(W, dtype=np.float64)
+            else:
+                rp, col = csr_bernoulli(spec["seed"], I.rng_tag(inst, q), n_pre, n_post, d["p"])
+                w = I.weights(spec, q, len(col)).astype(np.float64)
             keep += [rp, col, w]
             self.rows.append((rp, col, w))
             x = Q[q]
@@ -104,10 +120,13 @@ class GradedOracle:
         self.nnz = [len(r[1]) for r in self.rows]
 
     def __del__(self):
-        from . import lib
-        if getattr(self, "h", None):
-            lib().oracle_graded_destroy(self.h)
-            self.h = None
+        try:
+            from . import lib
+            if getattr(self, "h", None):
+                lib().oracle_graded_destroy(self.h)
+                self.h = None
+        except ImportError:        # interpreter shutdown: the process frees everything
+            pass
 
     def forward(self, target):
         from . import lib

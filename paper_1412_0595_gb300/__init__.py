@@ -8,6 +8,7 @@ C-ABI of ``include/snn.h``; importing this package fails if the library is
 missing (there is no CPU path).  PyTorch provides device memory and streams.
 """
 from ._lib import SNNError, lib  # noqa: F401  (loads the CUDA library or raises)
-from .network import DenseBatch, GradedNetwork, Network, SNNFunction, TorchAllocator, csr_bernoulli  # noqa: F401
+from .network import DenseBatch, DenseGrad, GradedNetwork, Network, SNNFunction, TorchAllocator, csr_bernoulli  # noqa: F401
 
-__all__ = ["Network", "GradedNetwork", "SNNFunction", "TorchAllocator", "csr_bernoulli", "SNNError", "lib"]
+__all__ = ["Network", "GradedNetwork", "SNNFunction", "DenseBatch", "DenseGrad", "TorchAllocator", "csr_bernoulli",
+           "SNNError", "lib"]

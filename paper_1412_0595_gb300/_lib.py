@@ -21,7 +21,7 @@ SYN_EXP, SYN_GRADED = 0, 1
 FIELD = {"V": 0, "m": 1, "h": 2, "n": 3, "g0": 4, "g1": 5, "iext": 6, "isyn": 7, "spikes": 8, "nspk": 9,
          "spike_count": 10, "nan_count": 11, "neuron_spikes": 12}
 OPT = {"record_isyn": 0, "graph_steps": 1, "prop_blocks": 2, "chunk": 3, "spin_limit": 4, "engine": 5,
-       "persist_steps": 6, "tiled": 7, "test_barrier_extra": 8, "cluster_ctas": 9}
+       "persist_steps": 6, "tiled": 7, "test_barrier_extra": 8, "cluster_ctas": 9, "dense_grad": 10}
 
 
 class PopDesc(C.Structure):
@@ -109,6 +109,10 @@ def _load():
         "snn_dense_batch_destroy": [vp],
         "snn_dense_batch_deliver": [vp, i32, vp, vp, vp, vp, i64, i32, vp],
         "snn_dense_batch_check": [vp, vp],
+        "snn_dense_grad_create": [P(Allocator), vp, P(vp)],
+        "snn_dense_grad_destroy": [vp],
+        "snn_dense_grad_run": [vp, vp, i64, vp, i64, i32, i32, i32, vp, i64, i32, vp],
+        "snn_dense_grad_check": [vp, vp],
     }
     for name, args in sig.items():
         f = getattr(L, name)

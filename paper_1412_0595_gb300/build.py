@@ -18,7 +18,7 @@ BUILD = PKG / "_build"
 LIB = BUILD / "libsnn.so"
 INCLUDE = ROOT / "include"
 
-SOURCES = ["api.cu", "neuron.cu", "propagate.cu", "csr.cu", "noalloc.cu", "persistent.cu", "propagate_tiled.cu", "tune.cu", "graded.cu", "graded_api.cu", "cluster.cu", "dense_batch.cu"]
+SOURCES = ["api.cu", "neuron.cu", "propagate.cu", "csr.cu", "noalloc.cu", "persistent.cu", "propagate_tiled.cu", "tune.cu", "graded.cu", "graded_api.cu", "cluster.cu", "dense_batch.cu", "graded_dense.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr",
          f"-I{INCLUDE}", f"-I{CSRC}"]

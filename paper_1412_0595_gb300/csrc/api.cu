@@ -793,6 +793,7 @@ snn_status snn_get_option(const snn_net* net, int32_t option, int64_t* value) {
     case SNN_OPT_TILED: *value = net->tiled; break;
     case SNN_OPT_TEST_BARRIER_EXTRA: *value = net->barrier_extra; break;
     case SNN_OPT_CLUSTER_CTAS: *value = net->cluster_size; break;
+    case SNN_OPT_DENSE_GRAD: *value = net->dense_grad; break;
     default: return fail(SNN_ERR_INVALID_ARG, "unknown option");
     }
     return SNN_OK;
@@ -837,6 +838,10 @@ snn_status snn_set_option(snn_net* net, int32_t option, int64_t value) {
     case SNN_OPT_PERSIST_STEPS:
         if (value < 1 || value > (1 << 24)) return fail(SNN_ERR_INVALID_ARG, "persistent steps in 1..2^24");
         net->persist_steps = (int32_t)value;
+        break;
+    case SNN_OPT_DENSE_GRAD:
+        if (value < 0 || value > 1) return fail(SNN_ERR_INVALID_ARG, "dense gradient: 0 CUDA cores, 1 tensor cores");
+        net->dense_grad = (int32_t)value;
         break;
     default: return fail(SNN_ERR_INVALID_ARG, "unknown option");
     }

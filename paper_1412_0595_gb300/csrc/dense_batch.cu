@@ -22,8 +22,8 @@
 // tile: 3 K steps x 3 parts x 2 row tiles, the W tiles shared by both) into
 // two 128-column FP32 accumulators in tensor memory; tcgen05.commit
 // releases a stage when its MMAs are done.  The eight
-// warps then read the accumulators with tcgen05.ld (warp w owns lanes
-// 32 (w % 4) .. + 31 of accumulator w / 4) and add s_b times them to G.  When
+// warps then read each accumulator with tcgen05.ld into shared memory and add
+// s_b times its rows to G, lanes along a row (contiguous global accesses).  When
 // the output has few tiles the K range is split over CTAs (split-K), which
 // then add with atomics.  Every wait is bounded: a wait that runs out sets
 // the sticky timeout bit, and the CTA still waits (bounded) for its copies
@@ -33,9 +33,8 @@
 #include <string>
 #include <vector>
 
-#include <cuda_bf16.h>
-
 #include "snn_internal.cuh"
+#include "tc_common.cuh"
 
 namespace {
 
@@ -50,20 +49,12 @@ constexpr int kThreadsMma = 256;
 
 static_assert(kTN == kTM, "S and W tiles share one tile shape");
 
-__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+using namespace snn::tc;
 
 // Element offset of (row, k) inside the tiled K-major layout with `kt` K tiles per row band.
 __host__ __device__ __forceinline__ int64_t tiled_offset(int64_t row, int64_t k, int64_t kt) {
-    const int64_t tile = (row / kTM) * kt + k / kTK;
-    const int r = (int)(row % kTM), c = (int)(k % kTK);
-    return tile * kTileElems + ((r >> 3) * (kTK / 8) + (c >> 3)) * 64 + (r & 7) * 8 + (c & 7);
+    return snn::tc::tiled_offset(row, k, kt, kTK);
 }
-
-__device__ __forceinline__ uint16_t bf16_rn(float x) {
-    return __bfloat16_as_ushort(__float2bfloat16_rn(x));
-}
-
-__device__ __forceinline__ float bf16_to_f(uint16_t h) { return __bfloat162float(__ushort_as_bfloat16(h)); }
 
 // W (n_pre x n_post, row-major FP32) -> three BF16 parts of W^T (post-major),
 // tiled; zero padding up to (np, kp).
@@ -73,10 +64,8 @@ __global__ void k_split_weights(const float* W, int32_t n_pre, int32_t n_post, i
     for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
         const int64_t n = e / kp, k = e % kp;
         const float w = (n < n_post && k < n_pre) ? W[k * n_post + n] : 0.0f;
-        const uint16_t hi = bf16_rn(w);
-        const float r1 = w - bf16_to_f(hi);
-        const uint16_t mid = bf16_rn(r1);
-        const uint16_t lo = bf16_rn(r1 - bf16_to_f(mid));
+        uint16_t hi, mid, lo;
+        split3(w, hi, mid, lo);
         const int64_t o = tiled_offset(n, k, kt);
         parts[o] = hi;
         parts[total + o] = mid;
@@ -106,51 +95,7 @@ __global__ void k_build_spikes(const int32_t* spk_off, const int32_t* spk, int32
     }
 }
 
-__device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
-    uint32_t done;
-    asm volatile(
-        "{\n\t.reg .pred p;\n\t"
-        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-        "selp.u32 %0, 1, 0, p;\n\t}"
-        : "=r"(done) : "r"(bar), "r"(parity) : "memory");
-    return done != 0;
-}
-
-__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, uint32_t limit) {
-    for (uint32_t it = 0; it < limit; ++it)
-        if (mbar_try_wait(bar, parity)) return true;
-    return false;
-}
-
-__device__ __forceinline__ void bulk_copy(void* dst, const void* src, uint32_t bytes, uint32_t bar) {
-    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
-                 ::"r"(smem_u32(dst)), "l"(src), "r"(bytes), "r"(bar) : "memory");
-}
-
-// Shared-memory matrix descriptor, K-major, no swizzle: start address, the
-// byte distance between core matrices along K (leading) and along M/N
-// (stride), descriptor version 1.
-__device__ __forceinline__ uint64_t smem_desc(uint32_t addr, uint32_t lbo, uint32_t sbo) {
-    return (uint64_t)((addr >> 4) & 0x3FFFu) | ((uint64_t)((lbo >> 4) & 0x3FFFu) << 16) |
-           ((uint64_t)((sbo >> 4) & 0x3FFFu) << 32) | (1ull << 46);
-}
-
-// Instruction descriptor of kind::f16: FP32 accumulator, BF16 A and B, both
-// K-major, N = 128, M = 128.
-constexpr uint32_t kIdesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(kTN >> 3) << 17) |
-                            ((uint32_t)(kTM >> 4) << 24);
-
-__device__ __forceinline__ void mma_bf16(uint32_t tmem, uint64_t a, uint64_t b, uint32_t accumulate) {
-    asm volatile(
-        "{\n\t.reg .pred p;\n\t"
-        "setp.ne.b32 p, %4, 0;\n\t"
-        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}"
-        ::"r"(tmem), "l"(a), "l"(b), "r"(kIdesc), "r"(accumulate) : "memory");
-}
-
-__device__ __forceinline__ void mma_commit(uint32_t bar) {
-    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar) : "memory");
-}
+constexpr uint32_t kIdesc = idesc_bf16(kTM, kTN);
 
 __global__ void __launch_bounds__(kThreadsMma, 1)
     k_dense_batch_mma(const uint16_t* __restrict__ S, const uint16_t* __restrict__ parts, int64_t np, int64_t kp,
@@ -224,7 +169,7 @@ __global__ void __launch_bounds__(kThreadsMma, 1)
                     const uint64_t db = smem_desc(smem_u32(stage_ptr(st, 2 + p)) + ks * 256, 128, kSbo);
                     for (int h = 0; h < 2; ++h) {
                         const uint64_t da = smem_desc(smem_u32(stage_ptr(st, h)) + ks * 256, 128, kSbo);
-                        mma_bf16(tmem + (uint32_t)(h * kTN), da, db, (i | ks | p) != 0);
+                        mma_bf16(tmem + (uint32_t)(h * kTN), da, db, kIdesc, (i | ks | p) != 0);
                     }
                 }
             mma_commit(smem_u32(&s_done[st]));
@@ -253,33 +198,23 @@ __global__ void __launch_bounds__(kThreadsMma, 1)
 
     __syncwarp();                                         // tcgen05.ld is warp-collective
     if (!s_fail) {
-        // warp w reads lanes 32 (w % 4) .. + 31 of accumulator w / 4:
-        // instance b = 128 (2 mt2 + w / 4) + 32 (w % 4) + lane
-        const int q = warp & 3, h = warp >> 2;
-        const int b = (2 * mt2 + h) * kTM + q * 32 + lane;
-        const float sb = b < B ? scale[b] : 0.0f;
-        for (int c0 = 0; c0 < kTN; c0 += 32) {
-            uint32_t v[32];
-            const uint32_t taddr = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(h * kTN + c0);
-            asm volatile(
-                "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
-                "{%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, "
-                "%16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
-                : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
-                  "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]),
-                  "=r"(v[15]), "=r"(v[16]), "=r"(v[17]), "=r"(v[18]), "=r"(v[19]), "=r"(v[20]), "=r"(v[21]),
-                  "=r"(v[22]), "=r"(v[23]), "=r"(v[24]), "=r"(v[25]), "=r"(v[26]), "=r"(v[27]), "=r"(v[28]),
-                  "=r"(v[29]), "=r"(v[30]), "=r"(v[31])
-                : "r"(taddr));
-            asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-            if (b < B) {
-                float* g = G + (int64_t)b * ldg + (int64_t)nt * kTN + c0;
-                const int lim = min(32, n_post - (nt * kTN + c0));
-                if (split)
-                    for (int j = 0; j < lim; ++j) atomicAdd(g + j, sb * __uint_as_float(v[j]));
-                else
-                    for (int j = 0; j < lim; ++j) g[j] += sb * __uint_as_float(v[j]);
+        // every copy has landed and every MMA is done: the stages hold the
+        // transposition tile; accumulator h covers instances 128 (2 mt2 + h) ..
+        float* st = reinterpret_cast<float*>(s_raw);
+        const int64_t j0 = (int64_t)nt * kTN;
+        const int cols = (int)(n_post - j0 < kTN ? n_post - j0 : kTN);
+        const bool vec = (ldg & 3) == 0 && (reinterpret_cast<uintptr_t>(G) & 15) == 0;
+        for (int h = 0; h < 2; ++h) {
+            const int64_t b0 = (int64_t)(2 * mt2 + h) * kTM;
+            const int64_t left = (int64_t)B - b0;
+            const int rows = (int)(left <= 0 ? 0 : (left < kTM ? left : kTM));
+            tmem_tile_to_smem(tmem + (uint32_t)(h * kTN), st, warp, lane);
+            __syncthreads();
+            if (rows > 0) {
+                if (split) smem_tile_to_global<true>(st, G + b0 * ldg + j0, ldg, rows, cols, scale + b0, vec, warp, lane);
+                else smem_tile_to_global<false>(st, G + b0 * ldg + j0, ldg, rows, cols, scale + b0, vec, warp, lane);
             }
+            __syncthreads();                              // the tile is read before the next one is written
         }
     }
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");

@@ -153,6 +153,7 @@ __global__ void __launch_bounds__(kShared ? kStagedThreads : kThreads, kShared ?
         int q = 0;
         while (a.gprojs[q].g_off + a.gprojs[q].n_post <= w) ++q;
         const GradProj& Q = a.gprojs[q];
+        if (Q.dense) continue;                       // dense projections have their own product
         const int j = (int)(w - Q.g_off);
         float acc = lane_dot<kShared>(Q.csc_w, Q.csc_pre, x + Q.pre_off, Q.csc_ptr[j], Q.csc_ptr[j + 1], lane);
 #pragma unroll
@@ -324,6 +325,24 @@ __global__ void __launch_bounds__(kThreads) k_graded_gather(const GradedArgs a, 
         for (int k = a.out_begin[pop]; k < a.out_begin[pop + 1]; ++k) {
             const GradProj& q = a.gprojs[a.out_list[k]];
             const float* nu = b.nu_step + q.g_off;
+            if (q.dense) {
+                // the neuron's row of the matrix against dL/dG of all posts
+                const float* row = q.w + (int64_t)local * q.n_post;
+                if ((q.n_post & 3) == 0 && (q.g_off & 3) == 0) {
+#pragma unroll 4
+                    for (int j = 4 * lane; j < q.n_post; j += 128) {
+                        const float4 w4 = __ldcs(reinterpret_cast<const float4*>(row + j));
+                        const float4 v4 = *reinterpret_cast<const float4*>(nu + j);
+                        acc = fmaf(w4.x, v4.x, acc);
+                        acc = fmaf(w4.y, v4.y, acc);
+                        acc = fmaf(w4.z, v4.z, acc);
+                        acc = fmaf(w4.w, v4.w, acc);
+                    }
+                } else {
+                    for (int j = lane; j < q.n_post; j += 32) acc = fmaf(row[j], nu[j], acc);
+                }
+                continue;
+            }
             for (int64_t e = q.row_ptr[local] + lane; e < q.row_ptr[local + 1]; e += 32)
                 acc = fmaf(q.w[e], nu[q.col[e]], acc);
         }

@@ -48,12 +48,20 @@ GradedArgs graded_args(snn_net* net) {
     return a;
 }
 
-// One time step: graded conductances from the current releases, then the
+// One time step: graded conductances from the current releases (the sparse
+// projections in one launch, each dense projection in its own), then the
 // neuron update.  `G` receives the step's G vector.
 cudaError_t graded_one_step(snn_net* net, GradedArgs a, float* G, int64_t t, cudaStream_t s) {
     a.G = G;
     a.t_rng = (uint32_t)t;
     cudaError_t e = launch_graded_spmv(a, s);
+    for (size_t q = 0; q < net->projs.size() && e == cudaSuccess; ++q) {
+        const ProjHost& P = net->projs[q];
+        if (P.d.layout != SNN_LAYOUT_DENSE) continue;
+        const PopHost& pre = net->pops[P.d.pre];
+        e = launch_graded_dense_fwd(P.w, a.r + pre.offset, pre.d.n, net->pops[P.d.post].d.n, G + P.g_off, P.dpart,
+                                    P.dld, P.dcount, P.dchunks, s);
+    }
     if (e == cudaSuccess) e = launch_graded_neuron(a, s);
     return e;
 }
@@ -80,6 +88,7 @@ snn_status upload_gprojs(snn_net* net) {
         d.csc_ptr = P.csc_ptr;
         d.csc_pre = P.csc_pre;
         d.csc_w = P.csc_w;
+        d.dense = P.d.layout == SNN_LAYOUT_DENSE ? 1 : 0;
     }
     if (!g.empty())
         SNN_CK(cudaMemcpy(net->d_gprojs, g.data(), g.size() * sizeof(GradProj), cudaMemcpyHostToDevice),
@@ -101,8 +110,8 @@ snn_status graded_setup(snn_net* net, cudaStream_t s) {
     std::vector<int> seen((size_t)np, 0);
     for (int q = 0; q < nq; ++q) {
         const snn_proj_desc& d = net->projs[q].d;
-        if (d.synapse != SNN_SYN_GRADED || d.layout != SNN_LAYOUT_CSR)
-            return fail(SNN_ERR_INVALID_ARG, "a graded network takes only graded compressed-row projections");
+        if (d.synapse != SNN_SYN_GRADED)
+            return fail(SNN_ERR_INVALID_ARG, "a graded network takes only graded projections");
         if (!(d.v_slope > 0) || !std::isfinite(d.v_thr))
             return fail(SNN_ERR_INVALID_ARG, "graded projection needs v_slope > 0 and finite v_thr");
         if (seen[d.pre] && (thr[d.pre] != d.v_thr || slope[d.pre] != d.v_slope))
@@ -119,6 +128,19 @@ snn_status graded_setup(snn_net* net, cudaStream_t s) {
     for (int q = 0; q < nq; ++q) {
         ProjHost& P = net->projs[q];
         const int32_t n_pre = net->pops[P.d.pre].d.n, n_post = net->pops[P.d.post].d.n;
+        if (P.d.layout == SNN_LAYOUT_DENSE) {
+            // the matrix itself serves both directions; the forward product's
+            // partial rows and per post block tickets
+            P.dchunks = dense_fwd_chunks(n_pre, n_post, net->sm_count);
+            P.dld = ((int64_t)n_post + 3) / 4 * 4;
+            const size_t blocks = ((size_t)n_post + 127) / 128;
+            SNN_TRY(net_alloc(net, &P.dpart, std::max<size_t>(1, (size_t)P.dchunks * P.dld), "dense partial rows"));
+            SNN_TRY(net_alloc(net, &P.dcount, std::max<size_t>(1, blocks), "dense tickets"));
+            SNN_CK(cudaMemsetAsync(P.dcount, 0, std::max<size_t>(1, blocks) * sizeof(unsigned), s), "clear");
+            P.g_off = g_off;
+            g_off += n_post;
+            continue;
+        }
         std::vector<int64_t> rp((size_t)n_pre + 1);
         std::vector<int32_t> col((size_t)P.nnz);
         std::vector<float> w((size_t)P.nnz);
@@ -231,6 +253,23 @@ snn_status ensure_segment_buffers(snn_net* net, int32_t K, int32_t n_out) {
     SNN_TRY(net_alloc(net, &net->nu_step, G, "step dL/dG"));
     SNN_TRY(net_alloc(net, &net->nu_km, G * kp, "segment dL/dG"));
     SNN_TRY(net_alloc(net, &net->adj, 6 * NT, "adjoints"));
+    // operand parts of the tensor-core weight gradient, sized for the largest dense projection
+    size_t need_a = 0, need_b = 0;
+    for (const auto& P : net->projs) {
+        if (P.d.layout != SNN_LAYOUT_DENSE) continue;
+        int64_t mp, np, kpg;
+        dense_grad_sizes(net->pops[P.d.pre].d.n, net->pops[P.d.post].d.n, K, &mp, &np, &kpg);
+        need_a = std::max(need_a, (size_t)(3 * mp * kpg));
+        need_b = std::max(need_b, (size_t)(3 * np * kpg));
+    }
+    if (need_a > net->grad_A_cap) {
+        SNN_TRY(net_alloc(net, &net->grad_A, need_a, "gradient operand parts"));
+        net->grad_A_cap = need_a;
+    }
+    if (need_b > net->grad_B_cap) {
+        SNN_TRY(net_alloc(net, &net->grad_B, need_b, "gradient operand parts"));
+        net->grad_B_cap = need_b;
+    }
     (void)n_out;
     net->seg_cap_K = K;
     return SNN_OK;
@@ -254,12 +293,13 @@ snn_status snn_set_scale(snn_net* net, int32_t proj, double scale) {
 snn_status snn_set_weights(snn_net* net, int32_t proj, const float* w, int32_t on_device, void* stream) {
     if (!net || !w || proj < 0 || proj >= (int32_t)net->projs.size()) return fail(SNN_ERR_INVALID_ARG, "bad argument");
     ProjHost& P = net->projs[proj];
-    if (P.d.layout != SNN_LAYOUT_CSR) return fail(SNN_ERR_INVALID_ARG, "weights of dense storage are set at creation");
     cudaStream_t s = (cudaStream_t)stream;
+    // compressed rows: nnz weights in row order; dense storage: the n_pre x n_post matrix
     if (P.nnz)
         SNN_CK(cudaMemcpyAsync(P.w, w, sizeof(float) * P.nnz, on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
                                s), "copy weights");
-    if (net->graded) SNN_CK(launch_scatter_csc(P.w, P.csc_perm, P.csc_w, P.nnz, s), "transposed weights");
+    if (net->graded && P.d.layout == SNN_LAYOUT_CSR)
+        SNN_CK(launch_scatter_csc(P.w, P.csc_perm, P.csc_w, P.nnz, s), "transposed weights");
     SNN_CK(cudaStreamSynchronize(s), "synchronize");
     return SNN_OK;
 }
@@ -385,8 +425,29 @@ snn_status snn_backward(snn_net* net, float* grad_scale, float* const* grad_w, v
             b.tl = tl;
             SNN_CK(launch_graded_reverse(r, b, s), "reverse step");
         }
-        for (int q = 0; q < nq; ++q)
-            SNN_CK(launch_graded_sddmm(a, b, q, net->pops[net->projs[q].d.pre].d.n, grad_w[q], L, s), "weight gradients");
+        for (int q = 0; q < nq; ++q) {
+            const ProjHost& P = net->projs[q];
+            if (P.d.layout == SNN_LAYOUT_DENSE) {
+                DenseGradArgs g{};
+                g.R = net->seg_r + net->pops[P.d.pre].offset;     // releases of the pre population
+                g.ldr = (int64_t)NT;
+                g.N = net->nu_km + (size_t)P.g_off * kp;           // dL/dG of the projection's posts
+                g.ldn = kp;
+                g.m = net->pops[P.d.pre].d.n;
+                g.n = net->pops[P.d.post].d.n;
+                g.L = L;
+                g.D = grad_w[q];
+                g.ldd = g.n;
+                g.engine = net->dense_grad;
+                g.A = net->grad_A;
+                g.B = net->grad_B;
+                g.error = net->error;
+                g.spin_limit = net->spin_limit;
+                SNN_CK(launch_dense_grad(g, s), "dense weight gradients");
+            } else {
+                SNN_CK(launch_graded_sddmm(a, b, q, net->pops[P.d.pre].d.n, grad_w[q], L, s), "weight gradients");
+            }
+        }
     }
     SNN_CK(launch_finish_grad_scale(net->d_grad_scale, grad_scale, nq, s), "scale gradients");
     SNN_CK(cudaStreamSynchronize(s), "synchronize");

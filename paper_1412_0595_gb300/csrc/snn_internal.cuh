@@ -102,6 +102,7 @@ struct GradProj {
     const int64_t* csc_ptr;            // transposed copy (post-major)
     const int32_t* csc_pre;
     const float* csc_w;
+    int32_t dense;                     // 1: w is the n_pre x n_post matrix (no row / column arrays)
 };
 
 struct GradedArgs {
@@ -143,6 +144,23 @@ struct AdjArgs {
     float* nu_km;                      // [G][kp] dL/dG of the segment, time-contiguous
     int32_t kp, tl;
     double* grad_scale;
+};
+
+// One rank-L update D[i][j] += sum_{t < L} R[t][i] N[j][t] (i < m, j < n):
+// the weight gradient of a dense graded projection over a segment, with R
+// the segment's releases of the pre population and N its dL/dG.
+struct DenseGradArgs {
+    const float* R;                    // R[t * ldr + i]
+    int64_t ldr;
+    const float* N;                    // N[j * ldn + t]
+    int64_t ldn;
+    int32_t m, n, L;
+    float* D;                          // D[i * ldd + j]
+    int64_t ldd;
+    int32_t engine;                    // 0 CUDA cores, 1 tensor cores
+    uint16_t *A, *B;                   // tensor cores: operand parts (dense_grad_sizes)
+    uint32_t* error;
+    uint32_t spin_limit;
 };
 
 struct NeuronArgs {
@@ -201,6 +219,10 @@ struct ProjHost {
     int32_t* csc_pre = nullptr;
     float* csc_w = nullptr;
     int64_t* csc_perm = nullptr;   // transposed position -> compressed-row position
+    float* dpart = nullptr;        // graded dense: partial rows of the forward product
+    unsigned* dcount = nullptr;    // graded dense: per post block ticket
+    int32_t dchunks = 1;           // graded dense: pre-row ranges of the forward product
+    int64_t dld = 0;               // graded dense: row stride of dpart
     int64_t g_off = 0;
     float scale;
     int64_t nnz;
@@ -267,6 +289,9 @@ struct snn_net {
     float *nu_step = nullptr, *nu_km = nullptr;
     float *adj = nullptr;                     // lV, lV_loc, lm, lh, ln (5 * n_total) + ly (n_total)
     int32_t seg_cap_K = 0;
+    uint16_t *grad_A = nullptr, *grad_B = nullptr;   // operand parts of the dense weight gradient
+    size_t grad_A_cap = 0, grad_B_cap = 0;
+    int32_t dense_grad = 1;                   // dense weight gradient: 0 CUDA cores, 1 tensor cores
     unsigned long long* counters = nullptr;   // 2 * n_pops
     unsigned long long* ticket = nullptr;     // [0] ticket, [1] epoch base
     int32_t* tile_pop = nullptr;
@@ -355,6 +380,11 @@ cudaError_t launch_graded_sddmm(const GradedArgs& a, const AdjArgs& b, int q, in
                                 cudaStream_t s);
 cudaError_t launch_scatter_csc(const float* w_csr, const int64_t* perm, float* w_csc, int64_t nnz, cudaStream_t s);
 cudaError_t launch_finish_grad_scale(const double* acc, float* out, int n, cudaStream_t s);
+int dense_fwd_chunks(int32_t n_pre, int32_t n_post, int sm_count);
+cudaError_t launch_graded_dense_fwd(const float* W, const float* x, int32_t n_pre, int32_t n_post, float* Gq,
+                                    float* part, int64_t ld_part, unsigned* count, int32_t chunks, cudaStream_t s);
+void dense_grad_sizes(int32_t n_pre, int32_t n_post, int32_t K, int64_t* mp, int64_t* np, int64_t* kp);
+cudaError_t launch_dense_grad(const DenseGradArgs& g, cudaStream_t s);
 cudaError_t launch_persistent(const PersistArgs& a, int grid, cudaStream_t s);
 cudaError_t launch_set_epoch_base(unsigned long long* ticket, int num_tiles, cudaStream_t s);
 

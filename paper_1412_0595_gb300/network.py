@@ -517,3 +517,44 @@ class DenseBatch:
         except Exception:
             pass
 
+
+class DenseGrad:
+    """Rank-K update D += R^T N (``snn_dense_grad_*``): the weight gradient of
+    a dense graded projection over a checkpoint segment, R (K x m, step-major)
+    the releases and N (n x K, time-contiguous) dL/dG.  Engine "tensor": three
+    BF16 parts per operand, six tensor-core products, FP32 accumulation;
+    engine "cuda": FP32 products on the CUDA cores."""
+
+    ENGINES = {"cuda": 0, "tensor": 1}
+
+    def __init__(self, device=None, stream=None):
+        self.device = torch.device("cuda") if device is None else torch.device(device)
+        self._alloc = TorchAllocator(self.device.index)
+        h = C.c_void_p()
+        check(L.lib.snn_dense_grad_create(self._alloc.ref(), _stream(stream), C.byref(h)))
+        self.h = h
+
+    def run(self, R, N, D, engine="tensor", stream=None):
+        """D[i, j] += sum_t R[t, i] N[j, t]; CUDA FP32 tensors with unit
+        stride in their last dimension."""
+        for t in (R, N, D):
+            assert t.is_cuda and t.dtype == torch.float32 and t.dim() == 2 and t.stride(1) == 1
+        K, m = R.shape
+        n = N.shape[0]
+        assert N.shape[1] == K and tuple(D.shape) == (m, n)
+        check(L.lib.snn_dense_grad_run(self.h, R.data_ptr(), int(R.stride(0)), N.data_ptr(), int(N.stride(0)), m, n, K,
+                                       D.data_ptr(), int(D.stride(0)), self.ENGINES[engine], _stream(stream)))
+
+    def check(self, stream=None):
+        check(L.lib.snn_dense_grad_check(self.h, _stream(stream)))
+
+    def close(self):
+        if getattr(self, "h", None):
+            L.lib.snn_dense_grad_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

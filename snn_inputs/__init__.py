@@ -187,12 +187,34 @@ def config_graded_small(steps=2000, recurrent=True, seed=SEED):
                          recurrent=recurrent, seed=seed)
 
 
+def config_graded_dense(n_in=100, n_mid=4096, n_out=100, p_in=0.05, steps=2000, dt=0.05,
+                        weights=GRADED_WEIGHTS, seed=SEED):
+    """The graded workload with dense storage (Eq. 2) for the middle
+    population's projections: In -> Mid compressed rows at p_in; Mid -> Mid
+    and Mid -> Out dense (every pair a weight, p = 1, nConn = N_mid, so the
+    mean drive per post matches the sparse form's)."""
+    pops = [hh_pop(n_in, drive=dict(INPUT_DRIVE)), hh_pop(n_mid), hh_pop(n_out)]
+    w = [("uniform", 0.0, float(x)) for x in weights]
+    projs = [proj(0, 1, "csr", p_in, w[0]), proj(1, 1, "dense", 1.0, w[1]), proj(1, 2, "dense", 1.0, w[2])]
+    for d in projs:
+        d.update(synapse="graded", v_thr=GRADED["v_thr"], v_slope=GRADED["v_slope"])
+    return net(pops, projs, dt=dt, steps=steps, seed=seed,
+               name=f"graded_dense_in{n_in}_mid{n_mid}_out{n_out}")
+
+
+def config_graded_dense_small(steps=2000, n_mid=160, seed=SEED):
+    """200-neuron copy of the dense form: In 20 / Mid 160 / Out 20, In -> Mid
+    at p = 0.25."""
+    return config_graded_dense(n_in=20, n_mid=n_mid, n_out=20, p_in=0.25, steps=steps, seed=seed)
+
+
 CONFIGS = {
     "small": config_small,
     "four_pop": config_four_pop,
     "sweep": config_sweep,
     "batched": config_batched,
     "graded": config_graded,
+    "graded_dense": config_graded_dense,
 }
 
 

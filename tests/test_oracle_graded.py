@@ -165,3 +165,45 @@ def test_finite_difference_error_shrinks_with_the_step():
         g.set_scale(0, s0)
         errs.append(abs((lp - lm) / (2 * h) - gs[0]) / abs(gs[0]))
     assert errs[0] > errs[1] > errs[2] and errs[3] < 1e-4
+
+
+def test_dense_storage_adjoint_matches_central_differences():
+    # the smooth network with dense (Eq. 2) storage of all three projections:
+    # every (pre, post) pair is a parameter, gradients in row-major order
+    pops = [I.hh_pop(12, v0_range=(-26.0, -14.0)), _passive(18), _passive(6)]
+    pops[0]["hh"]["C"] = 1e300
+    for d in pops[1:]:
+        d["v0_range"] = (-64.0, -60.0)
+    projs = [_graded_proj(0, 1, 0.0), _graded_proj(1, 1, 0.0), _graded_proj(1, 2, 0.0)]
+    for d, wmax in zip(projs, (5.0, 1.0, 5.0)):
+        d["layout"] = "dense"
+        d["weight"] = ("uniform", 0.0, wmax)
+    projs[1]["v_thr"] = projs[2]["v_thr"] = -62.0
+    spec = I.net(pops, projs, dt=0.05, steps=1)
+    g = GradedOracle(spec)
+    assert g.nnz == [12 * 18, 18 * 18, 18 * 6]
+    target = I.target_trace(spec, 400, g.n_out).astype(np.float64)
+    worst, gs = _fd_check(g, target, scale_step=1e-3, weight_step=1e-3)
+    assert np.all(np.abs(gs) > 1e-3)
+    assert worst < 1e-5
+
+
+def test_dense_storage_equals_compressed_rows_of_the_same_matrix():
+    # a thinned dense projection (p < 1) is the compressed-row projection with
+    # zeros filled in: same loss, and the dense gradient restricted to the
+    # stored synapses is the compressed-row gradient
+    spec_c = I.config_graded_small(steps=300)
+    spec_d = I.config_graded_small(steps=300)
+    spec_d["projs"][2]["layout"] = "dense"
+    gc, gd = GradedOracle(spec_c), GradedOracle(spec_d)
+    target = I.target_trace(spec_c, 300, gc.n_out).astype(np.float64)
+    lc, _ = gc.forward(target)
+    ld, _ = gd.forward(target)
+    assert ld == pytest.approx(lc, rel=1e-12)
+    gsc, gwc = gc.backward()
+    gsd, gwd = gd.backward()
+    assert np.allclose(gsd, gsc, rtol=1e-10, atol=0)
+    rp, col, _ = gc.rows[2]
+    n_post = spec_c["pops"][2]["n"]
+    rows = np.repeat(np.arange(len(rp) - 1), np.diff(rp))
+    assert np.allclose(gwd[2][rows * n_post + col], gwc[2], rtol=1e-10, atol=1e-300)

@@ -152,3 +152,23 @@ def test_dense_batch_oracle_matches_per_instance_delivery():
         net.set(1, "g0", G0[b])
         net.deliver(0, spikes[b].astype(np.int32))
         assert np.allclose(net.get(1, "g0"), G[b], rtol=1e-14, atol=1e-14)
+
+
+def test_dense_grad_update_brute_force_and_closed_forms():
+    # D[i, j] = D0[i, j] + sum_t R[t, i] N[j, t]: element-by-element loops on a
+    # small case, a K = 1 outer product, and all-ones operands (D0 + K)
+    rng = np.random.default_rng(9)
+    K, m, n = 5, 4, 3
+    R = rng.normal(size=(K, m))
+    N = rng.normal(size=(n, K))
+    D0 = rng.normal(size=(m, n))
+    D = oracle.dense_grad_update(R, N, D0)
+    for i in range(m):
+        for j in range(n):
+            s = D0[i, j]
+            for t in range(K):
+                s += R[t, i] * N[j, t]
+            assert D[i, j] == pytest.approx(s, rel=1e-13, abs=1e-13)
+    r, v = rng.normal(size=(1, m)), rng.normal(size=(n, 1))
+    assert np.allclose(oracle.dense_grad_update(r, v, np.zeros((m, n))), np.outer(r[0], v[:, 0]), rtol=1e-15, atol=0)
+    assert np.array_equal(oracle.dense_grad_update(np.ones((7, m)), np.ones((n, 7)), D0), D0 + 7.0)
