@@ -375,6 +375,11 @@ snn_status create_impl(const snn_pop_desc* pops, int32_t n_pops, const snn_proj_
     int dev = 0;
     CK(cudaGetDevice(&dev), "get device");
     CK(cudaDeviceGetAttribute(&net->sm_count, cudaDevAttrMultiProcessorCount, dev), "SM count");
+    {
+        int l2 = 0;
+        CK(cudaDeviceGetAttribute(&l2, cudaDevAttrL2CacheSize, dev), "L2 size");
+        net->l2_bytes = l2;
+    }
 
     // ---- structure-of-arrays layout: populations padded to whole tiles ----
     int64_t off = 0, tiles = 0;

@@ -331,7 +331,7 @@ __global__ void __launch_bounds__(kThreads) k_graded_gather(const GradedArgs a, 
                 if ((q.n_post & 3) == 0 && (q.g_off & 3) == 0) {
 #pragma unroll 4
                     for (int j = 4 * lane; j < q.n_post; j += 128) {
-                        const float4 w4 = __ldcs(reinterpret_cast<const float4*>(row + j));
+                        const float4 w4 = __ldg(reinterpret_cast<const float4*>(row + j));   // may stay in L2
                         const float4 v4 = *reinterpret_cast<const float4*>(nu + j);
                         acc = fmaf(w4.x, v4.x, acc);
                         acc = fmaf(w4.y, v4.y, acc);

@@ -60,7 +60,7 @@ cudaError_t graded_one_step(snn_net* net, GradedArgs a, float* G, int64_t t, cud
         if (P.d.layout != SNN_LAYOUT_DENSE) continue;
         const PopHost& pre = net->pops[P.d.pre];
         e = launch_graded_dense_fwd(P.w, a.r + pre.offset, pre.d.n, net->pops[P.d.post].d.n, G + P.g_off, P.dpart,
-                                    P.dld, P.dcount, P.dchunks, s);
+                                    P.dld, P.dcount, P.dchunks, P.dstream, s);
     }
     if (e == cudaSuccess) e = launch_graded_neuron(a, s);
     return e;
@@ -132,6 +132,8 @@ snn_status graded_setup(snn_net* net, cudaStream_t s) {
             // the matrix itself serves both directions; the forward product's
             // partial rows and per post block tickets
             P.dchunks = dense_fwd_chunks(n_pre, n_post, net->sm_count);
+            // a matrix within 60 % of L2 stays resident from step to step
+            P.dstream = 4.0 * (double)n_pre * (double)n_post > 0.6 * (double)net->l2_bytes;
             P.dld = ((int64_t)n_post + 3) / 4 * 4;
             const size_t blocks = ((size_t)n_post + 127) / 128;
             SNN_TRY(net_alloc(net, &P.dpart, std::max<size_t>(1, (size_t)P.dchunks * P.dld), "dense partial rows"));

@@ -39,7 +39,16 @@ using namespace snn::tc;
 constexpr int kFwdThreads = 256;
 constexpr int kFwdPosts = 128;              // posts per CTA (32 lanes x 4)
 
-template <bool kVec>
+// W rows: streamed (evict-first) when the matrix is larger than the L2 share
+// it may keep, else through the normal cached path so that it stays resident
+// from one step to the next.
+template <bool kStream>
+__device__ __forceinline__ float4 w_load(const float* p) {
+    if constexpr (kStream) return __ldcs(reinterpret_cast<const float4*>(p));
+    else return __ldg(reinterpret_cast<const float4*>(p));
+}
+
+template <bool kVec, bool kStream>
 __global__ void __launch_bounds__(kFwdThreads) k_graded_dense_fwd(const float* __restrict__ W,
                                                                   const float* __restrict__ x, int32_t n_pre,
                                                                   int32_t n_post, int32_t rows_per_chunk,
@@ -54,17 +63,17 @@ __global__ void __launch_bounds__(kFwdThreads) k_graded_dense_fwd(const float* _
     if (j < n_post) {
         int i = i0 + warp;
         if constexpr (kVec) {
-            // four rows in flight per lane; the sums stay in ascending row order
-            for (; i + 24 < i1; i += 32) {
-                float4 w[4];
-                float r[4];
+            // eight rows in flight per lane; the sums stay in ascending row order
+            for (; i + 56 < i1; i += 64) {
+                float4 w[8];
+                float r[8];
 #pragma unroll
-                for (int u = 0; u < 4; ++u) {
-                    w[u] = __ldcs(reinterpret_cast<const float4*>(W + (int64_t)(i + 8 * u) * n_post + j));
+                for (int u = 0; u < 8; ++u) {
+                    w[u] = w_load<kStream>(W + (int64_t)(i + 8 * u) * n_post + j);
                     r[u] = __ldg(x + i + 8 * u);
                 }
 #pragma unroll
-                for (int u = 0; u < 4; ++u) {
+                for (int u = 0; u < 8; ++u) {
                     acc.x = fmaf(w[u].x, r[u], acc.x);
                     acc.y = fmaf(w[u].y, r[u], acc.y);
                     acc.z = fmaf(w[u].z, r[u], acc.z);
@@ -72,7 +81,7 @@ __global__ void __launch_bounds__(kFwdThreads) k_graded_dense_fwd(const float* _
                 }
             }
             for (; i < i1; i += 8) {
-                const float4 w = __ldcs(reinterpret_cast<const float4*>(W + (int64_t)i * n_post + j));
+                const float4 w = w_load<kStream>(W + (int64_t)i * n_post + j);
                 const float r = __ldg(x + i);
                 acc.x = fmaf(w.x, r, acc.x);
                 acc.y = fmaf(w.y, r, acc.y);
@@ -151,40 +160,49 @@ constexpr uint32_t kGIdesc = idesc_bf16(kRows, kRows);
 __constant__ int c_pair_a[6] = {0, 0, 1, 0, 2, 1};
 __constant__ int c_pair_b[6] = {0, 1, 0, 2, 0, 1};
 
+// Eight consecutive K elements of one row are one 16-byte row of a core
+// matrix in the tiled layout: each thread splits eight values and writes each
+// part with one 16-byte store.
+__device__ __forceinline__ void split8_store(const float (&x)[8], uint16_t* dst, int64_t part_elems) {
+    uint16_t hi[8], mid[8], lo[8];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) split3(x[u], hi[u], mid[u], lo[u]);
+    auto pack = [](const uint16_t (&h)[8]) {
+        return make_uint4((uint32_t)h[0] | ((uint32_t)h[1] << 16), (uint32_t)h[2] | ((uint32_t)h[3] << 16),
+                          (uint32_t)h[4] | ((uint32_t)h[5] << 16), (uint32_t)h[6] | ((uint32_t)h[7] << 16));
+    };
+    *reinterpret_cast<uint4*>(dst) = pack(hi);
+    *reinterpret_cast<uint4*>(dst + part_elems) = pack(mid);
+    *reinterpret_cast<uint4*>(dst + 2 * part_elems) = pack(lo);
+}
+
 // A[i][t] = R[t][i] (for the network: a step's releases of the pre
-// population), 3 parts, tiled (mp x kp).  Grid (mp / 256, kp): one step per
-// block row, pre index fastest (coalesced reads of a step's row).
+// population), 3 parts, tiled (mp x kp).  Grid (mp / 256, kp / 8): a thread
+// takes eight steps of one pre index; pre index fastest across the warp
+// (coalesced reads of each step's row).
 __global__ void __launch_bounds__(256) k_grad_split_a(const float* __restrict__ R, int64_t ldr, int32_t m, int32_t L,
                                                       int64_t mp, int64_t kp, uint16_t* __restrict__ A) {
-    const int64_t total = mp * kp, kt = kp / kGK;
-    const int64_t i = (int64_t)blockIdx.x * 256 + threadIdx.x, t = blockIdx.y;
+    const int64_t i = (int64_t)blockIdx.x * 256 + threadIdx.x, t0 = (int64_t)blockIdx.y * 8;
     if (i >= mp) return;
-    const float v = (i < m && t < L) ? R[t * ldr + i] : 0.0f;
-    uint16_t hi, mid, lo;
-    split3(v, hi, mid, lo);
-    const int64_t o = tiled_offset(i, t, kt, kGK);
-    A[o] = hi;
-    A[total + o] = mid;
-    A[2 * total + o] = lo;
+    float x[8];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) x[u] = (i < m && t0 + u < L) ? R[(t0 + u) * ldr + i] : 0.0f;
+    split8_store(x, A + tiled_offset(i, t0, kp / kGK, kGK), mp * kp);
 }
 
 // B[j][t] = N[j][t] (for the network: dL/dG of a post over the segment,
-// time-contiguous), 3 parts, tiled (np x kp).  Blocks of 8 rows x 32 lanes,
-// step fastest (coalesced reads of a row of N).
+// time-contiguous), 3 parts, tiled (np x kp).  A thread takes eight steps of
+// one post, steps fastest across the warp (coalesced reads of a row of N).
 __global__ void __launch_bounds__(256) k_grad_split_b(const float* __restrict__ N, int64_t ldn, int32_t n, int32_t L,
                                                       int64_t np, int64_t kp, uint16_t* __restrict__ B) {
-    const int64_t total = np * kp, kt = kp / kGK;
-    const int64_t j = (int64_t)blockIdx.x * 8 + (threadIdx.x >> 5);
-    if (j >= np) return;
-    for (int64_t t = threadIdx.x & 31; t < kp; t += 32) {
-        const float v = (j < n && t < L) ? N[j * ldn + t] : 0.0f;
-        uint16_t hi, mid, lo;
-        split3(v, hi, mid, lo);
-        const int64_t o = tiled_offset(j, t, kt, kGK);
-        B[o] = hi;
-        B[total + o] = mid;
-        B[2 * total + o] = lo;
-    }
+    const int64_t per_row = kp / 8;
+    const int64_t e = (int64_t)blockIdx.x * 256 + threadIdx.x;
+    if (e >= np * per_row) return;
+    const int64_t j = e / per_row, t0 = (e % per_row) * 8;
+    float x[8];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) x[u] = (j < n && t0 + u < L) ? N[j * ldn + t0 + u] : 0.0f;
+    split8_store(x, B + tiled_offset(j, t0, kp / kGK, kGK), np * kp);
 }
 
 __global__ void __launch_bounds__(kGThreads, 1)
@@ -350,14 +368,22 @@ int dense_fwd_chunks(int32_t n_pre, int32_t n_post, int sm_count) {
 }
 
 cudaError_t launch_graded_dense_fwd(const float* W, const float* x, int32_t n_pre, int32_t n_post, float* Gq,
-                                    float* part, int64_t ld_part, unsigned* count, int32_t chunks, cudaStream_t s) {
+                                    float* part, int64_t ld_part, unsigned* count, int32_t chunks, bool stream,
+                                    cudaStream_t s) {
     if (n_post == 0) return cudaSuccess;
     const int rows = (n_pre + chunks - 1) / chunks;
     const dim3 grid((unsigned)((n_post + kFwdPosts - 1) / kFwdPosts), (unsigned)chunks);
-    if ((n_post & 3) == 0)
-        k_graded_dense_fwd<true><<<grid, kFwdThreads, 0, s>>>(W, x, n_pre, n_post, rows, Gq, part, ld_part, count);
-    else
-        k_graded_dense_fwd<false><<<grid, kFwdThreads, 0, s>>>(W, x, n_pre, n_post, rows, Gq, part, ld_part, count);
+    if ((n_post & 3) == 0) {
+        if (stream)
+            k_graded_dense_fwd<true, true><<<grid, kFwdThreads, 0, s>>>(W, x, n_pre, n_post, rows, Gq, part, ld_part,
+                                                                        count);
+        else
+            k_graded_dense_fwd<true, false><<<grid, kFwdThreads, 0, s>>>(W, x, n_pre, n_post, rows, Gq, part, ld_part,
+                                                                         count);
+    } else {
+        k_graded_dense_fwd<false, false><<<grid, kFwdThreads, 0, s>>>(W, x, n_pre, n_post, rows, Gq, part, ld_part,
+                                                                      count);
+    }
     return cudaGetLastError();
 }
 
@@ -376,11 +402,12 @@ cudaError_t launch_dense_grad(const DenseGradArgs& g, cudaStream_t s) {
     }
     int64_t mp, np, kp;
     dense_grad_sizes(g.m, g.n, g.L, &mp, &np, &kp);
-    k_grad_split_a<<<dim3((unsigned)(mp / 256 + (mp % 256 != 0)), (unsigned)kp), 256, 0, s>>>(g.R, g.ldr, g.m, g.L, mp,
-                                                                                          kp, g.A);
+    k_grad_split_a<<<dim3((unsigned)(mp / 256 + (mp % 256 != 0)), (unsigned)(kp / 8)), 256, 0, s>>>(g.R, g.ldr, g.m,
+                                                                                                g.L, mp, kp, g.A);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    k_grad_split_b<<<(unsigned)(np / 8), 256, 0, s>>>(g.N, g.ldn, g.n, g.L, np, kp, g.B);
+    const int64_t nb = np * (kp / 8);
+    k_grad_split_b<<<(unsigned)((nb + 255) / 256), 256, 0, s>>>(g.N, g.ldn, g.n, g.L, np, kp, g.B);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     const size_t smem = (size_t)kGStages * kGStageBytes;
     e = cudaFuncSetAttribute(k_dense_grad_mma, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);

@@ -222,6 +222,7 @@ struct ProjHost {
     float* dpart = nullptr;        // graded dense: partial rows of the forward product
     unsigned* dcount = nullptr;    // graded dense: per post block ticket
     int32_t dchunks = 1;           // graded dense: pre-row ranges of the forward product
+    bool dstream = true;           // graded dense: stream W (evict-first) instead of keeping it in L2
     int64_t dld = 0;               // graded dense: row stride of dpart
     int64_t g_off = 0;
     float scale;
@@ -249,6 +250,7 @@ struct snn_net {
     int32_t n_total = 0;           // padded SoA length
     int32_t num_tiles = 0;
     int sm_count = 148;
+    int64_t l2_bytes = 0;
     // device state
     float *V = nullptr, *m = nullptr, *h = nullptr, *n = nullptr, *g0 = nullptr, *g1 = nullptr,
           *iext = nullptr, *isyn = nullptr;
@@ -382,7 +384,8 @@ cudaError_t launch_scatter_csc(const float* w_csr, const int64_t* perm, float* w
 cudaError_t launch_finish_grad_scale(const double* acc, float* out, int n, cudaStream_t s);
 int dense_fwd_chunks(int32_t n_pre, int32_t n_post, int sm_count);
 cudaError_t launch_graded_dense_fwd(const float* W, const float* x, int32_t n_pre, int32_t n_post, float* Gq,
-                                    float* part, int64_t ld_part, unsigned* count, int32_t chunks, cudaStream_t s);
+                                    float* part, int64_t ld_part, unsigned* count, int32_t chunks, bool stream,
+                                    cudaStream_t s);
 void dense_grad_sizes(int32_t n_pre, int32_t n_post, int32_t K, int64_t* mp, int64_t* np, int64_t* kp);
 cudaError_t launch_dense_grad(const DenseGradArgs& g, cudaStream_t s);
 cudaError_t launch_persistent(const PersistArgs& a, int grid, cudaStream_t s);
