@@ -75,7 +75,7 @@ def _args():
     ap.add_argument("--no-scale-point", action="store_true",
                     help="skip the forced-activity propagation measurement at 100 x 1,000,000, p = 0.5")
     ap.add_argument("--profile", choices=["cluster", "tiled", "dense", "neuron", "graded", "dense_batch", "dense_grad",
-                                          "graded_dense"],
+                                          "graded_dense", "csr_mid"],
                     help="run a few launches of one kernel on its workload and exit (a target for ncu)")
     ap.add_argument("--record-traffic", nargs=3, metavar=("KERNEL", "BYTES", "COMMAND"),
                     help="store an ncu DRAM byte count per launch of KERNEL (with a hash of its sources) in "
@@ -883,6 +883,7 @@ def run_profile(a):
     command the ncu summaries under profiles/ were captured from.
       cluster: the four-population network, cluster engine, 1000 steps per launch;
       tiled:   forced-activity propagation, 100 rows x 1,000,000 posts, p = 0.5, CSR;
+      csr_mid: the same at p = 0.05 (below the post-tiled threshold: the row kernel);
       dense:   the same with dense rows;
       neuron:  8,000,000 HH neurons, one neuron phase per launch;
       graded:  the differentiable workload (20,000 middle neurons), 200 steps
@@ -904,9 +905,10 @@ def run_profile(a):
         net.set_option("persist_steps", 1000)
         for _ in range(3):
             net.launch_phase(4)
-    elif a.profile in ("tiled", "dense"):
+    elif a.profile in ("tiled", "dense", "csr_mid"):
         flush = _flush_buffers(torch, dev)
-        _forced_propagation(snn, torch, dev, 1_000_000, 0.5, "csr" if a.profile == "tiled" else a.profile, reps=3,
+        p = 0.05 if a.profile == "csr_mid" else 0.5
+        _forced_propagation(snn, torch, dev, 1_000_000, p, "dense" if a.profile == "dense" else "csr", reps=3,
                             flush=flush)
         return
     elif a.profile == "dense_batch":

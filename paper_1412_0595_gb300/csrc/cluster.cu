@@ -350,10 +350,10 @@ cudaError_t launch_npt(const PersistArgs& a, int cl, int per_cta, cudaStream_t s
     const size_t smem = cluster_smem(per_cta, a.n.num_tiles);
     cudaError_t e = cudaFuncSetAttribute(k_step_cluster<NPT>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
     if (e != cudaSuccess) return e;
-    if (smem > 48 * 1024) {
-        e = cudaFuncSetAttribute(k_step_cluster<NPT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e != cudaSuccess) return e;
-    }
+    // always opted in: the kernel's static shared memory counts toward the
+    // 48 KiB that a launch may use without the attribute
+    e = cudaFuncSetAttribute(k_step_cluster<NPT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
     cudaLaunchConfig_t cfg{};
     cfg.gridDim = dim3(cl);
     cfg.blockDim = dim3(kCT);
@@ -391,10 +391,8 @@ cudaError_t cluster_supported(int cl, int per_cta, int num_tiles, bool* ok) {
     const size_t smem = cluster_smem(per_cta, num_tiles);
     cudaError_t e = cudaFuncSetAttribute(k_step_cluster<4>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
     if (e != cudaSuccess) return e;
-    if (smem > 48 * 1024) {
-        e = cudaFuncSetAttribute(k_step_cluster<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e != cudaSuccess) return e;
-    }
+    e = cudaFuncSetAttribute(k_step_cluster<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
     cudaLaunchConfig_t cfg{};
     cfg.gridDim = dim3(cl);
     cfg.blockDim = dim3(kCT);

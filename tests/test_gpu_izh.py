@@ -56,14 +56,20 @@ def test_steps_match_oracle(gpu, engine):
         assert net.counters(p) == ref.counters(p)
 
 
+# Tolerances: about five standard deviations of the oracle's own 2 s counts
+# over 60 runs with every weight scaled by 1 +- e, |e| log-uniform in
+# [1e-8, 1e-6] (rounding-level changes): nConn = 100: excitatory 0.11 %,
+# inhibitory 0.53 %, total 0.11 %; nConn = 1000: 0.49 %, 1.59 %, 0.62 %
+# (largest single deviations 1.4 %, 6.0 %, 2.0 %).  Floors of 2 / 4 / 2 %.
+_RATE_TOL = {(100, "csr"): (0.02, 0.04, 0.02), (1000, "dense"): (0.025, 0.08, 0.031)}
+
+
 @pytest.mark.parametrize("n_conn,layout", [(100, "csr"), (1000, "dense")])
 def test_rates_match_oracle_over_two_seconds(gpu, n_conn, layout):
     # The full 1000-neuron network.  Spike lists part after ~200 steps (FP32
-    # against FP64 rounding); the counts then agree statistically.  Rounding-
-    # sized changes move the oracle's own counts: scaling every weight by
-    # 1 +- 1e-7 shifts the 200 inhibitory neurons' 5 s count by up to 1.2 %
-    # and 1e-6 by 1.6 %, so the small inhibitory population gets 4 %, the
-    # excitatory population and the network total 2 %.
+    # against FP64 rounding, and FP32 shared-memory sums whose order varies
+    # from run to run); the counts then agree statistically, within the
+    # oracle's own spread under rounding-level changes (_RATE_TOL).
     spec = I.config_izhikevich(n_conn=n_conn, layout=layout, steps=2000)
     net = gpu.Network.from_spec(spec)
     net.step(2000)
@@ -71,12 +77,13 @@ def test_rates_match_oracle_over_two_seconds(gpu, n_conn, layout):
     ref.step(2000)
     got = [net.counters(p) for p in (0, 1)]
     want = [ref.counters(p) for p in (0, 1)]
-    assert abs(got[0][0] - want[0][0]) <= 0.02 * want[0][0] + 1, (got, want)
-    assert abs(got[1][0] - want[1][0]) <= 0.04 * want[1][0] + 1, (got, want)
+    t_exc, t_inh, t_tot = _RATE_TOL[(n_conn, layout)]
+    assert abs(got[0][0] - want[0][0]) <= t_exc * want[0][0] + 1, (got, want)
+    assert abs(got[1][0] - want[1][0]) <= t_inh * want[1][0] + 1, (got, want)
     tot_g, tot_w = got[0][0] + got[1][0], want[0][0] + want[1][0]
-    assert abs(tot_g - tot_w) <= 0.02 * tot_w, (got, want)
+    assert abs(tot_g - tot_w) <= t_tot * tot_w, (got, want)
     assert got[0][1] == got[1][1] == want[0][1] == want[1][1] == 0
-    assert net.synaptic_events() == pytest.approx(ref.events, rel=0.02)
+    assert net.synaptic_events() == pytest.approx(ref.events, rel=t_tot)
 
 
 def test_blowup_counts_nans(gpu):
