@@ -280,12 +280,15 @@ def _differentiable(snn, torch, dev, steps=2000, K=100):
     t_f, t_b, t_fd = ev[0].elapsed_time(ev[1]), ev[1].elapsed_time(ev[2]), ev[2].elapsed_time(ev[3])
     peaks, src = _peaks()
     hbm = float(peaks.get("hbm_gbs", 6800.0))
-    fwd_gbs = nnz * 8 * steps / (t_f * 1e-3) / 1e9
+    # the transposed pre indices are 16-bit when every pre population has at most 65,536 neurons
+    per_syn = 6 if max(spec["pops"][d["pre"]]["n"] for d in spec["projs"]) <= 65536 else 8
+    fwd_gbs = nnz * per_syn * steps / (t_f * 1e-3) / 1e9
     out = {"workload": f"graded HH: In 100 -> Mid 20,000 (+ recurrent) -> Out 100, p = 0.05, {steps} steps of 0.05 ms",
            "synapses": nnz, "checkpoint_every": K, "loss": loss,
            "forward_ms": t_f, "backward_ms": t_b, "adjoint_total_ms": t_f + t_b,
            "six_forward_runs_ms": t_fd, "adjoint_vs_fd_speedup": t_fd / (t_f + t_b),
            "gradients": 3 + nnz, "grad_scale": gs.cpu().tolist(),
+           "forward_bytes_per_synapse": per_syn,
            "forward_synapse_stream_gbs": fwd_gbs, "forward_frac_hbm": fwd_gbs / hbm,
            "finite": bool(torch.isfinite(gs).all() and all(torch.isfinite(g).all() for g in gw))}
     net.close()

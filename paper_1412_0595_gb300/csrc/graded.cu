@@ -133,11 +133,42 @@ __device__ __forceinline__ float lane_dot(const float* w, const int32_t* idx, co
     return (acc[0] + acc[1]) + (acc[2] + acc[3]);
 }
 
+// lane_dot with 16-bit indices: four consecutive synapses' indices are one
+// 8-byte load (little-endian halves); same blocks and summation order.
+template <bool kShared>
+__device__ __forceinline__ float lane_dot16(const float* w, const uint16_t* idx, const float* x, int64_t b,
+                                            int64_t e, int lane) {
+    float acc[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+    for (int64_t k0 = (b & ~int64_t(3)) + 4 * lane; k0 < e; k0 += 512) {
+        float4 wv[4];
+        uint2 iv[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const int64_t k = k0 + 128 * u;
+            if (k < e) {
+                wv[u] = __ldcs(reinterpret_cast<const float4*>(w + k));
+                iv[u] = __ldcs(reinterpret_cast<const uint2*>(idx + k));
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const int64_t k = k0 + 128 * u;
+            if (k < e) {
+                if (k >= b) acc[u] = fmaf(wv[u].x, gather<kShared>(x, (int32_t)(iv[u].x & 0xFFFFu)), acc[u]);
+                if (k + 1 >= b && k + 1 < e) acc[u] = fmaf(wv[u].y, gather<kShared>(x, (int32_t)(iv[u].x >> 16)), acc[u]);
+                if (k + 2 >= b && k + 2 < e) acc[u] = fmaf(wv[u].z, gather<kShared>(x, (int32_t)(iv[u].y & 0xFFFFu)), acc[u]);
+                if (k + 3 >= b && k + 3 < e) acc[u] = fmaf(wv[u].w, gather<kShared>(x, (int32_t)(iv[u].y >> 16)), acc[u]);
+            }
+        }
+    }
+    return (acc[0] + acc[1]) + (acc[2] + acc[3]);
+}
+
 }  // namespace
 
 // One warp per post neuron.  kShared: the releases of the whole network
 // (n_total floats) are first copied into shared memory.
-template <bool kShared>
+template <bool kShared, bool kNarrow>
 __global__ void __launch_bounds__(kShared ? kStagedThreads : kThreads, kShared ? 1 : 4) k_graded_spmv(const GradedArgs a) {
     extern __shared__ float s_x[];
     const float* x = a.r;
@@ -155,7 +186,9 @@ __global__ void __launch_bounds__(kShared ? kStagedThreads : kThreads, kShared ?
         const GradProj& Q = a.gprojs[q];
         if (Q.dense) continue;                       // dense projections have their own product
         const int j = (int)(w - Q.g_off);
-        float acc = lane_dot<kShared>(Q.csc_w, Q.csc_pre, x + Q.pre_off, Q.csc_ptr[j], Q.csc_ptr[j + 1], lane);
+        float acc;
+        if constexpr (kNarrow) acc = lane_dot16<kShared>(Q.csc_w, Q.csc_pre16, x + Q.pre_off, Q.csc_ptr[j], Q.csc_ptr[j + 1], lane);
+        else acc = lane_dot<kShared>(Q.csc_w, Q.csc_pre, x + Q.pre_off, Q.csc_ptr[j], Q.csc_ptr[j + 1], lane);
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
         if (lane == 0) a.G[w] = acc;
@@ -419,8 +452,11 @@ static cudaError_t launch_staged(K kernel, size_t bytes, cudaStream_t s, Args...
 cudaError_t launch_graded_spmv(const GradedArgs& a, cudaStream_t s) {
     if (a.total_posts == 0) return cudaSuccess;
     const size_t bytes = sizeof(float) * (size_t)a.n_total;
-    if (bytes <= kStageMaxBytes) return launch_staged(k_graded_spmv<true>, bytes, s, a);
-    k_graded_spmv<false><<<grid_warps(a.total_posts), kThreads, 0, s>>>(a);
+    if (bytes <= kStageMaxBytes)
+        return a.narrow ? launch_staged(k_graded_spmv<true, true>, bytes, s, a)
+                        : launch_staged(k_graded_spmv<true, false>, bytes, s, a);
+    if (a.narrow) k_graded_spmv<false, true><<<grid_warps(a.total_posts), kThreads, 0, s>>>(a);
+    else k_graded_spmv<false, false><<<grid_warps(a.total_posts), kThreads, 0, s>>>(a);
     return cudaGetLastError();
 }
 

@@ -100,7 +100,8 @@ struct GradProj {
     const int32_t* col;
     const float* w;
     const int64_t* csc_ptr;            // transposed copy (post-major)
-    const int32_t* csc_pre;
+    const int32_t* csc_pre;            // pre indices, 32-bit, or
+    const uint16_t* csc_pre16;         // 16-bit when every graded pre population has at most 65,536 neurons
     const float* csc_w;
     int32_t dense;                     // 1: w is the n_pre x n_post matrix (no row / column arrays)
 };
@@ -116,6 +117,7 @@ struct GradedArgs {
     const int32_t* out_begin;          // [n_pops + 1] outgoing projections per population
     const int32_t* out_list;
     int32_t n_total;
+    int32_t narrow;                    // transposed pre indices are 16-bit (csc_pre16)
     float *V, *m, *h, *n, *iext;
     float* r;                          // release of every neuron (next step's input)
     float* G;                          // G vector of the current step
@@ -217,6 +219,7 @@ struct ProjHost {
     snn_proj_desc d;
     int64_t* csc_ptr = nullptr;    // graded: transposed copy
     int32_t* csc_pre = nullptr;
+    uint16_t* csc_pre16 = nullptr;
     float* csc_w = nullptr;
     int64_t* csc_perm = nullptr;   // transposed position -> compressed-row position
     float* dpart = nullptr;        // graded dense: partial rows of the forward product
@@ -271,6 +274,7 @@ struct snn_net {
     int32_t tiled = 2;                        // post-tiled rows: 0 off, 1 all compressed projections, 2 choose
     // graded (differentiable) networks
     bool graded = false;
+    bool graded_narrow = false;               // 16-bit transposed pre indices
     snn::GradProj* d_gprojs = nullptr;
     int32_t* in_begin = nullptr;
     int32_t* in_list = nullptr;
