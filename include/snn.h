@@ -404,7 +404,9 @@ snn_status snn_set_weights(snn_net* net, int32_t proj, const float* w, int32_t o
  * (E_q: the post population's reversal potential of the projection's
  * channel), then the Euler substeps; spike counts are still kept.  The paper
  * fixes no synapse model (Sec. 2); this graded one makes the loss below a
- * smooth function of the scales s_q (Sec. 5.1) and the weights. */
+ * smooth function of the scales s_q (Sec. 5.1) and the weights.  Graded
+ * projections use compressed rows or dense storage (Eq. 2, every pair a
+ * weight); populations must be HH. */
 
 /* Runs n_steps steps from the creation state (it resets the network first)
  * and evaluates L = mean over steps t and output neurons k of
@@ -419,12 +421,14 @@ snn_status snn_forward_record(snn_net* net, int64_t n_steps, int32_t checkpoint_
 
 /* Gradient of the last recorded L with respect to every projection's scale
  * (grad_scale: device, n_projs floats) and weights (grad_w: host array of
- * n_projs device pointers, each nnz floats in compressed-row order), by the
- * discrete adjoint of the recorded steps: each checkpoint segment is
- * recomputed, then swept in reverse (substeps, synaptic current,
- * pre-synaptic gather), and the weight gradients of the segment are summed
- * over its steps in one pass.  Overwrites the outputs.  SNN_ERR_STATE
- * without a recorded forward.  Synchronises `stream`. */
+ * n_projs device pointers, each nnz floats in compressed-row order, or
+ * n_pre x n_post row-major for dense storage), by the discrete adjoint of the
+ * recorded steps: each checkpoint segment is recomputed, then swept in
+ * reverse (substeps, synaptic current, pre-synaptic gather), and the weight
+ * gradients of the segment are summed over its steps in one pass (for dense
+ * storage a rank-K update, see snn_dense_grad_run and SNN_OPT_DENSE_GRAD).
+ * Overwrites the outputs.  SNN_ERR_STATE without a recorded forward.
+ * Synchronises `stream`. */
 snn_status snn_backward(snn_net* net, float* grad_scale, float* const* grad_w, void* stream);
 
 /* ---- checkpoint / resume --------------------------------------------------
