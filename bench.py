@@ -59,6 +59,9 @@ def _args():
                     help="time steps run before the per-kernel timing")
     ap.add_argument("--phase-reps", type=int, default=200,
                     help="back-to-back launches per kernel in the per-kernel timing")
+    ap.add_argument("--tiled-crossover", action="store_true",
+                    help="print one JSON line per (posts, density) point timing the row kernel against the "
+                         "post-tiled kernel on forced activity (the data behind the post-tiled threshold)")
     ap.add_argument("--sweep", action="store_true",
                     help="print one JSON line per point of the scaling sweep instead of the headline line")
     ap.add_argument("--no-batched", action="store_true", help="skip the batched-vs-sequential comparison")
@@ -175,6 +178,50 @@ def _forced_propagation(snn, torch, dev, n_mid, p, layout, reps=7, flush=None):
     t = statistics.median(times) * 1e-3
     return {"n_mid": n_mid, "p": p, "layout": layout, "events": events, "bytes": nbytes,
             "us": t * 1e6, "gbs": nbytes / t / 1e9, "events_per_s": events / t}
+
+
+def run_tiled_crossover(a):
+    """Forced activity (100 spiking rows, caches flushed before each of 7
+    launches, median): the row kernel (SNN_OPT_TILED 0) against the
+    post-tiled kernel (1) at several post-population sizes and densities;
+    fraction of the measured copy bandwidth at 8 B per synapse."""
+    import torch
+
+    import paper_1412_0595_gb300 as snn
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    peaks, _ = _peaks()
+    hbm = float(peaks.get("hbm_gbs", 6800.0))
+    flush = _flush_buffers(torch, dev)
+    rows = np.arange(100, dtype=np.int32)
+    for n_mid in (1_000_000, 300_000, 100_000):
+        for p in (0.01, 0.02, 0.05, 0.1, 0.2, 0.5):
+            spec = I.net([I.source_pop(100, 0.0), I.hh_pop(n_mid)],
+                         [I.proj(0, 1, "csr", p, ("lognormal", -3.0, 0.5))], dt=0.1, steps=1)
+            net = snn.Network.from_spec(spec, device=dev)
+            net.debug_propagate(0, rows)
+            nnz = net.nnz(0)
+            line = {"n_mid": n_mid, "p": p, "synapses": nnz}
+            for t in (0, 1):
+                net.set_option("tiled", t)
+                net.debug_propagate(0, rows)
+                s = torch.cuda.current_stream()
+                times = []
+                for _ in range(7):
+                    _flush_l2(flush)
+                    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                    e0.record(s)
+                    net.launch_phase(3)
+                    e1.record(s)
+                    e1.synchronize()
+                    times.append(e0.elapsed_time(e1))
+                net.sync()
+                us = statistics.median(times) * 1e3
+                name = "row" if t == 0 else "tiled"
+                line[name + "_us"] = us
+                line[name + "_frac_hbm"] = nnz * BYTES_PER_EVENT / (us * 1e-6) / 1e9 / hbm
+            print(json.dumps(line), flush=True)
+            net.close()
 
 
 def _neuron_rate(snn, torch, dev, n, reps=50):
@@ -1017,6 +1064,8 @@ def main():
         run_profile(a)
     elif a.sweep:
         run_sweep(a)
+    elif a.tiled_crossover:
+        run_tiled_crossover(a)
     elif a.impl == "reference":
         run_reference(a)
     else:

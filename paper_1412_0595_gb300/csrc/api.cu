@@ -195,16 +195,19 @@ NeuronArgs neuron_args(snn_net* net) {
 int prop_blocks(snn_net* net) { return net->prop_blocks > 0 ? net->prop_blocks : net->sm_count * 4; }
 
 // Post-tiled propagation pays off when a row has many synapses in each post
-// tile (at least 256: density x tile >= 256, i.e. density >= 1/8) and the post
-// population spans at least eight tiles; below that the row kernel's global
-// reductions stay in L2 and cost less than the staging.
+// tile and the post population spans at least eight tiles; below that the
+// row kernel's global reductions stay in L2 and cost less than the staging.
+// Measured crossover (100 spiking rows, caches flushed): about 200 synapses
+// per 2048-post tile for 300,000 posts and more (p = 0.1: 76 against 94 us at
+// 1,000,000 posts), 256 for smaller post populations (p = 0.1 at 100,000
+// posts: 22.5 against 20.5 us, the row kernel still ahead).
 bool want_tiled(const snn_net* net, const ProjHost& P) {
     if (P.d.layout != SNN_LAYOUT_CSR || net->tiled == 0) return false;
     if (net->tiled == 1) return true;
     const int32_t n_pre = net->pops[P.d.pre].d.n, n_post = net->pops[P.d.post].d.n;
     if (n_post < 8 * kPostTile || n_pre == 0) return false;
     const double per_tile = (double)P.nnz / n_pre * kPostTile / n_post;
-    return per_tile >= 256.0;
+    return per_tile >= (n_post >= 64 * kPostTile ? 192.0 : 256.0);
 }
 
 snn_status setup_tiled(snn_net* net, cudaStream_t s) {
