@@ -60,3 +60,14 @@ def test_replicas_reduce_and_reference_prints_once():
         assert t == 15.0 and e == 3000.0          # max of 10, 15; 1000 + 2000
     assert '"impl": "reference"' in out[0][2] and out[0][2].count("\n") == 1
     assert out[1][2] == ""
+    # the line keeps the bench contract
+    import json
+    line = json.loads(out[0][2])
+    for key in ("metric", "value", "unit", "n_gpus", "steps", "warmup", "ms_per_step", "higher_is_better",
+                "scaling", "vs_baseline", "dtype", "data", "config", "cpu_baseline", "e2e"):
+        assert key in line, key
+    assert line["metric"] == line["unit"] == "synaptic events/s" and line["higher_is_better"] is True
+    # 20 steps are too few for spikes to reach the middle population: events, and value, may be 0
+    assert line["n_gpus"] == world and line["value"] >= 0 and line["ms_per_step"] > 0 and line["dtype"] == "f64"
+    assert line["cpu_baseline"]["kind"] == "oracle" and line["cpu_baseline"]["value"] == line["value"]
+    assert line["e2e"]["h2d_bytes_per_step"] == line["e2e"]["d2h_bytes_per_step"] == 0
