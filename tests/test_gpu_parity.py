@@ -151,7 +151,20 @@ def _first_spike_steps(run_spikes, n):
     return first
 
 
+SADDLE_MV = -57.5253        # saddle of the resting state (oracle pin, tests/test_oracle_hh.py)
+
+
+def _input_only(spec):
+    """The driven input population alone: it receives no projection, and its
+    drive draws and initial potentials are keyed by its own index, so its
+    trajectory equals its trajectory inside the full network."""
+    sp = dict(spec)
+    sp["pops"], sp["projs"] = [spec["pops"][0]], []
+    return sp
+
+
 def test_four_population_workload_full_size_first_200_steps(gpu):
+    from _spread import perturbed_spread
     spec = I.config_four_pop(steps=200)
     net = gpu.Network.from_spec(spec)
     ref = oracle.from_spec(spec)
@@ -171,14 +184,82 @@ def test_four_population_workload_full_size_first_200_steps(gpu):
     fg, fo = _first_spike_steps(sg, n_in), _first_spike_steps(so, n_in)
     assert np.all(np.abs(fg - fo) <= 1)                     # first spikes within one step
     vg, vo = np.array(vg), np.array(vo)
-    # V within 1e-3 mV while the oracle trajectory is below the saddle of the
-    # resting state (-57.5253 mV); above it the upstroke amplifies the FP32
-    # rounding of V exponentially until the spike (chaotic divergence).
-    for i in range(n_in):
-        above = np.nonzero(vo[:, i] > -57.5253)[0]
-        end = above[0] if len(above) else 200
-        if end > 0:
-            assert np.abs(vg[:end, i] - vo[:end, i]).max() <= 1e-3, i
+    # Every driven input neuron over the whole window: V within 1e-3 mV while
+    # the oracle trajectory has stayed below the saddle of the resting state;
+    # after the oracle passes the saddle (an upstroke, spiking or not) within
+    # the oracle's own spread under FP32-level rounding of its state (bound
+    # per neuron, 60 seeded perturbed oracle runs).
+    v_in, spread = perturbed_spread(_input_only(spec), 0, 200)
+    assert np.array_equal(v_in, vo)                          # the input population alone is the same run
+    crossed = np.maximum.accumulate(vo > SADDLE_MV, axis=0)
+    dv = np.abs(vg - vo)
+    below = np.where(crossed, 0.0, dv)
+    assert below.max() <= 1e-3, np.unravel_index(below.argmax(), below.shape)
+    silent = [i for i in range(n_in) if fo[i] < 0 and fg[i] < 0]
+    assert len(silent) > 20
+    for i in silent:                                         # no spike in the window: the full window
+        assert dv[:, i].max() <= max(1e-3, spread[i]), (i, dv[:, i].max(), spread[i])
+    if all(np.array_equal(a, b) for a, b in zip(sg, so)):   # equal spike lists: spiking neurons too
+        for i in range(n_in):
+            assert dv[:, i].max() <= max(1e-3, spread[i]), (i, dv[:, i].max(), spread[i])
+
+
+def _compare_long_launch(net, ref, worst_v=1e-3):
+    # Mid, Out and Inh stay below the saddle (strongly subthreshold drive)
+    for p in (1, 2, 3):
+        vo = ref.get(p, "V")
+        assert vo.max() < SADDLE_MV
+        assert np.abs(net.read_host(p, "V") - vo).max() <= worst_v, p
+        for f in ("m", "h", "n"):
+            assert np.abs(net.read_host(p, f) - ref.get(p, f)).max() <= 1e-5, (p, f)
+        for f in ("g0", "g1"):
+            assert _rel_ok(net.read_host(p, f), ref.get(p, f)), (p, f)
+    for p in range(4):
+        assert net.counters(p)[1] == ref.counters(p)[1] == 0
+
+
+def test_four_population_workload_full_size_long_cluster_launches(gpu):
+    # the benchmarked launch shape: the whole 10,220-neuron network in one
+    # thread-block cluster, state in registers for 200 and then 1000 steps
+    # per launch, compared with the oracle after each launch
+    spec = I.config_four_pop(steps=1200)
+    net = gpu.Network.from_spec(spec)
+    assert net.engine == "cluster" and net.get_option("persist_steps") >= 1000
+    ref = oracle.from_spec(spec)
+    n_in = spec["pops"][0]["n"]
+    last_spike = np.full(n_in, -10)
+    co = np.zeros(n_in, np.int64)                            # oracle spikes per input neuron
+    done = 0
+    for launch in (200, 1000):
+        net.step(launch)
+        for _ in range(launch):
+            ref.step()
+            s = ref.spikes(0)
+            co[s] += 1
+            last_spike[s] = done
+            done += 1
+        _compare_long_launch(net, ref)
+        # per-neuron spike counts of the input population: equal, except for
+        # a spike in the launch's last step that FP32 may place one step later
+        cg = net.read_host(0, "neuron_spikes")[:n_in].astype(np.int64)
+        diff = np.nonzero(cg != co)[0]
+        assert all(last_spike[i] >= done - 1 and abs(cg[i] - co[i]) == 1 for i in diff), diff
+        assert net.counters(0)[0] == cg.sum() and ref.counters(0)[0] == co.sum()
+
+
+def test_four_population_workload_10000_step_rates(gpu):
+    # population rates over the benchmarked 10,000 steps (ten 1000-step
+    # cluster launches) within 2 % + one spike of the oracle's
+    spec = I.config_four_pop(steps=10000)
+    net = gpu.Network.from_spec(spec)
+    ref = oracle.from_spec(spec)
+    net.step(10000)
+    ref.step(10000)
+    for p in range(4):
+        cg, co = net.counters(p)[0], ref.counters(p)[0]
+        assert abs(cg - co) <= 0.02 * co + 1, (p, cg, co)
+    assert ref.counters(0)[0] > 1000
+    _compare_long_launch(net, ref)
 
 
 def test_population_rates_within_2_percent(gpu):
