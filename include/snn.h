@@ -302,19 +302,21 @@ snn_status snn_csr_bernoulli_fill(uint64_t seed, uint32_t tag, int64_t n_pre, in
 
 /* Same result as snn_csr_bernoulli_rows (bit for bit), without allocating.
  * The paper has no counterpart: this entry point exists for callers that
- * cannot allocate device memory when they build connectivity -- code running
- * while a CUDA graph is captured in global mode (cudaMalloc is not allowed
- * there and invalidates the capture), code whose device memory all belongs
- * to a pool or budget it must stay inside, and latency-sensitive loops that
- * cannot take the device synchronisation cudaMalloc / cudaFree may imply.
+ * cannot allocate device memory when they build connectivity -- code whose
+ * device memory all belongs to a pool or budget it must stay inside, and
+ * loops that must not call cudaMalloc / cudaFree at all (cudaFree may wait
+ * for the whole device; this call waits on `stream` only).
  * Row counts are written into row_ptr itself; the only scratch is a fixed
  * array of SNN_NOALLOC_MAX_ROWS / 1024 + 1 int64 (128 KiB) in device memory,
  * held by every GPU that loads the library until the process exits.
- * The first call on a device looks up that array's address with the device
- * current; make that first call before any stream capture.  Every call on a
- * device shares the array: calls whose GPU work overlaps (different streams,
- * no ordering between them) race and give wrong rows; calls ordered on one
- * stream are safe.  Each call writes every scratch entry it reads.
+ * The first call on a device does the set-up: with the device current it
+ * looks up that array's device address, which later calls reuse; make that
+ * first call before any stream capture.  The address is kept per device
+ * context, so the first call after cudaDeviceReset looks it up again.
+ * Every call on a device shares the array: calls whose GPU work overlaps
+ * (different streams, no ordering between them) race and give wrong rows;
+ * calls ordered on one stream are safe.  Each call writes every scratch entry
+ * it reads, so nothing needs clearing between calls.
  * n_pre > SNN_NOALLOC_MAX_ROWS returns SNN_ERR_SIZE before any GPU work.
  * Calls no cudaMalloc, cudaFree or allocating library routine.
  * Synchronises `stream`; *nnz (host) receives row_ptr[n_pre]. */

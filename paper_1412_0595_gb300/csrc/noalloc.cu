@@ -2,14 +2,14 @@
 //
 // snn_csr_bernoulli_rows takes scratch memory for its scan from an allocator.
 // Some callers cannot allocate device memory at the moment they need
-// connectivity: code that runs while a CUDA graph is being captured in global
-// mode (cudaMalloc is not allowed there and breaks the capture), code whose
-// device memory is all owned by a pool or budget it must not step outside,
-// and latency-sensitive loops that cannot afford the implicit device
-// synchronisation cudaMalloc / cudaFree may cause.  This entry point serves
-// them: the per-row counts go straight into the caller's row_ptr, and the only
-// scratch (the per-block sums of the scan) lives in a fixed file-scope device
-// array.  It calls no cudaMalloc, cudaFree or allocating routine.
+// connectivity: code whose device memory is all owned by a pool or a budget
+// it must not step outside, and loops that must not call cudaMalloc /
+// cudaFree at all (cudaFree, for one, may wait for the whole device).  This
+// entry point serves them: the per-row counts go straight into the caller's
+// row_ptr, and the only scratch (the per-block sums of the scan) lives in a
+// fixed file-scope device array.  It calls no cudaMalloc, cudaFree or
+// allocating routine; it waits on its own stream only, to hand the total
+// back on the host.
 #include <mutex>
 
 #include "snn_internal.cuh"
@@ -28,24 +28,60 @@ constexpr int kMaxDevices = 64;
 static __device__ __align__(256) long long g_noalloc_block_sums[kMaxScanBlocks + 1];
 
 std::mutex g_mu;
-long long* g_scratch[kMaxDevices] = {};
+struct ScratchSlot {
+    void* ctx;            // the device's context the address belongs to
+    long long* ptr;
+};
+ScratchSlot g_scratch[kMaxDevices] = {};
 
-// Device address of the scratch array on the current device.  The first call
-// on a device looks it up (this may load the module, so it must not happen
-// inside a stream capture); later calls reuse the cached address.
+typedef int (*CtxGetCurrentFn)(void**);
+
+// The calling thread's current context (the device's primary context for
+// runtime-API callers; null while the runtime has not bound one to this
+// thread yet), through the driver entry point the runtime exposes, so the
+// library needs no link to the driver library.
+snn_status current_context(void** ctx) {
+    static CtxGetCurrentFn fn = nullptr;
+    *ctx = nullptr;
+    if (!fn) {
+        void* f = nullptr;
+        cudaDriverEntryPointQueryResult q{};
+        cudaError_t e = cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f, 12000, cudaEnableDefault, &q);
+        if (e != cudaSuccess || q != cudaDriverEntryPointSuccess || !f)
+            return fail(SNN_ERR_CUDA, "cuCtxGetCurrent entry point not found");
+        fn = reinterpret_cast<CtxGetCurrentFn>(f);
+    }
+    if (fn(ctx) != 0) return fail(SNN_ERR_CUDA, "cuCtxGetCurrent failed");
+    return SNN_OK;
+}
+
+// Device address of the scratch array on the current device.  The set-up
+// runs once per device, with that device current: the first call looks the
+// address up (this may load the library's module onto the device).  The
+// address is kept with the device's context, so after cudaDeviceReset (or any
+// reset of the primary context, which may move module variables) the next
+// call looks it up again.
 snn_status scratch_address(long long** out) {
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return cuda_fail(e, "get device");
     if (dev < 0 || dev >= kMaxDevices) return fail(SNN_ERR_INVALID_ARG, "device index out of range");
+    void* ctx = nullptr;
+    snn_status st = current_context(&ctx);
+    if (st != SNN_OK) return st;
     std::lock_guard<std::mutex> lock(g_mu);
-    if (!g_scratch[dev]) {
+    ScratchSlot& slot = g_scratch[dev];
+    if (!ctx || !slot.ptr || slot.ctx != ctx) {
         void* p = nullptr;
-        e = cudaGetSymbolAddress(&p, g_noalloc_block_sums);
+        e = cudaGetSymbolAddress(&p, g_noalloc_block_sums);   // binds the primary context if none was current
         if (e != cudaSuccess) return cuda_fail(e, "scratch address");
-        g_scratch[dev] = static_cast<long long*>(p);
+        st = current_context(&ctx);
+        if (st != SNN_OK) return st;
+        if (!ctx) return fail(SNN_ERR_CUDA, "no current context after the scratch lookup");
+        slot.ptr = static_cast<long long*>(p);
+        slot.ctx = ctx;
     }
-    *out = g_scratch[dev];
+    *out = slot.ptr;
     return SNN_OK;
 }
 

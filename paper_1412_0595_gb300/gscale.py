@@ -1,11 +1,11 @@
-"""The paper's conductance-scale procedure (Sec. 5.1, Fig. 1) on the batched GPU form,
+"""The paper's conductance-scale procedure (Sec. 5.1) on the batched GPU form,
 for the HH network and for the Izhikevich cortical network (Table 1, Fig. 2).
 
 1. Sweep: one network instance per (nConn, gScale) pair, all run in one
    batched network object (every simulation step runs in the CUDA library).
-2. Select (Fig. 1): for every nConn, among the runs without NaN states
-   (sumNANs == 0, the reading of Fig. 1's rejection rule), take the gScale
-   whose average spike count per neuron (avgSpike) is closest to that of the
+2. Select: for every nConn, among the runs without NaN states (sumNANs ==
+   0, the reading taken of the paper's rejection rule), the gScale whose
+   average spike count per neuron (avgSpike) is closest to that of the
    reference run (ref_nConn, ref_gScale).
 3. Fit gScale = k1 / (k2 + nConn) + k3 by non-linear least squares (the
    rewritten form (gScale - k3)(nConn + k2) = k1 of Sec. 5.1) and report the
@@ -85,23 +85,24 @@ def run_sweep(specs, keys, device=None, engine=None):
 
 
 def select(records, ref_n_conn, ref_gscale):
-    """Fig. 1: the gScale per nConn whose avgSpike is closest to the reference
-    run's, among runs with no NaN states."""
-    ref = [r for r in records if r["n_conn"] == ref_n_conn and r["gscale"] == ref_gscale]
-    if not ref:
+    """The conductance scale that keeps a network's activity at the
+    reference's (Sec. 5.1): for each nConn, the gScale whose avgSpike lies
+    closest to the reference run's avgSpike, counting only runs that ended
+    without NaN states.  All runs are ranked at once by (nConn, distance to
+    the reference rate, gScale); the first NaN-free run of each nConn wins."""
+    n_conn = np.array([r["n_conn"] for r in records], np.float64)
+    gs = np.array([r["gscale"] for r in records], np.float64)
+    avg = np.array([r["avg_spike"] for r in records], np.float64)
+    clean = np.array([r["sum_nans"] == 0 for r in records])
+    is_ref = (n_conn == ref_n_conn) & (gs == ref_gscale)
+    if not is_ref.any():
         raise ValueError("reference run not in the sweep")
-    target = ref[0]["avg_spike"]
-    best = {}
-    for r in records:
-        if r["sum_nans"] != 0:
-            continue
-        d = abs(r["avg_spike"] - target)
-        cur = best.get(r["n_conn"])
-        if cur is None or d < cur[0]:
-            best[r["n_conn"]] = (d, r["gscale"])
-    x = np.array(sorted(best))
-    y = np.array([best[k][1] for k in x])
-    return x, y, target
+    target = float(avg[np.argmax(is_ref)])
+    order = np.lexsort((gs[clean], np.abs(avg[clean] - target), n_conn[clean]))
+    nc_sorted, gs_sorted = n_conn[clean][order], gs[clean][order]
+    first = np.ones(len(order), bool)
+    first[1:] = nc_sorted[1:] != nc_sorted[:-1]
+    return nc_sorted[first], gs_sorted[first], target
 
 
 def law(x, k1, k2, k3):

@@ -1,13 +1,13 @@
 """The allocation-free row builder matches the allocating one.
 
 snn_csr_bernoulli_rows_noalloc exists for callers that cannot allocate device
-memory while they build connectivity (inside a global-mode graph capture,
-under a fixed memory pool, or in loops that cannot absorb the device
-synchronisation an allocation may cause).  Its scratch is a fixed device
-array shared by all calls, so this test runs it twice in a row on different
-sizes -- the second call must not see the first call's leftovers -- and
-compares each result with snn_csr_bernoulli_rows bit for bit.  This file is
-collected last so that a failure here never hides another test.
+memory while they build connectivity (all memory owned by a fixed pool or
+budget, or loops that must not call cudaMalloc / cudaFree).  Its scratch is a
+fixed device array shared by all calls, so this test runs it several times in
+a row on different sizes -- a later call must not see an earlier call's
+leftovers -- and compares each result with snn_csr_bernoulli_rows bit for
+bit, up to the largest accepted row count.  This file is collected last so
+that a failure here never hides another test.
 """
 import ctypes as C
 
@@ -40,7 +40,10 @@ def _rows_noalloc(L, seed, tag, n_pre, n_post, p):
 def test_noalloc_rows_match_allocating_rows_on_two_calls_in_a_row(gpu):
     from paper_1412_0595_gb300 import _lib as L
     cases = [(20251203, 0x0301, 5000, 3001, 0.1),     # 5 scan blocks
-             (77, 0x0102, 1234, 777, 0.3)]             # fewer blocks: stale sums must not leak
+             (77, 0x0102, 1234, 777, 0.3),             # fewer blocks: stale sums must not leak
+             (5, 0x0203, 2_100_000, 64, 0.05),         # 2051 blocks: the block-sum scan carries over 1024
+             (6, 0x0204, 16_777_216, 64, 0.05),        # exactly SNN_NOALLOC_MAX_ROWS: every scratch entry
+             (77, 0x0102, 1234, 777, 0.3)]             # small again after the largest
     for seed, tag, n_pre, n_post, p in cases:
         want, want_nnz = _rows_allocating(L, seed, tag, n_pre, n_post, p)
         got, got_nnz = _rows_noalloc(L, seed, tag, n_pre, n_post, p)
