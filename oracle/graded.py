@@ -31,6 +31,8 @@ def _bind(L):
     L.oracle_graded_forward.restype = C.c_double
     L.oracle_graded_backward.argtypes = [C.c_void_p, f64p, C.POINTER(f64p)]
     L.oracle_graded_backward.restype = C.c_int
+    L.oracle_graded_backward_dy.argtypes = [C.c_void_p, f64p, f64p, C.POINTER(f64p)]
+    L.oracle_graded_backward_dy.restype = C.c_int
     L.oracle_graded_get_scale.argtypes = [C.c_void_p, C.c_int]
     L.oracle_graded_get_scale.restype = C.c_double
     L.oracle_graded_set_scale.argtypes = [C.c_void_p, C.c_int, C.c_double]
@@ -136,12 +138,21 @@ class GradedOracle:
         loss = lib().oracle_graded_forward(self.h, T, _p(target, C.c_double), _p(y, C.c_double))
         return loss, y
 
-    def backward(self):
+    def backward(self, dL_dy=None):
+        """Gradients of the forward pass's squared-error loss, or, with
+        dL_dy (T x n_out, dL/dy of the filter values the forward returned),
+        of any loss of y."""
         from . import lib
         gs = np.zeros(len(self.nnz))
         gw = [np.zeros(max(n, 1)) for n in self.nnz]
         arr = (C.POINTER(C.c_double) * max(1, len(gw)))(*[_p(a, C.c_double) for a in gw])
-        if lib().oracle_graded_backward(self.h, _p(gs, C.c_double), arr) != 0:
+        if dL_dy is None:
+            rc = lib().oracle_graded_backward(self.h, _p(gs, C.c_double), arr)
+        else:
+            d = np.ascontiguousarray(dL_dy, dtype=np.float64)
+            assert d.ndim == 2 and d.shape[1] == self.n_out
+            rc = lib().oracle_graded_backward_dy(self.h, _p(d, C.c_double), _p(gs, C.c_double), arr)
+        if rc != 0:
             raise RuntimeError("no recorded forward")
         return gs, [a[:n] for a, n in zip(gw, self.nnz)]
 

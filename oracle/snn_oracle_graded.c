@@ -275,8 +275,11 @@ double oracle_graded_forward(graded_net* g, int T, const double* target, double*
     return g->loss;
 }
 
-/* Reverse sweep: grad_scale[q] and grad_w[q][e] (compressed-row order). */
-int oracle_graded_backward(graded_net* g, double* grad_scale, double** grad_w)
+/* Reverse sweep: grad_scale[q] and grad_w[q][e] (compressed-row order) of a
+ * loss whose gradient with respect to the output filter is dL_dy[t][i] =
+ * dL / dy_i(t + 1) (T * N_out values); NULL takes the squared-error loss L of
+ * the forward pass, dL_dy = 2 (y - target) / (T * N_out). */
+static int graded_backward(graded_net* g, const double* dL_dy, double* grad_scale, double** grad_w)
 {
     if (!g->V || g->T <= 0) return -1;
     const int N = g->N, T = g->T;
@@ -302,7 +305,10 @@ int oracle_graded_backward(graded_net* g, double* grad_scale, double** grad_w)
         /* loss term of step t on y(t + 1) */
         for (int i = 0; i < n_out; ++i) {
             int k = OP->off + i;
-            ly[k] += nrm * (g->y[(size_t)(t + 1) * N + k] - g->target[(size_t)t * n_out + i]);
+            if (dL_dy)
+                ly[k] += dL_dy[(size_t)t * n_out + i];
+            else
+                ly[k] += nrm * (g->y[(size_t)(t + 1) * N + k] - g->target[(size_t)t * n_out + i]);
         }
         /* drive current of this step (recomputed, it holds no parameter) */
         for (int p = 0; p < g->n_pops; ++p) {
@@ -403,4 +409,16 @@ int oracle_graded_backward(graded_net* g, double* grad_scale, double** grad_w)
     }
     free(lV); free(lm); free(lh); free(ln); free(ly); free(nV); free(mu); free(nu); free(ie_now);
     return 0;
+}
+
+int oracle_graded_backward(graded_net* g, double* grad_scale, double** grad_w)
+{
+    return graded_backward(g, NULL, grad_scale, grad_w);
+}
+
+/* The adjoint seeded by the caller's dL/dy (T * N_out values, step-major). */
+int oracle_graded_backward_dy(graded_net* g, const double* dL_dy, double* grad_scale, double** grad_w)
+{
+    if (!dL_dy) return -1;
+    return graded_backward(g, dL_dy, grad_scale, grad_w);
 }

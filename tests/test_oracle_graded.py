@@ -207,3 +207,84 @@ def test_dense_storage_equals_compressed_rows_of_the_same_matrix():
     n_post = spec_c["pops"][2]["n"]
     rows = np.repeat(np.arange(len(rp) - 1), np.diff(rp))
     assert np.allclose(gwd[2][rows * n_post + col], gwc[2], rtol=1e-10, atol=1e-300)
+
+
+def _cubic(y, target):
+    """A loss other than the squared error: mean |y - target|^3, and its dL/dy."""
+    d = y - target
+    n = d.size
+    return float(np.sum(np.abs(d) ** 3) / n), 3.0 * np.abs(d) * d / n
+
+
+def _fd_check_loss(g, target, loss_fn, scale_step, weight_step, n_weights=3, seed=0):
+    """Like _fd_check, for the loss loss_fn(y, target) of the forward pass's
+    filter values y, with the adjoint seeded by its dL/dy."""
+    _, y = g.forward(target)
+    _, dl = loss_fn(y, target)
+    gs, gw = g.backward(dL_dy=dl)
+
+    def L():
+        return loss_fn(g.forward(target)[1], target)[0]
+
+    worst = 0.0
+    for q in range(len(gs)):
+        s0 = g.scale(q)
+        h = scale_step * abs(s0)
+        g.set_scale(q, s0 + h)
+        lp = L()
+        g.set_scale(q, s0 - h)
+        lm = L()
+        g.set_scale(q, s0)
+        worst = max(worst, abs((lp - lm) / (2 * h) - gs[q]) / max(abs(gs[q]), 1e-300))
+    rng = np.random.default_rng(seed)
+    for q in range(len(gw)):
+        idx = list(np.argsort(-np.abs(gw[q]))[:n_weights]) + list(rng.choice(len(gw[q]), n_weights, replace=False))
+        floor = 1e-3 * np.abs(gw[q]).max()
+        for k in idx:
+            w0 = g.weight(q, k)
+            h = weight_step * max(abs(w0), 1e-3)
+            g.set_weight(q, k, w0 + h)
+            lp = L()
+            g.set_weight(q, k, w0 - h)
+            lm = L()
+            g.set_weight(q, k, w0)
+            worst = max(worst, abs((lp - lm) / (2 * h) - gw[q][k]) / max(abs(gw[q][k]), floor, 1e-300))
+    return worst, gs
+
+
+def test_adjoint_seeded_by_dl_dy_equals_the_squared_error_adjoint():
+    # dL/dy = 2 (y - target) / (T n_out) is the squared-error loss's own seed
+    spec = I.config_graded_small(steps=400)
+    g = GradedOracle(spec)
+    target = I.target_trace(spec, 400, g.n_out).astype(np.float64)
+    _, y = g.forward(target)
+    gs0, gw0 = g.backward()
+    gs1, gw1 = g.backward(dL_dy=2.0 * (y - target) / y.size)
+    assert np.allclose(gs1, gs0, rtol=1e-12, atol=0)
+    for a, b in zip(gw1, gw0):
+        assert np.allclose(a, b, rtol=1e-11, atol=1e-14 * np.abs(b).max())
+
+
+def test_adjoint_of_another_loss_matches_central_differences():
+    # a loss of y other than the squared error (mean |y - target|^3): the
+    # adjoint seeded by its dL/dy against central differences of that loss,
+    # on the smooth network (no spikes) and on the 200-neuron copy
+    pops = [I.hh_pop(20, v0_range=(-26.0, -14.0)), _passive(30), _passive(10)]
+    pops[0]["hh"]["C"] = 1e300
+    for d in pops[1:]:
+        d["v0_range"] = (-64.0, -60.0)
+    projs = [_graded_proj(0, 1, 0.0, p=0.5), _graded_proj(1, 1, 0.0, p=0.3), _graded_proj(1, 2, 0.0, p=0.5)]
+    for d, wmax in zip(projs, (5.0, 1.0, 5.0)):
+        d["weight"] = ("uniform", 0.0, wmax)
+    projs[1]["v_thr"] = projs[2]["v_thr"] = -62.0
+    spec = I.net(pops, projs, dt=0.05, steps=1)
+    g = GradedOracle(spec)
+    target = I.target_trace(spec, 600, g.n_out).astype(np.float64)
+    worst, gs = _fd_check_loss(g, target, _cubic, scale_step=1e-3, weight_step=1e-3)
+    assert np.all(np.abs(gs) > 1e-4)
+    assert worst < 1e-5
+    spec = I.config_graded_small(steps=2000)
+    g = GradedOracle(spec)
+    target = I.target_trace(spec, 2000, g.n_out).astype(np.float64)
+    worst, gs = _fd_check_loss(g, target, _cubic, scale_step=1e-8, weight_step=1e-7)
+    assert worst < 5e-4
