@@ -567,12 +567,21 @@ snn_status create_impl(const snn_pop_desc* pops, int32_t n_pops, const snn_proj_
     CK(persistent_capacity(net->sm_count, &net->persist_grid), "persistent occupancy");
     {
         int per = 0;
-        const int cl = cluster_plan(net->num_tiles * kTile, n_pops, &per);
+        const int cl = cluster_plan(net->num_tiles * kTile, n_pops, n_projs, &per);
+        // compressed rows, in projection order, whose segments fit the shared cache
+        int seg_rows = 0;
+        for (int q = 0; q < n_projs; ++q) {
+            if (net->projs[q].d.layout != SNN_LAYOUT_CSR) continue;
+            const int n_pre = pops[net->projs[q].d.pre].n;
+            if (seg_rows + n_pre > kClusterSegCacheRows) break;
+            seg_rows += n_pre;
+        }
         bool ok = false;
         if (cl && !graded_requested(projs, n_projs))
-            CK(cluster_supported(cl, per, net->num_tiles, &ok), "cluster occupancy");
+            CK(cluster_supported(cl, per, net->num_tiles, seg_rows, &ok), "cluster occupancy");
         net->cluster_size = ok ? cl : 0;
         net->cluster_per_cta = ok ? per : 0;
+        net->cluster_seg_rows = ok ? seg_rows : 0;
         for (int q = 0; ok && q < n_projs; ++q) {   // each row's segment in each CTA's slice
             ProjHost& P = net->projs[q];
             if (P.d.layout != SNN_LAYOUT_CSR) continue;
@@ -673,7 +682,8 @@ snn_status snn_step(snn_net* net, int64_t n_steps, void* stream) {
         if (use_cluster(net)) {
             for (int64_t left = n_steps; left > 0;) {
                 const int32_t k = (int32_t)std::min<int64_t>(left, net->persist_steps);
-                CK(launch_cluster(persist_args(net, k), net->cluster_size, net->cluster_per_cta, s), "cluster steps");
+                CK(launch_cluster(persist_args(net, k), net->cluster_size, net->cluster_per_cta,
+                                  (int)net->projs.size(), net->cluster_seg_rows, s), "cluster steps");
                 left -= k;
             }
             return SNN_OK;
@@ -889,7 +899,8 @@ snn_status snn_launch_phase(snn_net* net, int32_t phase, void* stream) {
     cudaStream_t s = (cudaStream_t)stream;
     if (phase == 4) {
         if (net->cluster_size == 0) return fail(SNN_ERR_STATE, "network does not fit one cluster");
-        CK(launch_cluster(persist_args(net, net->persist_steps), net->cluster_size, net->cluster_per_cta, s),
+        CK(launch_cluster(persist_args(net, net->persist_steps), net->cluster_size, net->cluster_per_cta,
+                          (int)net->projs.size(), net->cluster_seg_rows, s),
            "cluster phase");
     } else if (phase == 3) {
         if (!net->dbg_staged) return fail(SNN_ERR_STATE, "no spike list staged by snn_debug_propagate");

@@ -26,9 +26,11 @@ namespace snn {
 
 namespace {
 
-constexpr int kCT = 1024;          // threads per CTA
+constexpr int kCT = 1024;          // a CTA's slice holds up to 4 kCT neurons
+constexpr int kMaxThreads = 512;   // threads per CTA at most (128 registers a thread)
 constexpr int kMaxSlicePops = 4 * kCT / kTile + 1;   // populations one CTA's slice can touch
 constexpr int kMaxClusterTiles = 16 * 4 * kCT / kTile;  // tiles of the largest network one cluster holds
+constexpr int kMaxClusterProjs = 64;                 // projections of a network the cluster engine runs
 
 __device__ __forceinline__ void st_cluster_u64(const unsigned long long* local_addr, int rank, unsigned long long v) {
     const uint32_t laddr = (uint32_t)__cvta_generic_to_shared(local_addr);
@@ -44,24 +46,44 @@ __device__ __forceinline__ uint32_t word_spikes(unsigned long long w, uint32_t t
     return (uint32_t)(w >> 32) == tag ? (uint32_t)w : 0u;
 }
 
+// What a pull needs of a projection, copied into shared memory at launch
+// start so that a spike's row costs one dependent global load (its synapses).
+struct ClusterProj {
+    const int32_t* col;
+    const float* w;
+    const int64_t* csplit;     // [n_pre][cluster size + 1] row segments per CTA slice
+    int32_t layout, channel, post_soa, n_post;
+    float scale;
+    int32_t seg_off;           // compressed rows: first row in the shared segment cache, or -1
+};
+
 // Adds this CTA's share of the outgoing rows of spiking neuron `idx` (SoA
 // index) into the shared accumulators: part `sub` of `parts` (warps) of the
 // segment of each row whose post neurons lie in [base, base + per_cta), with
 // up to four synapses per lane in flight.
-__device__ __forceinline__ void pull_row(const PersistArgs& A, const int32_t* s_tile_pop, const int32_t* s_tile_local,
-                                         const int32_t* s_out_begin, int idx, int rank, int n_ranks, int base,
-                                         int per_cta, float* acc, int sub, int parts, int lane) {
+__device__ __forceinline__ void pull_row(const ClusterProj* s_proj, const int32_t* s_out_list,
+                                         const longlong2* s_seg, const int32_t* s_tile_pop,
+                                         const int32_t* s_tile_local, const int32_t* s_out_begin, int idx, int rank,
+                                         int n_ranks, int base, int per_cta, float* acc, int sub, int parts, int lane) {
     const int tile = idx / kTile;
     const int p = s_tile_pop[tile];
     const int local = s_tile_local[tile] + (idx % kTile);
     const int stride = 32 * parts;
     for (int qq = s_out_begin[p]; qq < s_out_begin[p + 1]; ++qq) {
-        const DevProj& Q = A.projs[__ldg(A.out_list + qq)];
+        const ClusterProj& Q = s_proj[s_out_list[qq]];
         const float sc = Q.scale;
         float* mine = acc + Q.channel * per_cta + (Q.post_soa - base);
         if (Q.layout == SNN_LAYOUT_CSR) {
-            const int64_t* sp = Q.csplit + (int64_t)local * (n_ranks + 1) + rank;
-            const int64_t sb = __ldg(sp), se = __ldg(sp + 1);
+            int64_t sb, se;
+            if (Q.seg_off >= 0) {
+                const longlong2 g = s_seg[Q.seg_off + local];
+                sb = g.x;
+                se = g.y;
+            } else {
+                const int64_t* sp = Q.csplit + (int64_t)local * (n_ranks + 1) + rank;
+                sb = __ldg(sp);
+                se = __ldg(sp + 1);
+            }
             int64_t x = sb + 32 * sub + lane;
             for (; x + 3 * stride < se; x += 4 * stride) {
                 int c[4];
@@ -89,14 +111,17 @@ __device__ __forceinline__ void pull_row(const PersistArgs& A, const int32_t* s_
     }
 }
 
-template <int NPT>
-__global__ void __launch_bounds__(kCT, 1) k_step_cluster(const PersistArgs A, int per_cta) {
+template <int PPT, int MAXT>
+__global__ void __launch_bounds__(MAXT, 1) k_step_cluster(const PersistArgs A, int per_cta, int n_projs, int seg_rows) {
     extern __shared__ float s_mem[];
-    // spike words [2 parities][n_words] (8-byte aligned at the start), then the
-    // accumulators [step parity][channel 0/1][per_cta]
-    unsigned long long* bits = reinterpret_cast<unsigned long long*>(s_mem);
+    // row segments [seg_rows] (16-byte aligned at the start), spike words
+    // [2 parities][n_words], then the accumulators [step parity][channel 0/1][per_cta]
+    longlong2* s_seg = reinterpret_cast<longlong2*>(s_mem);
+    unsigned long long* bits = reinterpret_cast<unsigned long long*>(s_seg + seg_rows);
     const int n_words = A.n.num_tiles * (kTile / 32);
     float* acc = reinterpret_cast<float*>(bits + 2 * n_words);
+    __shared__ ClusterProj s_proj[kMaxClusterProjs];
+    __shared__ int32_t s_out_list[kMaxClusterProjs];
     __shared__ DevPop s_pops[kMaxSlicePops];
     __shared__ int32_t s_tile_pop[kMaxClusterTiles], s_tile_local[kMaxClusterTiles];
     __shared__ int32_t s_out_begin[kMaxClusterTiles + 1];
@@ -108,6 +133,8 @@ __global__ void __launch_bounds__(kCT, 1) k_step_cluster(const PersistArgs A, in
     const NeuronArgs& a = A.n;
     const int n_ranks = (int)cluster.num_blocks();
     const int rank = (int)cluster.block_rank();
+    const int T = (int)blockDim.x;
+    const int n_warps = T / 32;
     const int base = rank * per_cta;                       // first owned SoA index
     const int n_soa = a.num_tiles * kTile;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -119,16 +146,46 @@ __global__ void __launch_bounds__(kCT, 1) k_step_cluster(const PersistArgs A, in
     const int p_lo = base < n_soa ? a.tile_pop[base / kTile] : 0;
     const int p_hi = last_idx >= base ? a.tile_pop[last_idx / kTile] : p_lo - 1;
     for (int p = p_lo; p <= p_hi; ++p) copy_pop(s_pops + (p - p_lo), a.pops + p);
-    for (int j = threadIdx.x; j < 4 * per_cta; j += kCT) acc[j] = 0.0f;
-    for (int j = threadIdx.x; j < 2 * n_words; j += kCT) bits[j] = 0ull;
-    for (int p = threadIdx.x; p < kMaxSlicePops; p += kCT) s_pop_spikes[p] = 0ull;
-    for (int tl = threadIdx.x; tl < a.num_tiles; tl += kCT) {
+    for (int j = threadIdx.x; j < 4 * per_cta; j += T) acc[j] = 0.0f;
+    for (int j = threadIdx.x; j < 2 * n_words; j += T) bits[j] = 0ull;
+    for (int p = threadIdx.x; p < kMaxSlicePops; p += T) s_pop_spikes[p] = 0ull;
+    for (int tl = threadIdx.x; tl < a.num_tiles; tl += T) {
         const int p = a.tile_pop[tl];
         s_tile_pop[tl] = p;
         s_tile_local[tl] = (tl - a.pops[p].first_tile) * kTile;
     }
     const int n_pops = a.tile_pop[a.num_tiles - 1] + 1;
-    for (int p = threadIdx.x; p <= n_pops; p += kCT) s_out_begin[p] = A.out_begin[p];
+    for (int p = threadIdx.x; p <= n_pops; p += T) s_out_begin[p] = A.out_begin[p];
+    for (int q = threadIdx.x; q < n_projs; q += T) {
+        const DevProj& Q = A.projs[q];
+        ClusterProj c;
+        c.col = Q.col;
+        c.w = Q.w;
+        c.csplit = Q.csplit;
+        c.layout = Q.layout;
+        c.channel = Q.channel;
+        c.post_soa = Q.post_soa;
+        c.n_post = Q.n_post;
+        c.scale = Q.scale;
+        // compressed rows, in projection order, share the segment cache while it has room
+        int off = 0;
+        for (int r = 0; r < q; ++r)
+            if (A.projs[r].layout == SNN_LAYOUT_CSR) off += A.projs[r].n_pre;
+        c.seg_off = (Q.layout == SNN_LAYOUT_CSR && off + Q.n_pre <= seg_rows) ? off : -1;
+        s_proj[q] = c;
+        s_out_list[q] = A.out_list[q];
+    }
+    __syncthreads();
+    // this CTA's segment of every cached compressed row
+    for (int q = 0; q < n_projs; ++q) {
+        const ClusterProj& Q = s_proj[q];
+        if (Q.seg_off < 0) continue;
+        const int n_pre = A.projs[q].n_pre;
+        for (int i = threadIdx.x; i < n_pre; i += T) {
+            const int64_t* sp = Q.csplit + (int64_t)i * (n_ranks + 1) + rank;
+            s_seg[Q.seg_off + i] = make_longlong2(sp[0], sp[1]);
+        }
+    }
     __syncthreads();
     // Heavy rows: populations whose outgoing rows put, on average, 64 or more
     // synapses into one CTA's slice.  Every warp takes a share of each of their
@@ -147,7 +204,7 @@ __global__ void __launch_bounds__(kCT, 1) k_step_cluster(const PersistArgs A, in
                     work += (float)Q.n_post / n_ranks;
             }
             const int n_in_tile = min(kTile, P.n - s_tile_local[tl]);
-            const int words = (n_in_tile + 31) / 32;
+            const int words = 2 * ((n_in_tile + 63) / 64);  // both halves of each 64-neuron group
             s_tile_heavy[tl] = work >= 64.0f ? 1 : 0;
             if (work >= 64.0f) {
                 for (int j = 0; j < words; ++j)
@@ -162,36 +219,54 @@ __global__ void __launch_bounds__(kCT, 1) k_step_cluster(const PersistArgs A, in
         s_n_heavy = nh;
     }
 
-    NeuronState st[NPT];
-    int pop_of[NPT], local_of[NPT], n_spk[NPT];
-    bool live[NPT];
+    NeuronPair st[PPT];
+    int pop_of[PPT], local_of[PPT];
+    int2 n_spk[PPT];
+    unsigned live[PPT];                                    // bit e: neuron local + e exists
 #pragma unroll
-    for (int u = 0; u < NPT; ++u) {
-        const int off = threadIdx.x + u * kCT;
+    for (int u = 0; u < PPT; ++u) {
+        const int off = 2 * ((int)threadIdx.x + u * T);
         const int idx = base + off;
-        live[u] = false;
+        live[u] = 0u;
         pop_of[u] = 0;
         local_of[u] = 0;
-        n_spk[u] = 0;
-        st[u] = NeuronState{};
+        n_spk[u] = make_int2(0, 0);
+        st[u] = NeuronPair{};
         if (off < per_cta && idx < n_soa) {
             const int tile = idx / kTile;
             const int p = a.tile_pop[tile];
             const DevPop& P = a.pops[p];
             const int local = (tile - P.first_tile) * kTile + (idx % kTile);
             if (local < P.n) {
-                live[u] = true;
+                live[u] = local + 1 < P.n ? 3u : 1u;
                 pop_of[u] = p - p_lo;
                 local_of[u] = local;
-                if (P.kind != SNN_POP_SOURCE)
-                    st[u] = NeuronState{a.V[idx], a.m[idx], a.h[idx], a.n[idx], a.g0[idx], a.g1[idx], a.iext[idx]};
+                if (P.kind != SNN_POP_SOURCE) {
+                    // pairs start at even SoA offsets: 8-byte aligned loads
+                    st[u].V = *reinterpret_cast<const float2*>(a.V + idx);
+                    st[u].m = *reinterpret_cast<const float2*>(a.m + idx);
+                    st[u].h = *reinterpret_cast<const float2*>(a.h + idx);
+                    st[u].n = *reinterpret_cast<const float2*>(a.n + idx);
+                    st[u].g0 = *reinterpret_cast<const float2*>(a.g0 + idx);
+                    st[u].g1 = *reinterpret_cast<const float2*>(a.g1 + idx);
+                    st[u].ie = *reinterpret_cast<const float2*>(a.iext + idx);
+                }
             }
         }
+    }
+    // with one pair per thread, an HH pair's population constants stay in
+    // registers for the whole launch
+    HHPairConsts hc{};
+    bool hh_reg = false;
+    if (PPT == 1 && live[0]) {
+        const DevPop& P = a.pops[pop_of[0] + p_lo];
+        hh_reg = P.kind == SNN_POP_HH;
+        if (hh_reg) hc = hh_pair_consts(P, a.hs);
     }
     // the list lengths of the launch's last step (and of the step after it)
     // start at zero; only the last step writes the API spike list
 #pragma unroll
-    for (int u = 0; u < NPT; ++u)
+    for (int u = 0; u < PPT; ++u)
         if (live[u] && local_of[u] == 0) {
             s_pops[pop_of[u]].nspk[0] = 0;
             s_pops[pop_of[u]].nspk[1] = 0;
@@ -207,11 +282,11 @@ __global__ void __launch_bounds__(kCT, 1) k_step_cluster(const PersistArgs A, in
         // ---- pull: the previous step's spikes, my slice of their rows --------
         // Light rows: each lane reads one word; the warp then adds, spike by
         // spike, this CTA's segment of each row.  Heavy rows: every warp reads
-        // the heavy words and adds a 1/32 share of each segment.
+        // the heavy words and adds a 1/n_warps share of each segment.
         if (k > 0) {
             const unsigned long long* prev = bits + (slot ^ 1) * n_words;
             const uint32_t tag = (uint32_t)(e64 - 1ull);
-            for (int w0 = warp * 32; w0 < n_words; w0 += kCT) {
+            for (int w0 = warp * 32; w0 < n_words; w0 += T) {
                 const int wd = w0 + lane;
                 const uint32_t m = (wd < n_words && !s_tile_heavy[wd / (kTile / 32)]) ? word_spikes(prev[wd], tag) : 0u;
                 unsigned nz = __ballot_sync(0xffffffffu, m != 0u);
@@ -219,11 +294,12 @@ __global__ void __launch_bounds__(kCT, 1) k_step_cluster(const PersistArgs A, in
                     const int l = __ffs(nz) - 1;
                     nz &= nz - 1u;
                     uint32_t mm = __shfl_sync(0xffffffffu, m, l);
+                    const int w = w0 + l;
                     while (mm) {
                         const int bit = __ffs(mm) - 1;
                         mm &= mm - 1u;
-                        pull_row(A, s_tile_pop, s_tile_local, s_out_begin, (w0 + l) * 32 + bit, rank, n_ranks, base,
-                                 per_cta, acc_k, 0, 1, lane);
+                        pull_row(s_proj, s_out_list, s_seg, s_tile_pop, s_tile_local, s_out_begin,
+                                 64 * (w >> 1) + 2 * bit + (w & 1), rank, n_ranks, base, per_cta, acc_k, 0, 1, lane);
                     }
                 }
             }
@@ -240,8 +316,9 @@ __global__ void __launch_bounds__(kCT, 1) k_step_cluster(const PersistArgs A, in
                     while (mm) {
                         const int bit = __ffs(mm) - 1;
                         mm &= mm - 1u;
-                        pull_row(A, s_tile_pop, s_tile_local, s_out_begin, wd * 32 + bit, rank, n_ranks, base,
-                                 per_cta, acc_k, warp, kCT / 32, lane);
+                        pull_row(s_proj, s_out_list, s_seg, s_tile_pop, s_tile_local, s_out_begin,
+                                 64 * (wd >> 1) + 2 * bit + (wd & 1), rank, n_ranks, base, per_cta, acc_k, warp,
+                                 n_warps, lane);
                     }
                 }
             }
@@ -253,40 +330,59 @@ __global__ void __launch_bounds__(kCT, 1) k_step_cluster(const PersistArgs A, in
         unsigned long long* cur = bits + slot * n_words;
         bool wrote = false;                                // this warp stored spike words
 #pragma unroll
-        for (int u = 0; u < NPT; ++u) {
-            const int off = threadIdx.x + u * kCT;
+        for (int u = 0; u < PPT; ++u) {
+            const int off = 2 * ((int)threadIdx.x + u * T);
             const int idx = base + off;
-            bool spike = false;
+            unsigned spike = 0u;
             if (live[u]) {
                 const DevPop& P = s_pops[pop_of[u]];
                 if (P.kind != SNN_POP_SOURCE) {
-                    st[u].g0 += acc_k[off];
-                    st[u].g1 += acc_k[per_cta + off];
-                    acc_k[off] = 0.0f;
-                    acc_k[per_cta + off] = 0.0f;
+                    float2* a0 = reinterpret_cast<float2*>(acc_k + off);
+                    float2* a1 = reinterpret_cast<float2*>(acc_k + per_cta + off);
+                    st[u].g0 = vadd(st[u].g0, *a0);
+                    st[u].g1 = vadd(st[u].g1, *a1);
+                    *a0 = make_float2(0.0f, 0.0f);
+                    *a1 = make_float2(0.0f, 0.0f);
                 }
-                float isyn;
-                spike = neuron_step(P, key, t, local_of[u], a.hs, a.n_sub, st[u], &isyn);
+                float2 isyn;
+                if (PPT == 1 && hh_reg)
+                    spike = hh_step_pair(hc, key, t, local_of[u], a.n_sub, st[u], &isyn) & live[u];
+                else
+                    spike = neuron_step_pair(P, key, t, local_of[u], a.hs, a.n_sub, st[u], &isyn) & live[u];
                 if (P.kind != SNN_POP_SOURCE) {
-                    if (isnan(st[u].V)) atomicAdd(P.nan_count, 1ull);
-                    if (a.isyn_rec) a.isyn_rec[idx] = isyn;
+                    const int nans = (isnan(st[u].V.x) ? 1 : 0) + ((live[u] & 2u) && isnan(st[u].V.y) ? 1 : 0);
+                    if (nans) atomicAdd(P.nan_count, (unsigned long long)nans);
+                    if (a.isyn_rec) {
+                        a.isyn_rec[idx] = isyn.x;
+                        if (live[u] & 2u) a.isyn_rec[idx + 1] = isyn.y;
+                    }
                 }
-                n_spk[u] += spike ? 1 : 0;
+                n_spk[u].x += (int)(spike & 1u);
+                n_spk[u].y += (int)(spike >> 1);
             }
-            const unsigned ballot = __ballot_sync(0xffffffffu, spike);
-            if (ballot && off < per_cta) {
+            const unsigned b0 = __ballot_sync(0xffffffffu, spike & 1u);
+            const unsigned b1 = __ballot_sync(0xffffffffu, spike & 2u);
+            if ((b0 | b1) && off < per_cta) {
                 wrote = true;
-                // the warp's 32 neurons are one word of every CTA's spike words
-                const int wd = (base + u * kCT + warp * 32) / 32;
-                if (lane < n_ranks) st_cluster_u64(cur + wd, lane, ((unsigned long long)(uint32_t)e64 << 32) | ballot);
+                // the warp's 64 neurons are words 2g and 2g + 1 of every CTA's spike words
+                const int wd = (base + 2 * (u * T + warp * 32)) / 32;
+                const unsigned long long tg = (unsigned long long)(uint32_t)e64 << 32;
+                if (lane < n_ranks) {
+                    if (b0) st_cluster_u64(cur + wd, lane, tg | b0);
+                    if (b1) st_cluster_u64(cur + wd + 1, lane, tg | b1);
+                }
                 // a warp's neurons share one population
-                if (lane == 0) atomicAdd(s_pop_spikes + pop_of[u], (unsigned long long)__popc(ballot));
+                const int cnt = __popc(b0) + __popc(b1);
+                if (lane == 0) atomicAdd(s_pop_spikes + pop_of[u], (unsigned long long)cnt);
                 if (last) {                                // the API spike list of the last step
                     const DevPop& P = s_pops[pop_of[u]];
                     int pos = 0;
-                    if (lane == 0) pos = atomicAdd(P.nspk + slot, __popc(ballot));
+                    if (lane == 0) pos = atomicAdd(P.nspk + slot, cnt);
                     pos = __shfl_sync(0xffffffffu, pos, 0);
-                    if (spike) P.spk[pos + __popc(ballot & ((1u << lane) - 1u))] = local_of[u];
+                    const unsigned lt = (1u << lane) - 1u;
+                    const int before = pos + __popc(b0 & lt) + __popc(b1 & lt);
+                    if (spike & 1u) P.spk[before] = local_of[u];
+                    if (spike & 2u) P.spk[before + (int)(spike & 1u)] = local_of[u] + 1;
                 }
             }
         }
@@ -303,17 +399,27 @@ __global__ void __launch_bounds__(kCT, 1) k_step_cluster(const PersistArgs A, in
     // fold the last step's events (pulled above), write the state and the
     // launch's spike counts back
 #pragma unroll
-    for (int u = 0; u < NPT; ++u) {
+    for (int u = 0; u < PPT; ++u) {
         if (!live[u]) continue;
         const DevPop& P = s_pops[pop_of[u]];
-        if (n_spk[u]) P.neuron_spikes[local_of[u]] += n_spk[u];
+        if (n_spk[u].x) P.neuron_spikes[local_of[u]] += n_spk[u].x;
+        if (n_spk[u].y) P.neuron_spikes[local_of[u] + 1] += n_spk[u].y;
         if (P.kind == SNN_POP_SOURCE) continue;
-        const int off = threadIdx.x + u * kCT;
+        const int off = 2 * ((int)threadIdx.x + u * T);
         const int idx = base + off;
-        st[u].g0 += acc_end[off];
-        st[u].g1 += acc_end[per_cta + off];
-        a.V[idx] = st[u].V; a.m[idx] = st[u].m; a.h[idx] = st[u].h; a.n[idx] = st[u].n;
-        a.g0[idx] = st[u].g0; a.g1[idx] = st[u].g1; a.iext[idx] = st[u].ie;
+        st[u].g0 = vadd(st[u].g0, *reinterpret_cast<const float2*>(acc_end + off));
+        st[u].g1 = vadd(st[u].g1, *reinterpret_cast<const float2*>(acc_end + per_cta + off));
+        if (!(live[u] & 2u)) {                             // a padding slot (odd population size) stays zero
+            st[u].V.y = st[u].m.y = st[u].h.y = st[u].n.y = 0.0f;
+            st[u].g0.y = st[u].g1.y = st[u].ie.y = 0.0f;
+        }
+        *reinterpret_cast<float2*>(a.V + idx) = st[u].V;
+        *reinterpret_cast<float2*>(a.m + idx) = st[u].m;
+        *reinterpret_cast<float2*>(a.h + idx) = st[u].h;
+        *reinterpret_cast<float2*>(a.n + idx) = st[u].n;
+        *reinterpret_cast<float2*>(a.g0 + idx) = st[u].g0;
+        *reinterpret_cast<float2*>(a.g1 + idx) = st[u].g1;
+        *reinterpret_cast<float2*>(a.iext + idx) = st[u].ie;
     }
     const int tp = (int)threadIdx.x;                       // signed: an empty slice has p_hi - p_lo = -1
     if (tp <= p_hi - p_lo && s_pop_spikes[tp]) atomicAdd(s_pops[tp].spike_count, s_pop_spikes[tp]);
@@ -341,43 +447,65 @@ __global__ void k_cluster_splits(const int64_t* row_ptr, const int32_t* col, int
     }
 }
 
-size_t cluster_smem(int per_cta, int num_tiles) {
-    return sizeof(unsigned long long) * 2 * (size_t)num_tiles * (kTile / 32) + sizeof(float) * 4 * (size_t)per_cta;
+size_t cluster_smem(int per_cta, int num_tiles, int seg_rows) {
+    return sizeof(longlong2) * (size_t)seg_rows + sizeof(unsigned long long) * 2 * (size_t)num_tiles * (kTile / 32) +
+           sizeof(float) * 4 * (size_t)per_cta;
 }
 
-template <int NPT>
-cudaError_t launch_npt(const PersistArgs& a, int cl, int per_cta, cudaStream_t s) {
-    const size_t smem = cluster_smem(per_cta, a.n.num_tiles);
-    cudaError_t e = cudaFuncSetAttribute(k_step_cluster<NPT>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
-    if (e != cudaSuccess) return e;
-    // always opted in: the kernel's static shared memory counts toward the
-    // 48 KiB that a launch may use without the attribute
-    e = cudaFuncSetAttribute(k_step_cluster<NPT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
+// Threads of a CTA for a slice of per_cta neurons (a multiple of 64), at most
+// 512 so that a thread may hold 128 registers: one neuron pair per thread up
+// to 1024 neurons, two up to 2048, four above.
+int cluster_threads(int per_cta, int* ppt) {
+    *ppt = per_cta <= 1024 ? 1 : per_cta <= 2048 ? 2 : 4;
+    const int pairs = per_cta / 2;
+    return ((pairs + *ppt - 1) / *ppt + 31) / 32 * 32;
+}
+
+// The kernel instance for a slice: one pair per thread with at most 384
+// threads (up to 168 registers a thread), else at most 512 threads.
+const void* cluster_fn(int per_cta, int* threads) {
+    int ppt = 1;
+    *threads = cluster_threads(per_cta, &ppt);
+    if (ppt == 1 && *threads <= 384) return (const void*)k_step_cluster<1, 384>;
+    if (ppt == 1) return (const void*)k_step_cluster<1, kMaxThreads>;
+    if (ppt == 2) return (const void*)k_step_cluster<2, kMaxThreads>;
+    return (const void*)k_step_cluster<4, kMaxThreads>;
+}
+
+cudaLaunchConfig_t cluster_config(int cl, int threads, size_t smem, cudaLaunchAttribute* attr, cudaStream_t s) {
     cudaLaunchConfig_t cfg{};
     cfg.gridDim = dim3(cl);
-    cfg.blockDim = dim3(kCT);
+    cfg.blockDim = dim3(threads);
     cfg.dynamicSmemBytes = smem;
     cfg.stream = s;
-    cudaLaunchAttribute attr[1];
     attr[0].id = cudaLaunchAttributeClusterDimension;
     attr[0].val.clusterDim.x = cl;
     attr[0].val.clusterDim.y = 1;
     attr[0].val.clusterDim.z = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    return cudaLaunchKernelEx(&cfg, k_step_cluster<NPT>, a, per_cta);
+    return cfg;
+}
+
+cudaError_t prepare(const void* fn, size_t smem) {
+    cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+    if (e != cudaSuccess) return e;
+    // always opted in: the kernel's static shared memory counts toward the
+    // 48 KiB that a launch may use without the attribute
+    return cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
 }
 
 }  // namespace
 
 // Cluster size and neurons per CTA for a network of n_total (padded) neurons,
-// or 0 when it does not fit one cluster (16 CTAs x 1024 threads x 4 neurons).
-int cluster_plan(int n_total, int n_pops, int* per_cta) {
-    if (n_pops > kMaxClusterTiles) return 0;
-    const int warps = (n_total + 31) / 32;
+// or 0 when it does not fit one cluster (16 CTAs x 4096 neurons, at most 64
+// projections).
+// Slices are whole 64-neuron warp groups (a warp of neuron pairs).
+int cluster_plan(int n_total, int n_pops, int n_projs, int* per_cta) {
+    if (n_pops > kMaxClusterTiles || n_projs > kMaxClusterProjs) return 0;
+    const int groups = (n_total + 63) / 64;
     for (int cl : {16, 8}) {
-        const int pc = (warps + cl - 1) / cl * 32;          // whole warps per CTA
+        const int pc = (groups + cl - 1) / cl * 64;
         if (pc <= 4 * kCT) {
             *per_cta = pc;
             return cl;
@@ -386,26 +514,17 @@ int cluster_plan(int n_total, int n_pops, int* per_cta) {
     return 0;
 }
 
-cudaError_t cluster_supported(int cl, int per_cta, int num_tiles, bool* ok) {
+cudaError_t cluster_supported(int cl, int per_cta, int num_tiles, int seg_rows, bool* ok) {
     *ok = false;
-    const size_t smem = cluster_smem(per_cta, num_tiles);
-    cudaError_t e = cudaFuncSetAttribute(k_step_cluster<4>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+    const size_t smem = cluster_smem(per_cta, num_tiles, seg_rows);
+    int threads = 0;
+    const void* fn = cluster_fn(per_cta, &threads);
+    cudaError_t e = prepare(fn, smem);
     if (e != cudaSuccess) return e;
-    e = cudaFuncSetAttribute(k_step_cluster<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    cudaLaunchConfig_t cfg{};
-    cfg.gridDim = dim3(cl);
-    cfg.blockDim = dim3(kCT);
-    cfg.dynamicSmemBytes = smem;
     cudaLaunchAttribute attr[1];
-    attr[0].id = cudaLaunchAttributeClusterDimension;
-    attr[0].val.clusterDim.x = cl;
-    attr[0].val.clusterDim.y = 1;
-    attr[0].val.clusterDim.z = 1;
-    cfg.attrs = attr;
-    cfg.numAttrs = 1;
+    cudaLaunchConfig_t cfg = cluster_config(cl, threads, smem, attr, nullptr);
     int n = 0;
-    e = cudaOccupancyMaxActiveClusters(&n, k_step_cluster<4>, &cfg);
+    e = cudaOccupancyMaxActiveClusters(&n, fn, &cfg);
     if (e != cudaSuccess) return e;
     *ok = n >= 1;
     return cudaSuccess;
@@ -420,12 +539,17 @@ cudaError_t launch_cluster_splits(const int64_t* row_ptr, const int32_t* col, in
     return cudaGetLastError();
 }
 
-cudaError_t launch_cluster(const PersistArgs& a, int cl, int per_cta, cudaStream_t s) {
+cudaError_t launch_cluster(const PersistArgs& a, int cl, int per_cta, int n_projs, int seg_rows, cudaStream_t s) {
     if (a.n.num_tiles == 0 || a.n_steps <= 0) return cudaSuccess;
-    const int npt = (per_cta + kCT - 1) / kCT;
-    if (npt <= 1) return launch_npt<1>(a, cl, per_cta, s);
-    if (npt <= 2) return launch_npt<2>(a, cl, per_cta, s);
-    return launch_npt<4>(a, cl, per_cta, s);
+    const size_t smem = cluster_smem(per_cta, a.n.num_tiles, seg_rows);
+    int threads = 0;
+    const void* fn = cluster_fn(per_cta, &threads);
+    cudaError_t e = prepare(fn, smem);
+    if (e != cudaSuccess) return e;
+    cudaLaunchAttribute attr[1];
+    cudaLaunchConfig_t cfg = cluster_config(cl, threads, smem, attr, s);
+    void* args[] = {const_cast<PersistArgs*>(&a), &per_cta, &n_projs, &seg_rows};
+    return cudaLaunchKernelExC(&cfg, fn, args);
 }
 
 }  // namespace snn

@@ -122,25 +122,22 @@ struct GradedArgs {
     float* r;                          // release of every neuron (next step's input)
     float* G;                          // G vector of the current step
     float* y;                          // output filter state [n_out]
-    float* y_out;                      // optional [T][n_out] record of y
-    const float* target;               // [T][n_out] or nullptr (no loss)
-    double* loss;
+    float* y_out;                      // [T][n_out] record of y (recorded forward) or nullptr
+    const float* dL_dy;                // [T][n_out] caller's dL/dy (reverse sweep)
     int32_t out_pop, n_out;
     int32_t t_rec;                     // step index within the recorded forward
     uint32_t t_rng;                    // step counter of the drive random numbers
     int32_t n_sub;
-    float hs, a_filter, loss_scale;
+    float hs, a_filter;
     uint32_t seed_lo, seed_hi;
     float* rec_state;                  // [5][n_total] step-start V, m, h, n, I_ext (after drive) or nullptr
     float* rec_r;                      // [n_total] releases used by the step
-    float* rec_y;                      // [n_out] y after the step
 };
 
 struct AdjArgs {
     const float* st;                   // [5][n_total] step-start state of the step being reversed
     const float* r_step;               // [n_total] releases of that step
     const float* r_seg;                // [K][n_total] releases of the segment
-    const float* y_after;              // [n_out] y after that step
     float *lV, *lV_loc, *lm, *lh, *ln, *ly;
     float* nu_step;                    // [G] dL/dG of the step
     float* nu_km;                      // [G][kp] dL/dG of the segment, time-contiguous
@@ -271,6 +268,7 @@ struct snn_net {
     int32_t persist_grid = 0;                 // co-resident CTAs of the persistent kernel
     int32_t barrier_extra = 0;                // test hook of SNN_OPT_TEST_BARRIER_EXTRA
     int32_t cluster_size = 0, cluster_per_cta = 0;   // cluster engine plan (0: does not fit)
+    int32_t cluster_seg_rows = 0;             // compressed rows whose CTA segments the cluster engine keeps in shared memory
     int32_t tiled = 2;                        // post-tiled rows: 0 off, 1 all compressed projections, 2 choose
     // graded (differentiable) networks
     bool graded = false;
@@ -280,18 +278,16 @@ struct snn_net {
     int32_t* in_list = nullptr;
     int64_t total_posts = 0;
     float *r = nullptr, *G = nullptr, *y = nullptr;
-    double* d_loss = nullptr;
     double* d_grad_scale = nullptr;
     int64_t g_t = 0;                          // graded step counter
     // recorded forward
     int64_t rec_T = 0;
     int32_t rec_K = 0, rec_out_pop = -1, rec_n_out = 0;
-    double rec_tau = 0.0, rec_loss = 0.0;
+    double rec_tau = 0.0;
     float* rec_ckpt = nullptr;                // [n_ckpt][6][n_total]
-    float* rec_target = nullptr;              // [T][n_out]
-    size_t rec_ckpt_cap = 0, rec_target_cap = 0;
+    size_t rec_ckpt_cap = 0;
     // segment buffers of the adjoint
-    float *seg_state = nullptr, *seg_r = nullptr, *seg_G = nullptr, *seg_y = nullptr;
+    float *seg_state = nullptr, *seg_r = nullptr, *seg_G = nullptr;
     float *nu_step = nullptr, *nu_km = nullptr;
     float *adj = nullptr;                     // lV, lV_loc, lm, lh, ln (5 * n_total) + ly (n_total)
     int32_t seg_cap_K = 0;
@@ -373,11 +369,14 @@ cudaError_t launch_propagate_tiled(const DevProj* q, int32_t P, const unsigned l
                                    int sm_count, uint32_t* error, uint32_t spin_limit, cudaStream_t s);
 constexpr int32_t kPostTile = 2048;          // posts per tile of the post-tiled propagation (8 KiB)
 cudaError_t persistent_capacity(int sm_count, int* blocks);
-int cluster_plan(int n_total, int n_pops, int* per_cta);
-cudaError_t cluster_supported(int cl, int per_cta, int num_tiles, bool* ok);
+// Compressed rows whose segment in a CTA's slice the cluster engine keeps in
+// shared memory (16 bytes each).
+constexpr int kClusterSegCacheRows = 2048;
+int cluster_plan(int n_total, int n_pops, int n_projs, int* per_cta);
+cudaError_t cluster_supported(int cl, int per_cta, int num_tiles, int seg_rows, bool* ok);
 cudaError_t launch_cluster_splits(const int64_t* row_ptr, const int32_t* col, int32_t n_pre, int32_t post_soa,
                                   int32_t n_post, int32_t n_ranks, int32_t per_cta, int64_t* split, cudaStream_t s);
-cudaError_t launch_cluster(const PersistArgs& a, int cl, int per_cta, cudaStream_t s);
+cudaError_t launch_cluster(const PersistArgs& a, int cl, int per_cta, int n_projs, int seg_rows, cudaStream_t s);
 cudaError_t launch_graded_spmv(const GradedArgs& a, cudaStream_t s);
 cudaError_t launch_graded_neuron(const GradedArgs& a, cudaStream_t s);
 cudaError_t launch_graded_release_init(const GradedArgs& a, cudaStream_t s);
