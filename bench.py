@@ -302,29 +302,43 @@ def _batched(snn, torch, dev, n_inst, steps):
             "instances_with_nan": int((nan_b > 0).sum()), "nan_counts_equal": bool(np.array_equal(nan_b, nan_s))}
 
 
+def _timed(torch, fn):
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    r = fn()
+    e1.record()
+    e1.synchronize()
+    return e0.elapsed_time(e1), r
+
+
+def _plain_forward_runs(net, steps, n=6):
+    """The n plain forward runs a central difference over the 3 scales needs:
+    snn_step from the creation state, recording nothing (no checkpoints, no
+    filter: a lower bound on what each difference quotient costs)."""
+    for _ in range(n):
+        net.reset()
+        net.step(steps)
+
+
 def _differentiable(snn, torch, dev, steps=2000, K=100):
     """Differentiable form (graded synapses, 20,000 middle neurons, p = 0.05):
-    recorded forward + adjoint backward against the 6 plain forward runs a
-    central finite difference over the 3 projection scales needs."""
+    recorded forward (y) + squared-error loss on top (torch) + adjoint
+    backward (dL/dy seed) against the 6 plain forward runs a central finite
+    difference over the 3 projection scales needs."""
+    from paper_1412_0595_gb300.network import squared_error
     spec = I.config_graded(steps=steps)
     net = snn.GradedNetwork.from_spec(spec, device=dev)
     n_out = spec["pops"][-1]["n"]
     target = torch.from_numpy(I.target_trace(spec, steps, n_out)).to(dev)
     nnz = sum(net.nnz(q) for q in range(net.n_projs))
-    net.forward_record(target, checkpoint_every=K)
-    net.backward()
+    y = net.forward_record(steps, checkpoint_every=K)
+    net.backward(squared_error(y, target)[1])
     torch.cuda.synchronize()
-    ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
-    ev[0].record()
-    loss = net.forward_record(target, checkpoint_every=K)
-    ev[1].record()
-    gs, gw = net.backward()
-    ev[2].record()
-    for _ in range(6):
-        net.forward_record(target, checkpoint_every=K)
-    ev[3].record()
-    ev[3].synchronize()
-    t_f, t_b, t_fd = ev[0].elapsed_time(ev[1]), ev[1].elapsed_time(ev[2]), ev[2].elapsed_time(ev[3])
+    t_f, y = _timed(torch, lambda: net.forward_record(steps, checkpoint_every=K))
+    loss, dl = squared_error(y, target)
+    t_b, (gs, gw) = _timed(torch, lambda: net.backward(dl))
+    t_fd, _ = _timed(torch, lambda: [net.forward_record(steps, checkpoint_every=K) for _ in range(6)])
+    t_plain, _ = _timed(torch, lambda: _plain_forward_runs(net, steps))
     peaks, src = _peaks()
     hbm = float(peaks.get("hbm_gbs", 6800.0))
     # the transposed pre indices are 16-bit when every pre population has at most 65,536 neurons
@@ -333,7 +347,8 @@ def _differentiable(snn, torch, dev, steps=2000, K=100):
     out = {"workload": f"graded HH: In 100 -> Mid 20,000 (+ recurrent) -> Out 100, p = 0.05, {steps} steps of 0.05 ms",
            "synapses": nnz, "checkpoint_every": K, "loss": loss,
            "forward_ms": t_f, "backward_ms": t_b, "adjoint_total_ms": t_f + t_b,
-           "six_forward_runs_ms": t_fd, "adjoint_vs_fd_speedup": t_fd / (t_f + t_b),
+           "six_plain_forward_runs_ms": t_plain, "adjoint_vs_plain_fd": t_plain / (t_f + t_b),
+           "six_recorded_forward_runs_ms": t_fd, "adjoint_vs_fd_speedup": t_fd / (t_f + t_b),
            "gradients": 3 + nnz, "grad_scale": gs.cpu().tolist(),
            "forward_bytes_per_synapse": per_syn,
            "forward_synapse_stream_gbs": fwd_gbs, "forward_frac_hbm": fwd_gbs / hbm,
@@ -348,30 +363,23 @@ def _differentiable_dense(snn, torch, dev, steps=2000, K=100):
     Mid -> Mid and Mid -> Out dense.  Recorded forward, adjoint with the
     weight gradient on the tensor cores and on the CUDA cores, and the 6
     forward runs of a central difference over the 3 scales."""
+    from paper_1412_0595_gb300.network import squared_error
     spec = I.config_graded_dense(steps=steps)
     net = snn.GradedNetwork.from_spec(spec, device=dev)
     n_out = spec["pops"][-1]["n"]
     target = torch.from_numpy(I.target_trace(spec, steps, n_out)).to(dev)
-    net.forward_record(target, checkpoint_every=K)
-    net.backward()
+    y = net.forward_record(steps, checkpoint_every=K)
+    net.backward(squared_error(y, target)[1])
     torch.cuda.synchronize()
-
-    def timed(fn):
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record()
-        r = fn()
-        e1.record()
-        e1.synchronize()
-        return e0.elapsed_time(e1), r
-
-    t_f, loss = timed(lambda: net.forward_record(target, checkpoint_every=K))
+    t_f, y = _timed(torch, lambda: net.forward_record(steps, checkpoint_every=K))
+    loss, dl = squared_error(y, target)
     net.set_option("dense_grad", 1)
-    t_bt, (gs, gw) = timed(net.backward)
+    t_bt, (gs, gw) = _timed(torch, lambda: net.backward(dl))
     net.set_option("dense_grad", 0)
-    net.forward_record(target, checkpoint_every=K)
-    t_bc, (gs_c, gw_c) = timed(net.backward)
+    t_bc, (gs_c, gw_c) = _timed(torch, lambda: net.backward(dl))
     net.set_option("dense_grad", 1)
-    t_fd, _ = timed(lambda: [net.forward_record(target, checkpoint_every=K) for _ in range(6)])
+    t_fd, _ = _timed(torch, lambda: [net.forward_record(steps, checkpoint_every=K) for _ in range(6)])
+    t_plain, _ = _timed(torch, lambda: _plain_forward_runs(net, steps))
     n_mid = spec["pops"][1]["n"]
     dense_w = n_mid * n_mid + n_mid * n_out
     peaks, _ = _peaks()
@@ -382,7 +390,8 @@ def _differentiable_dense(snn, torch, dev, steps=2000, K=100):
                        f"{steps} steps of 0.05 ms",
            "dense_weights": dense_w, "checkpoint_every": K, "loss": loss,
            "forward_ms": t_f, "backward_tensor_ms": t_bt, "backward_cuda_core_ms": t_bc,
-           "six_forward_runs_ms": t_fd, "adjoint_vs_fd_speedup": t_fd / (t_f + t_bt),
+           "six_plain_forward_runs_ms": t_plain, "adjoint_vs_plain_fd": t_plain / (t_f + t_bt),
+           "six_recorded_forward_runs_ms": t_fd, "adjoint_vs_fd_speedup": t_fd / (t_f + t_bt),
            "forward_dense_weight_stream_gbs": fwd_gbs, "forward_frac_hbm": fwd_gbs / hbm,
            "weight_grad_rel_diff_tensor_vs_cuda_core": rel,
            "finite": bool(torch.isfinite(gs).all() and all(torch.isfinite(g).all() for g in gw))}
@@ -985,22 +994,22 @@ def run_profile(a):
         h.close()
         return
     elif a.profile == "graded_dense":
+        from paper_1412_0595_gb300.network import squared_error
         spec = I.config_graded_dense(steps=200)
         net = snn.GradedNetwork.from_spec(spec, device=dev)
         target = torch.from_numpy(I.target_trace(spec, 200, spec["pops"][-1]["n"])).to(dev)
-        net.forward_record(target, checkpoint_every=100)
-        net.backward()
+        net.backward(squared_error(net.forward_record(200, checkpoint_every=100), target)[1])
     elif a.profile == "neuron":
         net = snn.Network.from_spec(I.net([I.hh_pop(8_000_000)], [], dt=0.1, steps=1), device=dev)
         net.set_option("engine", 0)
         for _ in range(4):
             net.launch_phase(0)
     else:
+        from paper_1412_0595_gb300.network import squared_error
         spec = I.config_graded(steps=200)
         net = snn.GradedNetwork.from_spec(spec, device=dev)
         target = torch.from_numpy(I.target_trace(spec, 200, spec["pops"][-1]["n"])).to(dev)
-        net.forward_record(target, checkpoint_every=100)
-        net.backward()
+        net.backward(squared_error(net.forward_record(200, checkpoint_every=100), target)[1])
     torch.cuda.synchronize()
     net.sync()
     net.close()

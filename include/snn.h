@@ -405,33 +405,35 @@ snn_status snn_set_weights(snn_net* net, int32_t proj, const float* w, int32_t o
  * each step, G_q[k] = sum_i w_ik r_i and I_syn_k = sum_q s_q (E_q - V_k) G_q[k]
  * (E_q: the post population's reversal potential of the projection's
  * channel), then the Euler substeps; spike counts are still kept.  The paper
- * fixes no synapse model (Sec. 2); this graded one makes the loss below a
+ * fixes no synapse model (Sec. 2); this graded one makes the output y below a
  * smooth function of the scales s_q (Sec. 5.1) and the weights.  Graded
  * projections use compressed rows or dense storage (Eq. 2, every pair a
  * weight); populations must be HH. */
 
 /* Runs n_steps steps from the creation state (it resets the network first)
- * and evaluates L = mean over steps t and output neurons k of
- * (y_k(t+1) - target[t][k])^2, where y follows the output population's V
- * with y += (dt / tau_f)(V - y), starting at V(0).  target (device,
- * n_steps x n_out floats) is copied; y_out (device, n_steps x n_out) may be
- * NULL; *loss (host) receives L.  Stores the state every checkpoint_every
- * steps (1..512) for snn_backward.  Synchronises `stream`.  SNN_ERR_STATE for
- * a spiking network. */
+ * and writes the output filter: y_out[t][k] = y_k(t + 1) (device, n_steps x
+ * n_out floats, step-major, owned by the caller), where y follows the output
+ * population's V with y += (dt / tau_f)(V - y), starting at V(0).  Any loss
+ * L(y) is the caller's; snn_backward takes its gradient dL/dy.  Stores the
+ * state every checkpoint_every steps (1..512) for snn_backward.
+ * Synchronises `stream`.  SNN_ERR_STATE for a spiking network;
+ * SNN_ERR_INVALID_ARG for y_out == NULL or bad sizes. */
 snn_status snn_forward_record(snn_net* net, int64_t n_steps, int32_t checkpoint_every, int32_t out_pop,
-                              double tau_f, const float* target, float* y_out, double* loss, void* stream);
+                              double tau_f, float* y_out, void* stream);
 
-/* Gradient of the last recorded L with respect to every projection's scale
- * (grad_scale: device, n_projs floats) and weights (grad_w: host array of
- * n_projs device pointers, each nnz floats in compressed-row order, or
- * n_pre x n_post row-major for dense storage), by the discrete adjoint of the
- * recorded steps: each checkpoint segment is recomputed, then swept in
- * reverse (substeps, synaptic current, pre-synaptic gather), and the weight
+/* Gradient of a loss L(y) of the last recorded forward's y with respect to
+ * every projection's scale (grad_scale: device, n_projs floats) and weights
+ * (grad_w: host array of n_projs device pointers, each nnz floats in
+ * compressed-row order, or n_pre x n_post row-major for dense storage),
+ * given dL_dy (device, n_steps x n_out floats in y_out's layout, read during
+ * the call, owned by the caller), by the discrete adjoint of the recorded
+ * steps: each checkpoint segment is recomputed, then swept in reverse
+ * (filter, substeps, synaptic current, pre-synaptic gather), and the weight
  * gradients of the segment are summed over its steps in one pass (for dense
  * storage a rank-K update, see snn_dense_grad_run and SNN_OPT_DENSE_GRAD).
  * Overwrites the outputs.  SNN_ERR_STATE without a recorded forward.
  * Synchronises `stream`. */
-snn_status snn_backward(snn_net* net, float* grad_scale, float* const* grad_w, void* stream);
+snn_status snn_backward(snn_net* net, const float* dL_dy, float* grad_scale, float* const* grad_w, void* stream);
 
 /* ---- checkpoint / resume --------------------------------------------------
  * A snapshot holds the whole dynamic state: V, m, h, n, conductances, drive

@@ -98,8 +98,8 @@ def _load():
         "snn_csr_bernoulli_rows_noalloc": [u64, u32, i64, i64, dbl, vp, P(i64), vp],
         "snn_set_scale": [vp, i32, dbl],
         "snn_set_weights": [vp, i32, vp, i32, vp],
-        "snn_forward_record": [vp, i64, i32, i32, dbl, vp, vp, P(dbl), vp],
-        "snn_backward": [vp, vp, P(vp), vp],
+        "snn_forward_record": [vp, i64, i32, i32, dbl, vp, vp],
+        "snn_backward": [vp, vp, vp, P(vp), vp],
         "snn_state_size": [vp, P(sz)],
         "snn_save_state": [vp, vp, sz, i32, vp],
         "snn_load_state": [vp, vp, sz, i32, vp],

@@ -6,13 +6,14 @@
 //                    compressed rows: no atomics, a fixed summation order, so
 //                    a recomputed step is bit-identical to the first pass;
 //   k_graded_neuron  I_syn = sum_q s_q (E_q - V) G_q, drive events, Euler
-//                    substeps, drive decay, output filter y += a (V - y) and
-//                    squared error against the target, and the next release
+//                    substeps, drive decay, output filter y += a (V - y)
+//                    (recorded into y_out), and the next release
 //                    r = 1 / (1 + exp((v_thr - V) / slope)).
 // Adjoint (per checkpoint segment of K steps, in reverse):
 //   the segment is recomputed from its checkpoint with the same two kernels,
 //   storing step-start states, releases and G;
-//   k_graded_reverse back through the filter, the substeps (recomputed in
+//   k_graded_reverse back through the filter (seeded by the caller's dL/dy),
+//                    the substeps (recomputed in
 //                    registers, analytic rate derivatives) and the synaptic
 //                    current: state adjoints, dL/dG_q = mu s_q (E_q - V), and
 //                    dL/ds_q partial sums;
@@ -236,11 +237,6 @@ __global__ void __launch_bounds__(kNeuronThreads) k_graded_neuron(const GradedAr
         const float y = a.y[local] + a.a_filter * (V - a.y[local]);
         a.y[local] = y;
         if (a.y_out) a.y_out[(size_t)a.t_rec * a.n_out + local] = y;
-        if (a.rec_y) a.rec_y[local] = y;
-        if (a.target) {
-            const float d = y - a.target[(size_t)a.t_rec * a.n_out + local];
-            atomicAdd(a.loss, (double)d * (double)d);
-        }
     }
 }
 
@@ -298,8 +294,7 @@ __global__ void __launch_bounds__(kNeuronThreads) k_graded_reverse(const GradedA
         float ly_prev = 0.0f;
         if (pop == a.out_pop) {
             float ly = b.ly[local];
-            const float y = b.y_after[local];
-            ly += a.loss_scale * (y - a.target[(size_t)a.t_rec * a.n_out + local]);
+            ly += a.dL_dy[(size_t)a.t_rec * a.n_out + local];
             lV += a.a_filter * ly;
             ly_prev = (1.0f - a.a_filter) * ly;
         }

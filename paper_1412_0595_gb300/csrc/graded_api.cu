@@ -38,7 +38,6 @@ GradedArgs graded_args(snn_net* net) {
     a.r = net->r;
     a.G = net->G;
     a.y = net->y;
-    a.loss = net->d_loss;
     a.out_pop = net->rec_out_pop;
     a.n_out = net->rec_n_out;
     a.n_sub = net->n_sub;
@@ -223,7 +222,6 @@ snn_status graded_setup(snn_net* net, cudaStream_t s) {
     SNN_TRY(net_alloc(net, &net->r, NT, "releases"));
     SNN_TRY(net_alloc(net, &net->G, std::max<size_t>(1, (size_t)g_off), "graded conductances"));
     SNN_TRY(net_alloc(net, &net->y, NT, "output filter"));
-    SNN_TRY(net_alloc(net, &net->d_loss, 1, "loss"));
     SNN_TRY(net_alloc(net, &net->d_grad_scale, std::max<size_t>(1, (size_t)nq), "scale gradients"));
     SNN_CK(cudaMemcpyAsync(net->in_begin, ib.data(), ib.size() * sizeof(int32_t), cudaMemcpyHostToDevice, s), "upload");
     SNN_CK(cudaMemcpyAsync(net->in_list, il.data(), il.size() * sizeof(int32_t), cudaMemcpyHostToDevice, s), "upload");
@@ -251,7 +249,6 @@ snn_status graded_reset(snn_net* net, cudaStream_t s) {
 
 snn_status graded_step(snn_net* net, int64_t n_steps, cudaStream_t s) {
     GradedArgs a = graded_args(net);
-    a.target = nullptr;
     a.out_pop = -1;
     for (int64_t k = 0; k < n_steps; ++k) {
         SNN_CK(graded_one_step(net, a, net->G, net->g_t, s), "graded step");
@@ -271,7 +268,6 @@ snn_status ensure_segment_buffers(snn_net* net, int32_t K, int32_t n_out) {
     SNN_TRY(net_alloc(net, &net->seg_state, (size_t)K * 5 * NT, "segment states"));
     SNN_TRY(net_alloc(net, &net->seg_r, (size_t)K * NT, "segment releases"));
     SNN_TRY(net_alloc(net, &net->seg_G, (size_t)K * G, "segment conductances"));
-    SNN_TRY(net_alloc(net, &net->seg_y, (size_t)K * NT, "segment filter"));
     SNN_TRY(net_alloc(net, &net->nu_step, G, "step dL/dG"));
     SNN_TRY(net_alloc(net, &net->nu_km, G * kp, "segment dL/dG"));
     SNN_TRY(net_alloc(net, &net->adj, 6 * NT, "adjoints"));
@@ -327,24 +323,20 @@ snn_status snn_set_weights(snn_net* net, int32_t proj, const float* w, int32_t o
 }
 
 snn_status snn_forward_record(snn_net* net, int64_t n_steps, int32_t checkpoint_every, int32_t out_pop,
-                              double tau_f, const float* target, float* y_out, double* loss, void* stream) {
+                              double tau_f, float* y_out, void* stream) {
     if (!net) return fail(SNN_ERR_INVALID_ARG, "net is NULL");
     if (!net->graded) return fail(SNN_ERR_STATE, "recorded forward needs a graded network");
     if (n_steps < 1 || n_steps >= (int64_t(1) << 31) || checkpoint_every < 1 || checkpoint_every > kMaxSeg ||
-        out_pop < 0 || out_pop >= (int32_t)net->pops.size() || !(tau_f > 0) || !target)
-        return fail(SNN_ERR_INVALID_ARG, "bad steps, checkpoint interval (1..512), output population, tau or target");
+        out_pop < 0 || out_pop >= (int32_t)net->pops.size() || !(tau_f > 0) || !y_out)
+        return fail(SNN_ERR_INVALID_ARG, "bad steps, checkpoint interval (1..512), output population, tau or y_out");
     cudaStream_t s = (cudaStream_t)stream;
     const int32_t n_out = net->pops[out_pop].d.n;
     const size_t NT = std::max<size_t>(1, (size_t)net->n_total);
     const int64_t n_ckpt = (n_steps + checkpoint_every - 1) / checkpoint_every;
-    // buffers for checkpoints and the target (grown as needed)
+    // checkpoint buffer (grown as needed)
     if (net->rec_ckpt_cap < (size_t)n_ckpt * 6 * NT) {
         SNN_TRY(net_alloc(net, &net->rec_ckpt, (size_t)n_ckpt * 6 * NT, "checkpoints"));
         net->rec_ckpt_cap = (size_t)n_ckpt * 6 * NT;
-    }
-    if (net->rec_target_cap < (size_t)n_steps * n_out) {
-        SNN_TRY(net_alloc(net, &net->rec_target, std::max<size_t>(1, (size_t)n_steps * n_out), "target"));
-        net->rec_target_cap = (size_t)n_steps * n_out;
     }
     SNN_TRY(ensure_segment_buffers(net, checkpoint_every, n_out));
     net->rec_T = n_steps;
@@ -352,13 +344,9 @@ snn_status snn_forward_record(snn_net* net, int64_t n_steps, int32_t checkpoint_
     net->rec_out_pop = out_pop;
     net->rec_n_out = n_out;
     net->rec_tau = tau_f;
-    SNN_CK(cudaMemcpyAsync(net->rec_target, target, sizeof(float) * (size_t)n_steps * n_out, cudaMemcpyDeviceToDevice, s),
-           "copy target");
     // start from the creation state
     SNN_TRY(snn_reset(net, stream));
-    SNN_CK(cudaMemsetAsync(net->d_loss, 0, sizeof(double), s), "clear loss");
     GradedArgs a = graded_args(net);
-    a.target = net->rec_target;
     a.y_out = y_out;
     SNN_TRY(graded_reset(net, s));
     for (int64_t t = 0; t < n_steps; ++t) {
@@ -372,18 +360,14 @@ snn_status snn_forward_record(snn_net* net, int64_t n_steps, int32_t checkpoint_
         SNN_CK(graded_one_step(net, a, net->G, t, s), "recorded step");
     }
     net->g_t = n_steps;
-    double acc = 0.0;
-    SNN_CK(cudaMemcpyAsync(&acc, net->d_loss, sizeof(double), cudaMemcpyDeviceToHost, s), "read loss");
     SNN_CK(cudaStreamSynchronize(s), "synchronize");
-    net->rec_loss = acc / ((double)n_steps * n_out);
-    if (loss) *loss = net->rec_loss;
     return snn_sync(net, stream);
 }
 
-snn_status snn_backward(snn_net* net, float* grad_scale, float* const* grad_w, void* stream) {
+snn_status snn_backward(snn_net* net, const float* dL_dy, float* grad_scale, float* const* grad_w, void* stream) {
     if (!net) return fail(SNN_ERR_INVALID_ARG, "net is NULL");
     if (!net->graded || net->rec_T == 0) return fail(SNN_ERR_STATE, "no recorded forward");
-    if (!grad_scale || !grad_w) return fail(SNN_ERR_INVALID_ARG, "gradient buffers are NULL");
+    if (!dL_dy || !grad_scale || !grad_w) return fail(SNN_ERR_INVALID_ARG, "dL/dy or gradient buffers are NULL");
     const int nq = (int)net->projs.size();
     for (int q = 0; q < nq; ++q)
         if (!grad_w[q] && net->projs[q].nnz) return fail(SNN_ERR_INVALID_ARG, "weight gradient buffer is NULL");
@@ -419,7 +403,6 @@ snn_status snn_backward(snn_net* net, float* grad_scale, float* const* grad_w, v
         SNN_CK(cudaMemcpyAsync(net->iext, c + 4 * NT, NT * sizeof(float), cudaMemcpyDeviceToDevice, s), "restore");
         SNN_CK(cudaMemcpyAsync(net->y, c + 5 * NT, NT * sizeof(float), cudaMemcpyDeviceToDevice, s), "restore");
         GradedArgs a = graded_args(net);
-        a.target = nullptr;
         // releases from the restored V, without resetting the filter
         {
             GradedArgs ri = a;
@@ -430,7 +413,6 @@ snn_status snn_backward(snn_net* net, float* grad_scale, float* const* grad_w, v
             GradedArgs f = a;
             f.rec_state = net->seg_state + (size_t)tl * 5 * NT;
             f.rec_r = net->seg_r + (size_t)tl * NT;
-            f.rec_y = net->seg_y + (size_t)tl * NT;
             f.t_rec = (int32_t)(t0 + tl);
             SNN_CK(graded_one_step(net, f, net->seg_G + (size_t)tl * G, t0 + tl, s), "segment recompute");
         }
@@ -438,12 +420,10 @@ snn_status snn_backward(snn_net* net, float* grad_scale, float* const* grad_w, v
         for (int32_t tl = L - 1; tl >= 0; --tl) {
             GradedArgs r = a;
             r.G = net->seg_G + (size_t)tl * G;
-            r.target = net->rec_target;
+            r.dL_dy = dL_dy;
             r.t_rec = (int32_t)(t0 + tl);
-            r.loss_scale = (float)(2.0 / ((double)T * n_out));
             b.st = net->seg_state + (size_t)tl * 5 * NT;
             b.r_step = net->seg_r + (size_t)tl * NT;
-            b.y_after = net->seg_y + (size_t)tl * NT;
             b.tl = tl;
             SNN_CK(launch_graded_reverse(r, b, s), "reverse step");
         }

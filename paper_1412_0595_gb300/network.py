@@ -418,50 +418,58 @@ class GradedNetwork(Network):
         assert t.numel() == self.nnz(q)
         check(L.lib.snn_set_weights(self.h, int(q), t.data_ptr(), 1, _stream(stream)))
 
-    def forward_record(self, target, out_pop=None, tau_f=5.0, checkpoint_every=100, return_y=False, stream=None):
-        """Loss L of the recorded run; `target` is a (T, n_out) tensor."""
+    def forward_record(self, n_steps, out_pop=None, tau_f=5.0, checkpoint_every=100, stream=None):
+        """Recorded run of n_steps from the creation state; returns the output
+        filter y as a (n_steps, n_out) device tensor (y[t] = y(t + 1))."""
         out_pop = len(self.sizes) - 1 if out_pop is None else int(out_pop)
-        tgt = _dev(target, torch.float32, self.device)
-        T, n_out = tgt.shape
-        assert n_out == self.sizes[out_pop]
-        y = torch.empty((T, n_out), dtype=torch.float32, device=self.device) if return_y else None
-        loss = C.c_double()
-        check(L.lib.snn_forward_record(self.h, int(T), int(checkpoint_every), out_pop, float(tau_f), tgt.data_ptr(),
-                                       y.data_ptr() if y is not None else None, C.byref(loss), _stream(stream)))
-        return (loss.value, y) if return_y else loss.value
+        y = torch.empty((int(n_steps), self.sizes[out_pop]), dtype=torch.float32, device=self.device)
+        check(L.lib.snn_forward_record(self.h, int(n_steps), int(checkpoint_every), out_pop, float(tau_f),
+                                       y.data_ptr(), _stream(stream)))
+        return y
 
-    def backward(self, stream=None):
-        """(dL/ds per projection, [dL/dw per projection, compressed-row order])."""
+    def backward(self, dL_dy, stream=None):
+        """(dL/ds per projection, [dL/dw per projection, compressed-row order])
+        of a loss of the last recorded y, given dL/dy in y's layout."""
+        g = _dev(dL_dy, torch.float32, self.device)
         gs = torch.empty(self.n_projs, dtype=torch.float32, device=self.device)
         gw = [torch.empty(max(self.nnz(q), 1), dtype=torch.float32, device=self.device) for q in range(self.n_projs)]
         ptrs = (C.c_void_p * max(1, self.n_projs))(*[t.data_ptr() for t in gw])
-        check(L.lib.snn_backward(self.h, gs.data_ptr(), ptrs, _stream(stream)))
-        return gs, [g[: self.nnz(q)] for q, g in enumerate(gw)]
+        check(L.lib.snn_backward(self.h, g.data_ptr(), gs.data_ptr(), ptrs, _stream(stream)))
+        return gs, [x[: self.nnz(q)] for q, x in enumerate(gw)]
+
+
+def squared_error(y, target):
+    """Mean squared error of y against target and its gradient dL/dy (a loss
+    on top of the network's output; computed in torch, outside the library)."""
+    t = target.to(device=y.device, dtype=y.dtype)
+    d = y - t
+    return (d.double() ** 2).mean().item(), (2.0 / d.numel()) * d
 
 
 class SNNFunction(torch.autograd.Function):
-    """L(scales, weights) of a graded network as an autograd node.
+    """y(scales, weights) of a graded network as an autograd node.
 
-    forward(net, target, out_pop, tau_f, checkpoint_every, scales, *weights):
+    forward(net, n_steps, out_pop, tau_f, checkpoint_every, scales, *weights):
     sets every projection's scale s_q and weights, runs the recorded forward
-    and returns L as a 0-d tensor; backward returns dL/ds and dL/dw from the
-    network's discrete adjoint."""
+    and returns the output filter y (n_steps x n_out); backward takes dL/dy
+    from whatever loss or torch graph sits on top and returns dL/ds and dL/dw
+    from the network's discrete adjoint.  The network holds one recorded run:
+    call backward before the next forward on the same network."""
 
     @staticmethod
-    def forward(ctx, net, target, out_pop, tau_f, checkpoint_every, scales, *weights):
+    def forward(ctx, net, n_steps, out_pop, tau_f, checkpoint_every, scales, *weights):
         for q in range(net.n_projs):
             net.set_scale(q, float(scales[q]))
             net.set_weights(q, weights[q].detach())
-        loss = net.forward_record(target, out_pop, tau_f, checkpoint_every)
+        y = net.forward_record(n_steps, out_pop, tau_f, checkpoint_every)
         ctx.net = net
-        return torch.tensor(loss, dtype=torch.float64, device=scales.device)
+        ctx.scale_dtype = scales.dtype
+        return y
 
     @staticmethod
-    def backward(ctx, grad_out):
-        gs, gw = ctx.net.backward()
-        g = grad_out.to(torch.float32)
-        return (None, None, None, None, None, (g * gs).to(torch.float64) if gs.dtype != torch.float64 else g * gs,
-                *[g * x for x in gw])
+    def backward(ctx, grad_y):
+        gs, gw = ctx.net.backward(grad_y.contiguous())
+        return (None, None, None, None, None, gs.to(ctx.scale_dtype), *gw)
 
 
 class DenseBatch:

@@ -1,5 +1,6 @@
 """Differentiable form on the GPU against the FP64 oracle: recorded forward
-(loss, filtered output) and the discrete adjoint (dL/ds, dL/dw)."""
+(the output filter y) and the discrete adjoint (dL/ds, dL/dw) seeded by a
+caller's dL/dy, for the squared-error loss and for another loss of y."""
 import numpy as np
 import pytest
 import torch
@@ -27,11 +28,24 @@ def _pair(gpu, spec, T):
     return net, ref, target
 
 
+def _mse(gpu, net, target, K, backward=True):
+    """Recorded forward, squared-error loss on top of y (torch), and the
+    adjoint seeded by its dL/dy: (loss, y, dL/ds, dL/dw)."""
+    from paper_1412_0595_gb300.network import squared_error
+    T = target.shape[0]
+    y = net.forward_record(T, checkpoint_every=K)
+    loss, dl = squared_error(y, torch.from_numpy(target))
+    if not backward:
+        return loss, y, None, None
+    gs, gw = net.backward(dl)
+    return loss, y, gs, gw
+
+
 def test_graded_forward_matches_oracle_200_neuron_copy(gpu):
     T = 2000
     spec = I.config_graded_small(steps=T)
     net, ref, target = _pair(gpu, spec, T)
-    loss, y = net.forward_record(torch.from_numpy(target), checkpoint_every=100, return_y=True)
+    loss, y, _, _ = _mse(gpu, net, target, 100, backward=False)
     rloss, ry = ref.forward(target.astype(np.float64))
     assert loss == pytest.approx(rloss, rel=1e-3)
     assert np.abs(y.cpu().numpy() - ry).max() < 0.05
@@ -43,14 +57,35 @@ def test_graded_gradients_match_oracle_adjoint_before_divergence(gpu):
     T = 200
     spec = I.config_graded_small(steps=T)
     net, ref, target = _pair(gpu, spec, T)
-    net.forward_record(torch.from_numpy(target), checkpoint_every=64)
-    gs, gw = net.backward()
+    _, _, gs, gw = _mse(gpu, net, target, 64)
     ref.forward(target.astype(np.float64))
-    rgs, rgw = ref.backward()
+    rgs, rgw = ref.backward()                       # the oracle's own squared-error adjoint
     assert _rel_l2(gs.cpu().numpy(), rgs) < 1e-3
     for q in range(3):
         assert _rel_l2(gw[q].cpu().numpy(), rgw[q]) < 2e-3, q
         assert _cos(gw[q].cpu().numpy(), rgw[q]) > 0.99999, q
+
+
+def test_gradients_of_another_loss_match_the_oracle_adjoint_with_the_same_dl_dy(gpu):
+    # a loss of y other than the squared error, mean |y - target|^3: both
+    # adjoints are seeded with the same dL/dy (taken from the GPU's y)
+    T = 200
+    spec = I.config_graded_small(steps=T)
+    net, ref, target = _pair(gpu, spec, T)
+    y = net.forward_record(T, checkpoint_every=64)
+    d = y - torch.from_numpy(target).cuda()
+    dl = 3.0 * d.abs() * d / d.numel()
+    gs, gw = net.backward(dl)
+    ref.forward(target.astype(np.float64))
+    rgs, rgw = ref.backward(dL_dy=dl.double().cpu().numpy())
+    assert np.all(np.abs(rgs) > 0)
+    assert _rel_l2(gs.cpu().numpy(), rgs) < 1e-3
+    for q in range(3):
+        assert _rel_l2(gw[q].cpu().numpy(), rgw[q]) < 2e-3, q
+        assert _cos(gw[q].cpu().numpy(), rgw[q]) > 0.99999, q
+    # dL/dy is linear in the seed: twice the seed, twice the gradients
+    gs2, _ = net.backward(2.0 * dl)
+    assert torch.allclose(gs2, 2.0 * gs, rtol=1e-6, atol=0)
 
 
 def test_graded_gradients_match_oracle_adjoint_smooth_network(gpu):
@@ -67,8 +102,7 @@ def test_graded_gradients_match_oracle_adjoint_smooth_network(gpu):
     spec = I.net(pops, projs, dt=0.05, steps=1)
     T = 600
     net, ref, target = _pair(gpu, spec, T)
-    loss = net.forward_record(torch.from_numpy(target), checkpoint_every=100)
-    gs, gw = net.backward()
+    loss, _, gs, gw = _mse(gpu, net, target, 100)
     rloss, _ = ref.forward(target.astype(np.float64))
     rgs, rgw = ref.backward()
     assert loss == pytest.approx(rloss, rel=1e-5)
@@ -83,8 +117,7 @@ def test_graded_gradients_2000_steps_output_projection(gpu):
     T = 2000
     spec = I.config_graded_small(steps=T)
     net, ref, target = _pair(gpu, spec, T)
-    net.forward_record(torch.from_numpy(target), checkpoint_every=100)
-    gs, gw = net.backward()
+    _, _, gs, gw = _mse(gpu, net, target, 100)
     ref.forward(target.astype(np.float64))
     rgs, rgw = ref.backward()
     assert gs[2].item() == pytest.approx(rgs[2], rel=1e-2)
@@ -99,8 +132,7 @@ def test_checkpoint_interval_does_not_change_the_gradient(gpu):
     net, ref, target = _pair(gpu, spec, T)
     out = []
     for K in (100, 37, 512):
-        l = net.forward_record(torch.from_numpy(target), checkpoint_every=K)
-        gs, gw = net.backward()
+        l, _, gs, gw = _mse(gpu, net, target, K)
         out.append((l, gs.cpu().numpy(), [g.cpu().numpy() for g in gw]))
     for l, gs, gw in out[1:]:
         assert l == out[0][0]                                   # the forward is deterministic
@@ -110,21 +142,30 @@ def test_checkpoint_interval_does_not_change_the_gradient(gpu):
 
 
 def test_autograd_function_and_a_descent_step(gpu):
+    # y from the autograd node, any torch loss on top; autograd's dL/dy
+    # reaches the network's adjoint
+    from paper_1412_0595_gb300.network import squared_error
     T = 400
     spec = I.config_graded_small(steps=T)
     net, ref, target = _pair(gpu, spec, T)
     tgt = torch.from_numpy(target).cuda()
     scales = torch.tensor([ref.scale(q) for q in range(3)], dtype=torch.float64, device="cuda", requires_grad=True)
     ws = [torch.from_numpy(ref.rows[q][2].astype(np.float32)).cuda().requires_grad_(True) for q in range(3)]
-    loss = gpu.SNNFunction.apply(net, tgt, 2, 5.0, 100, scales, *ws)
+    y = gpu.SNNFunction.apply(net, T, 2, 5.0, 100, scales, *ws)
+    assert tuple(y.shape) == (T, ref.n_out)
+    loss = ((y - tgt) ** 2).mean() + 0.1 * (y - tgt).abs().mean()
     loss.backward()
-    gs, gw = net.backward()
+    d = (y - tgt).detach()
+    gs, gw = net.backward(2.0 * d / d.numel() + 0.1 * torch.sign(d) / d.numel())
     assert torch.allclose(scales.grad.float(), gs, rtol=1e-6, atol=0)
-    assert torch.equal(ws[0].grad, gw[0])
+    assert torch.allclose(ws[0].grad, gw[0], rtol=1e-6, atol=1e-12 * gw[0].abs().max().item())
     with torch.no_grad():                                      # a small step downhill on the scales
         new_scales = scales * (1.0 - 1e-5 * torch.sign(scales.grad))
-    loss2 = gpu.SNNFunction.apply(net, tgt, 2, 5.0, 100, new_scales, *[w.detach() for w in ws])
+    y2 = gpu.SNNFunction.apply(net, T, 2, 5.0, 100, new_scales, *[w.detach() for w in ws])
+    loss2 = ((y2 - tgt) ** 2).mean() + 0.1 * (y2 - tgt).abs().mean()
     assert loss2.item() < loss.item()
+    mse, _ = squared_error(y2, tgt)
+    assert mse == pytest.approx(((y2.double() - tgt.double()) ** 2).mean().item(), rel=1e-12)
 
 
 def test_full_size_differentiable_workload_first_100_steps(gpu):
@@ -132,10 +173,9 @@ def test_full_size_differentiable_workload_first_100_steps(gpu):
     T = 100
     spec = I.config_graded(steps=T)
     net, ref, target = _pair(gpu, spec, T)
-    loss = net.forward_record(torch.from_numpy(target), checkpoint_every=50)
+    loss, _, gs, gw = _mse(gpu, net, target, 50)
     rloss, _ = ref.forward(target.astype(np.float64))
     assert loss == pytest.approx(rloss, rel=1e-4)
-    gs, gw = net.backward()
     rgs, rgw = ref.backward()
     assert _rel_l2(gs.cpu().numpy(), rgs) < 1e-3
     for q in range(3):
@@ -147,5 +187,5 @@ def test_backward_without_forward_is_rejected(gpu):
     import paper_1412_0595_gb300 as snn
     net = gpu.GradedNetwork.from_spec(I.config_graded_small(steps=10))
     with pytest.raises(snn.SNNError) as e:
-        net.backward()
+        net.backward(torch.zeros((10, 20), device="cuda"))
     assert e.value.name == "SNN_ERR_STATE"

@@ -22,6 +22,19 @@ def _cos(a, b):
     return float(a @ b / (np.linalg.norm(a) * np.linalg.norm(b)))
 
 
+def _mse(net, target, K, backward=True):
+    """Recorded forward, squared-error loss of y (torch) and, optionally, the
+    adjoint seeded by its dL/dy."""
+    from paper_1412_0595_gb300.network import squared_error
+    tgt = target if isinstance(target, torch.Tensor) else torch.from_numpy(target)
+    y = net.forward_record(tgt.shape[0], checkpoint_every=K)
+    loss, dl = squared_error(y, tgt)
+    if not backward:
+        return loss, y
+    gs, gw = net.backward(dl)
+    return loss, y, gs, gw
+
+
 def _smooth_dense_spec(n_pre=12, n_mid=18, n_out=6):
     # no spikes: clamped pre cells near the release threshold drive passive
     # cells whose releases are centred at rest, so every weight matters
@@ -49,8 +62,7 @@ def test_dense_gradients_match_oracle_smooth_network(gpu, engine, sizes):
     net.set_option("dense_grad", engine)
     ref = GradedOracle(spec)
     target = I.target_trace(spec, T, ref.n_out)
-    loss = net.forward_record(torch.from_numpy(target), checkpoint_every=100)
-    gs, gw = net.backward()
+    loss, _, gs, gw = _mse(net, target, 100)
     rloss, _ = ref.forward(target.astype(np.float64))
     rgs, rgw = ref.backward()
     assert loss == pytest.approx(rloss, rel=1e-5)
@@ -66,7 +78,7 @@ def test_dense_forward_matches_oracle_200_neuron_copy(gpu):
     net = gpu.GradedNetwork.from_spec(spec)
     ref = GradedOracle(spec)
     target = I.target_trace(spec, T, ref.n_out)
-    loss, y = net.forward_record(torch.from_numpy(target), checkpoint_every=100, return_y=True)
+    loss, y = _mse(net, target, 100, backward=False)
     rloss, ry = ref.forward(target.astype(np.float64))
     assert loss == pytest.approx(rloss, rel=1e-3)
     assert np.abs(y.cpu().numpy() - ry).max() < 0.05
@@ -82,8 +94,7 @@ def test_dense_gradients_match_oracle_before_divergence(gpu, engine):
     net.set_option("dense_grad", engine)
     ref = GradedOracle(spec)
     target = I.target_trace(spec, T, ref.n_out)
-    net.forward_record(torch.from_numpy(target), checkpoint_every=64)
-    gs, gw = net.backward()
+    _, _, gs, gw = _mse(net, target, 64)
     ref.forward(target.astype(np.float64))
     rgs, rgw = ref.backward()
     assert _rel_l2(gs.cpu().numpy(), rgs) < 1e-3
@@ -106,8 +117,8 @@ def test_tensor_and_cuda_core_gradients_agree_for_every_segment_length(gpu):
         got = []
         for engine in (0, 1):
             net.set_option("dense_grad", engine)
-            losses.append(net.forward_record(target, checkpoint_every=K))
-            gs, gw = net.backward()
+            loss, _, gs, gw = _mse(net, target, K)
+            losses.append(loss)
             got.append((gs.cpu().numpy(), [g.cpu().numpy() for g in gw]))
         (gs0, gw0), (gs1, gw1) = got
         assert np.allclose(gs0, gs1, rtol=1e-12, atol=0), K   # dL/ds does not depend on the engine
@@ -128,11 +139,11 @@ def test_dense_weights_can_be_set_and_change_the_loss(gpu):
     net = gpu.GradedNetwork.from_spec(spec)
     ref = GradedOracle(spec)
     target = torch.from_numpy(I.target_trace(spec, T, ref.n_out))
-    l0 = net.forward_record(target, checkpoint_every=100)
+    l0 = _mse(net, target, 100, backward=False)[0]
     rl0, _ = ref.forward(target.numpy().astype(np.float64))
     w = np.random.default_rng(3).uniform(0.0, 600.0, ref.nnz[2]).astype(np.float32)
     net.set_weights(2, torch.from_numpy(w).cuda())
-    l1 = net.forward_record(target, checkpoint_every=100)
+    l1 = _mse(net, target, 100, backward=False)[0]
     for k in range(ref.nnz[2]):
         ref.set_weight(2, k, float(w[k]))
     rl1, _ = ref.forward(target.numpy().astype(np.float64))
@@ -141,4 +152,4 @@ def test_dense_weights_can_be_set_and_change_the_loss(gpu):
     assert l1 == pytest.approx(rl1, rel=1e-2)
     w0 = I.weights(spec, 2, ref.nnz[2]).astype(np.float32)
     net.set_weights(2, torch.from_numpy(w0).cuda())
-    assert net.forward_record(target, checkpoint_every=100) == l0
+    assert _mse(net, target, 100, backward=False)[0] == l0
