@@ -263,6 +263,15 @@ __global__ void __launch_bounds__(MAXT, 1) k_step_cluster(const PersistArgs A, i
         hh_reg = P.kind == SNN_POP_HH;
         if (hh_reg) hc = hh_pair_consts(P, a.hs);
     }
+    // Such a pair's drive events and first-substep rates of the next step
+    // depend on nothing a pull delivers: they are computed while the
+    // end-of-step cluster barrier completes.
+    RatesT<float2> r_next{};
+    unsigned drive_next = 0u;
+    if (PPT == 1 && hh_reg) {
+        r_next = hh_rates(st[0].V);
+        drive_next = hh_drive_pair(hc, key, (uint32_t)(epoch0 - ebase), local_of[0]);
+    }
     // the list lengths of the launch's last step (and of the step after it)
     // start at zero; only the last step writes the API spike list
 #pragma unroll
@@ -346,7 +355,7 @@ __global__ void __launch_bounds__(MAXT, 1) k_step_cluster(const PersistArgs A, i
                 }
                 float2 isyn;
                 if (PPT == 1 && hh_reg)
-                    spike = hh_step_pair(hc, key, t, local_of[u], a.n_sub, st[u], &isyn) & live[u];
+                    spike = hh_step_pair_given(hc, drive_next, r_next, a.n_sub, st[u], &isyn) & live[u];
                 else
                     spike = neuron_step_pair(P, key, t, local_of[u], a.hs, a.n_sub, st[u], &isyn) & live[u];
                 if (P.kind != SNN_POP_SOURCE) {
@@ -392,6 +401,10 @@ __global__ void __launch_bounds__(MAXT, 1) k_step_cluster(const PersistArgs A, i
         // (see acc_k above), so a step without spikes runs no fence.
         if (wrote) asm volatile("fence.acq_rel.cluster;" ::: "memory");
         asm volatile("barrier.cluster.arrive.relaxed.aligned;" ::: "memory");
+        if (PPT == 1 && hh_reg && !last) {
+            r_next = hh_rates(st[0].V);
+            drive_next = hh_drive_pair(hc, key, t + 1u, local_of[0]);
+        }
         asm volatile("barrier.cluster.wait.acquire.aligned;" ::: "memory");
     }
     const float* acc_end = acc + (A.n_steps & 1) * 2 * per_cta;

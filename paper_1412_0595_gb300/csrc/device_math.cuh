@@ -46,14 +46,6 @@ __device__ __forceinline__ float linoid(float x) {
     return x / expm1f(x);
 }
 
-// Taylor series of x / (exp(x) - 1) about 0 to x^4 (Bernoulli numbers
-// B1 = -1/2, B2 = 1/6, B4 = -1/30): 1 - x/2 + x^2/12 - x^4/720; the first
-// omitted term is x^6/30240, below 2e-11 for |x| < 0.1.
-__device__ __forceinline__ float linoid_series(float x) {
-    const float x2 = x * x;
-    return fmaf(x2, fmaf(x2, -1.0f / 720.0f, 1.0f / 12.0f), fmaf(-0.5f, x, 1.0f));
-}
-
 struct HHCell {
     float gNa, ENa, gK, EK, gL, EL;
 };
@@ -106,66 +98,70 @@ template <class T> struct RatesT {
     T am, bm, ah, bh, an, bn;
 };
 
-// Traub-Miles rates (1/ms, V in mV):
-//   alpha_m = 1.28 x / (exp(x) - 1), x = (-52 - V)/4     beta_m = 1.4 y / (exp(y) - 1), y = (V + 25)/5
-//   alpha_h = 0.128 exp((-48 - V)/18)                   beta_h = 4 / (exp(-y) + 1)
-//   alpha_n = 0.16 z / (exp(z) - 1), z = (-50 - V)/5     beta_n = 0.5 exp((-55 - V)/40)
-//
-// Careful form, one neuron: four exponentials and a reciprocal per rational
-// rate.  E = exp(y) serves three rates: beta_h = 4 E / (E + 1) and, with
-// exp(z) = exp(-5) / E, alpha_n = 0.16 z E / (exp(-5) - E).  Linoid rates
-// switch to the series for |argument| < 0.1, where exp(x) - 1 loses digits
-// to cancellation.
-__device__ __forceinline__ HHRates hh_rates_careful(float V) {
-    constexpr float L = 1.4426950408889634f;             // log2(e)
-    constexpr float kExpM5 = 6.737946999085467e-3f;     // exp(-5)
-    const float xs = fmaf(V, -0.25f * 1.28f, -13.0f * 1.28f);   // 1.28 x
-    const float ys = fmaf(V, 0.2f * 1.4f, 5.0f * 1.4f);         // 1.4 y
-    const float zs = fmaf(V, -0.2f * 0.16f, -10.0f * 0.16f);    // 0.16 z
-    const float Em = ex2_fast(fmaf(V, -0.25f * L, -13.0f * L));
-    const float E = ex2_fast(fmaf(V, 0.2f * L, 5.0f * L));
-    HHRates r;
-    r.ah = ex2_fast(fmaf(V, -L / 18.0f, -48.0f * L / 18.0f - 2.965784284662087f));   // + log2 0.128
-    r.bn = ex2_fast(fmaf(V, -L / 40.0f, -55.0f * L / 40.0f - 1.0f));                 // + log2 0.5
-    r.am = xs * rcp_fast(Em - 1.0f);
-    r.bm = ys * rcp_fast(E - 1.0f);
-    r.an = zs * E * rcp_fast(kExpM5 - E);
-    const float x = fmaf(V, -0.25f, -13.0f), y = fmaf(V, 0.2f, 5.0f), z = fmaf(V, -0.2f, -10.0f);
-    if (fabsf(x) < 0.1f) r.am = 1.28f * linoid_series(x);
-    if (fabsf(y) < 0.1f) r.bm = 1.4f * linoid_series(y);
-    if (fabsf(z) < 0.1f) r.an = 0.16f * linoid_series(z);
-    r.bh = 4.0f * E * rcp_fast(E + 1.0f);
-    return r;
+// Per-element helpers of the near-singularity handling.
+struct Near1 {
+    bool x, y, z;
+};
+struct Near2 {
+    Near1 e0, e1;
+};
+__device__ __forceinline__ Near1 near_flags(float xs, float ys, float zs) {
+    // |x| < 0.05 <=> |1.28 x| < 0.064, |y| < 0.05 <=> |1.4 y| < 0.07, |z| < 0.05 <=> |0.16 z| < 0.008
+    return Near1{fabsf(xs) < 0.064f, fabsf(ys) < 0.07f, fabsf(zs) < 0.008f};
+}
+__device__ __forceinline__ Near1 near_of(float xs, float ys, float zs) { return near_flags(xs, ys, zs); }
+__device__ __forceinline__ Near2 near_of(float2 xs, float2 ys, float2 zs) {
+    return Near2{near_flags(xs.x, ys.x, zs.x), near_flags(xs.y, ys.y, zs.y)};
+}
+__device__ __forceinline__ bool any_near(const Near1& f) { return f.x | f.y | f.z; }
+__device__ __forceinline__ bool any_near(const Near2& f) { return any_near(f.e0) | any_near(f.e1); }
+__device__ __forceinline__ float sel_x(const Near1& f, float a, float b) { return f.x ? a : b; }
+__device__ __forceinline__ float sel_y(const Near1& f, float a, float b) { return f.y ? a : b; }
+__device__ __forceinline__ float sel_z(const Near1& f, float a, float b) { return f.z ? a : b; }
+__device__ __forceinline__ float2 sel_x(const Near2& f, float2 a, float2 b) {
+    return make_float2(f.e0.x ? a.x : b.x, f.e1.x ? a.y : b.y);
+}
+__device__ __forceinline__ float2 sel_y(const Near2& f, float2 a, float2 b) {
+    return make_float2(f.e0.y ? a.x : b.x, f.e1.y ? a.y : b.y);
+}
+__device__ __forceinline__ float2 sel_z(const Near2& f, float2 a, float2 b) {
+    return make_float2(f.e0.z ? a.x : b.x, f.e1.z ? a.y : b.y);
 }
 
-// The careful form covers -52.4 < V < -24.5 mV (every linoid argument within
-// 0.1 of its singularity lies there); outside it the fast form below applies.
-__device__ __forceinline__ bool rates_need_care(float V) { return fabsf(V + 38.45f) < 13.95f; }
-
-// Fast form: the four denominators a = exp(x) - 1, b = exp(y) - 1,
-// c = exp(-5) - exp(y), d = exp(y) + 1 share one reciprocal r = 1/(a b c d),
-// and 1/a = b (c d r), 1/b = a (c d r), 1/c = d (a b r), 1/d = c (a b r):
-// four exponentials and one reciprocal instead of four and four.  Outside
-// [-52.4, -24.5] mV no denominator is near zero; the product overflows FP32
+// Traub-Miles rates, one or two neurons.  The four denominators of the
+// rational rates, a = exp(x) - 1, b = exp(y) - 1, c = exp(-5) - exp(y) and
+// d = exp(y) + 1 (E = exp(y) also serves beta_h = 4 E / (E + 1) and, with
+// exp(z) = exp(-5) / E, alpha_n = 0.16 z E / (exp(-5) - E)), share one
+// reciprocal r = 1/(a b c d): 1/a = b (c d r), 1/b = a (c d r),
+// 1/c = d (a b r), 1/d = c (a b r) -- four exponentials and one reciprocal.
+// Near a removable singularity (linoid argument within 0.05 of zero, where
+// exp(x) - 1 would lose digits to cancellation) the rate is the series
+// k (1 - x/2 + x^2/12) (the omitted x^4/720 is below 1e-8 relative there) and
+// its denominator enters the product as 1, so the other rates, in which it
+// cancels, stay exact and nothing divides by zero.  Outside those windows the
+// cancellation error is below 5e-6 relative.  The product overflows FP32
 // only above about +120 mV (the rates then turn NaN, as the separate
 // reciprocals do from about +390 mV), far outside the Euler dynamics of a
-// stable run.
-template <class T>
-__device__ __forceinline__ RatesT<T> hh_rates_fast(T V) {
-    constexpr float L = 1.4426950408889634f;
+// stable run.  The windows are rare (an upstroke crosses each in about one
+// substep), so a warp takes the careful form only when one of its lanes is in
+// one; both forms give the same value outside the windows.
+template <class T, bool kCareful>
+__device__ __forceinline__ RatesT<T> hh_rates_form(T V, T xs, T ys, T zs, T Em, T E) {
     constexpr float kExpM5 = 6.737946999085467e-3f;
-    const T xs = vfma(V, splat<T>(-0.25f * 1.28f), splat<T>(-13.0f * 1.28f));
-    const T ys = vfma(V, splat<T>(0.2f * 1.4f), splat<T>(5.0f * 1.4f));
-    const T zs = vfma(V, splat<T>(-0.2f * 0.16f), splat<T>(-10.0f * 0.16f));
-    const T Em = vex2(vfma(V, splat<T>(-0.25f * L), splat<T>(-13.0f * L)));
-    const T E = vex2(vfma(V, splat<T>(0.2f * L), splat<T>(5.0f * L)));
+    constexpr float L = 1.4426950408889634f;
     RatesT<T> r;
-    r.ah = vex2(vfma(V, splat<T>(-L / 18.0f), splat<T>(-48.0f * L / 18.0f - 2.965784284662087f)));
-    r.bn = vex2(vfma(V, splat<T>(-L / 40.0f), splat<T>(-55.0f * L / 40.0f - 1.0f)));
-    const T a = vadd(Em, splat<T>(-1.0f));
-    const T b = vadd(E, splat<T>(-1.0f));
-    const T c = vfma(E, splat<T>(-1.0f), splat<T>(kExpM5));
+    r.ah = vex2(vfma(V, splat<T>(-L / 18.0f), splat<T>(-48.0f * L / 18.0f - 2.965784284662087f)));   // + log2 0.128
+    r.bn = vex2(vfma(V, splat<T>(-L / 40.0f), splat<T>(-55.0f * L / 40.0f - 1.0f)));                 // + log2 0.5
+    T a = vadd(Em, splat<T>(-1.0f));
+    T b = vadd(E, splat<T>(-1.0f));
+    T c = vfma(E, splat<T>(-1.0f), splat<T>(kExpM5));
     const T d = vadd(E, splat<T>(1.0f));
+    const auto nf = near_of(xs, ys, zs);
+    if (kCareful) {
+        a = sel_x(nf, splat<T>(1.0f), a);
+        b = sel_y(nf, splat<T>(1.0f), b);
+        c = sel_z(nf, splat<T>(1.0f), c);
+    }
     const T ab = vmul(a, b), cd = vmul(c, d);
     const T rr = vrcp(vmul(ab, cd));
     const T abr = vmul(ab, rr), cdr = vmul(cd, rr);
@@ -173,27 +169,41 @@ __device__ __forceinline__ RatesT<T> hh_rates_fast(T V) {
     r.bm = vmul(ys, vmul(a, cdr));
     r.an = vmul(vmul(zs, E), vmul(d, abr));
     r.bh = vmul(vmul(E, splat<T>(4.0f)), vmul(c, abr));
+    if (kCareful) {
+        // k L(x) as a quadratic in xs = k x: k - xs/2 + xs^2 / (12 k); for
+        // alpha_n, E cancels: 0.16 z E / (exp(-5) - E) = 0.16 L(z)
+        const T sm = vfma(xs, vfma(xs, splat<T>(1.0f / (12.0f * 1.28f)), splat<T>(-0.5f)), splat<T>(1.28f));
+        const T sb = vfma(ys, vfma(ys, splat<T>(1.0f / (12.0f * 1.4f)), splat<T>(-0.5f)), splat<T>(1.4f));
+        const T sn = vfma(zs, vfma(zs, splat<T>(1.0f / (12.0f * 0.16f)), splat<T>(-0.5f)), splat<T>(0.16f));
+        r.am = sel_x(nf, sm, r.am);
+        r.bm = sel_y(nf, sb, r.bm);
+        r.an = sel_z(nf, sn, r.an);
+    }
     return r;
+}
+
+__device__ __forceinline__ unsigned active_lanes() { return __activemask(); }
+
+template <class T>
+__device__ __forceinline__ RatesT<T> hh_rates_t(T V) {
+    constexpr float L = 1.4426950408889634f;
+    const T xs = vfma(V, splat<T>(-0.25f * 1.28f), splat<T>(-13.0f * 1.28f));   // 1.28 x, x = (-52 - V)/4
+    const T ys = vfma(V, splat<T>(0.2f * 1.4f), splat<T>(5.0f * 1.4f));         // 1.4 y,  y = (V + 25)/5
+    const T zs = vfma(V, splat<T>(-0.2f * 0.16f), splat<T>(-10.0f * 0.16f));    // 0.16 z, z = (-50 - V)/5
+    const T Em = vex2(vfma(V, splat<T>(-0.25f * L), splat<T>(-13.0f * L)));
+    const T E = vex2(vfma(V, splat<T>(0.2f * L), splat<T>(5.0f * L)));
+    // warp-uniform choice of the form (every lane of the warp takes the same branch)
+    if (__any_sync(active_lanes(), any_near(near_of(xs, ys, zs))))
+        return hh_rates_form<T, true>(V, xs, ys, zs, Em, E);
+    return hh_rates_form<T, false>(V, xs, ys, zs, Em, E);
 }
 
 __device__ __forceinline__ HHRates hh_rates(float V) {
-    if (rates_need_care(V)) return hh_rates_careful(V);
-    const RatesT<float> f = hh_rates_fast<float>(V);
+    const RatesT<float> f = hh_rates_t<float>(V);
     return HHRates{f.am, f.bm, f.ah, f.bh, f.an, f.bn};
 }
 
-__device__ __forceinline__ RatesT<float2> hh_rates(float2 V) {
-    RatesT<float2> r = hh_rates_fast<float2>(V);
-    if (rates_need_care(V.x)) {
-        const HHRates c = hh_rates_careful(V.x);
-        r.am.x = c.am; r.bm.x = c.bm; r.ah.x = c.ah; r.bh.x = c.bh; r.an.x = c.an; r.bn.x = c.bn;
-    }
-    if (rates_need_care(V.y)) {
-        const HHRates c = hh_rates_careful(V.y);
-        r.am.y = c.am; r.bm.y = c.bm; r.ah.y = c.ah; r.bh.y = c.bh; r.an.y = c.an; r.bn.y = c.bn;
-    }
-    return r;
-}
+__device__ __forceinline__ RatesT<float2> hh_rates(float2 V) { return hh_rates_t<float2>(V); }
 
 __device__ __forceinline__ RatesT<float> as_rates_t(const HHRates& r) {
     return RatesT<float>{r.am, r.bm, r.ah, r.bh, r.an, r.bn};
@@ -213,13 +223,14 @@ __device__ __forceinline__ HHConstT<T> hh_consts(const HHCell& c, float hs, floa
                        splat<T>(c.gNa * c.ENa), splat<T>(hs), splat<T>(hs_over_C), splat<T>(c.gL * c.EL)};
 }
 
-// One forward-Euler substep with every right-hand side at the substep start;
-// I_base = I_syn + I_ext + gL EL (held over the substeps).
+// One forward-Euler substep with every right-hand side at the substep start,
+// given the rates at V; I_base = I_syn + I_ext + gL EL (held over the
+// substeps).
 //   V += hs/C (I_base - gL V - gK n^4 (V - EK) - gNa m^3 h (V - ENa))
 //   x += hs (alpha_x - (alpha_x + beta_x) x),  x in {m, h, n}
 template <class T>
-__device__ __forceinline__ void hh_substep_t(const HHConstT<T>& k, T I_base, T& V, T& m, T& h, T& n) {
-    const RatesT<T> r = as_rates_t(hh_rates(V));
+__device__ __forceinline__ void hh_substep_r(const HHConstT<T>& k, const RatesT<T>& r, T I_base, T& V, T& m, T& h,
+                                             T& n) {
     const T m3h = vmul(vmul(vmul(m, m), m), h);
     const T n2 = vmul(n, n);
     const T n4 = vmul(n2, n2);
@@ -230,6 +241,11 @@ __device__ __forceinline__ void hh_substep_t(const HHConstT<T>& k, T I_base, T& 
     h = vfma(k.hs, vfma(vneg(vadd(r.ah, r.bh)), h, r.ah), h);
     n = vfma(k.hs, vfma(vneg(vadd(r.an, r.bn)), n, r.an), n);
     V = vfma(k.hs_over_C, I, V);
+}
+
+template <class T>
+__device__ __forceinline__ void hh_substep_t(const HHConstT<T>& k, T I_base, T& V, T& m, T& h, T& n) {
+    hh_substep_r<T>(k, as_rates_t(hh_rates(V)), I_base, V, m, h, n);
 }
 
 // One-neuron form used by the graded network's forward and adjoint passes

@@ -147,25 +147,33 @@ __device__ __forceinline__ HHPairConsts hh_pair_consts(const DevPop& P, float hs
     return c;
 }
 
-// The HH update of neurons local and local + 1 through step t (the pair form
-// of neuron_step's HH branch, identical per element).
-__device__ __forceinline__ unsigned hh_step_pair(const HHPairConsts& c, PhiloxKey key, uint32_t t, int local, int n_sub,
-                                                 NeuronPair& s, float2* isyn) {
-    if (c.thr_drive) {
-        const uint4 r0 = philox_4x32_10(make_uint4((uint32_t)local, t, c.tag, kStreamDrive), key);
-        const uint4 r1 = philox_4x32_10(make_uint4((uint32_t)local + 1u, t, c.tag, kStreamDrive), key);
-        if (below(r0.x, c.thr_drive)) s.ie.x += c.drive_amp;
-        if (below(r1.x, c.thr_drive)) s.ie.y += c.drive_amp;
-    }
+// The drive events of neurons local and local + 1 at step t (bit e: one
+// event for neuron local + e).
+__device__ __forceinline__ unsigned hh_drive_pair(const HHPairConsts& c, PhiloxKey key, uint32_t t, int local) {
+    if (!c.thr_drive) return 0u;
+    const uint4 r0 = philox_4x32_10(make_uint4((uint32_t)local, t, c.tag, kStreamDrive), key);
+    const uint4 r1 = philox_4x32_10(make_uint4((uint32_t)local + 1u, t, c.tag, kStreamDrive), key);
+    return (below(r0.x, c.thr_drive) ? 1u : 0u) | (below(r1.x, c.thr_drive) ? 2u : 0u);
+}
+
+// The HH update of neurons local and local + 1 through one step (the pair
+// form of neuron_step's HH branch, identical per element), given the step's
+// drive events and the rates at the step-start potentials (both depend on
+// nothing a pull delivers, so a caller may compute them early).
+__device__ __forceinline__ unsigned hh_step_pair_given(const HHPairConsts& c, unsigned drive, const RatesT<float2>& r0,
+                                                       int n_sub, NeuronPair& s, float2* isyn) {
+    if (drive & 1u) s.ie.x += c.drive_amp;
+    if (drive & 2u) s.ie.y += c.drive_amp;
     const float2 V0 = s.V;
     const float2 m1 = splat<float2>(-1.0f);
     const float2 I_syn = vfma(s.g0, vfma(V0, m1, c.E0), vmul(s.g1, vfma(V0, m1, c.E1)));
     const float2 I_base = vadd(vadd(I_syn, s.ie), c.k.gLEL);
+    hh_substep_r<float2>(c.k, r0, I_base, s.V, s.m, s.h, s.n);
     if (n_sub == 4) {
 #pragma unroll
-        for (int q = 0; q < 4; ++q) hh_substep_t<float2>(c.k, I_base, s.V, s.m, s.h, s.n);
+        for (int q = 1; q < 4; ++q) hh_substep_t<float2>(c.k, I_base, s.V, s.m, s.h, s.n);
     } else {
-        for (int q = 0; q < n_sub; ++q) hh_substep_t<float2>(c.k, I_base, s.V, s.m, s.h, s.n);
+        for (int q = 1; q < n_sub; ++q) hh_substep_t<float2>(c.k, I_base, s.V, s.m, s.h, s.n);
     }
     s.g0 = vmul(s.g0, c.d0);
     s.g1 = vmul(s.g1, c.d1);
@@ -173,6 +181,12 @@ __device__ __forceinline__ unsigned hh_step_pair(const HHPairConsts& c, PhiloxKe
     *isyn = I_syn;
     return ((V0.x < c.v_thresh) && (s.V.x >= c.v_thresh) ? 1u : 0u) |
            ((V0.y < c.v_thresh) && (s.V.y >= c.v_thresh) ? 2u : 0u);
+}
+
+__device__ __forceinline__ unsigned hh_step_pair(const HHPairConsts& c, PhiloxKey key, uint32_t t, int local, int n_sub,
+                                                 NeuronPair& s, float2* isyn) {
+    const unsigned drive = hh_drive_pair(c, key, t, local);
+    return hh_step_pair_given(c, drive, hh_rates(s.V), n_sub, s, isyn);
 }
 
 __device__ __forceinline__ unsigned neuron_step_pair(const DevPop& P, PhiloxKey key, uint32_t t, int local,
