@@ -59,11 +59,6 @@ def _args():
                     help="time steps run before the per-kernel timing")
     ap.add_argument("--phase-reps", type=int, default=200,
                     help="back-to-back launches per kernel in the per-kernel timing")
-    ap.add_argument("--tiled-crossover", action="store_true",
-                    help="print one JSON line per (posts, density) point timing the row kernel against the "
-                         "post-tiled kernel on forced activity (the data behind the post-tiled threshold)")
-    ap.add_argument("--sweep", action="store_true",
-                    help="print one JSON line per point of the scaling sweep instead of the headline line")
     ap.add_argument("--no-batched", action="store_true", help="skip the batched-vs-sequential comparison")
     ap.add_argument("--batch-instances", type=int, default=512)
     ap.add_argument("--batch-steps", type=int, default=5000)
@@ -77,12 +72,6 @@ def _args():
                     help="skip the occupancy-rule baseline (the paper's block sizing) beside the autotuned run")
     ap.add_argument("--no-scale-point", action="store_true",
                     help="skip the forced-activity propagation measurement at 100 x 1,000,000, p = 0.5")
-    ap.add_argument("--profile", choices=["cluster", "tiled", "dense", "neuron", "graded", "dense_batch", "dense_grad",
-                                          "graded_dense", "csr_mid"],
-                    help="run a few launches of one kernel on its workload and exit (a target for ncu)")
-    ap.add_argument("--record-traffic", nargs=3, metavar=("KERNEL", "BYTES", "COMMAND"),
-                    help="store an ncu DRAM byte count per launch of KERNEL (with a hash of its sources) in "
-                         "profiles/traffic.json and exit")
     return ap.parse_args()
 
 
@@ -180,50 +169,6 @@ def _forced_propagation(snn, torch, dev, n_mid, p, layout, reps=7, flush=None):
             "us": t * 1e6, "gbs": nbytes / t / 1e9, "events_per_s": events / t}
 
 
-def run_tiled_crossover(a):
-    """Forced activity (100 spiking rows, caches flushed before each of 7
-    launches, median): the row kernel (SNN_OPT_TILED 0) against the
-    post-tiled kernel (1) at several post-population sizes and densities;
-    fraction of the measured copy bandwidth at 8 B per synapse."""
-    import torch
-
-    import paper_1412_0595_gb300 as snn
-    dev = torch.device("cuda", 0)
-    torch.cuda.set_device(dev)
-    peaks, _ = _peaks()
-    hbm = float(peaks.get("hbm_gbs", 6800.0))
-    flush = _flush_buffers(torch, dev)
-    rows = np.arange(100, dtype=np.int32)
-    for n_mid in (1_000_000, 300_000, 100_000):
-        for p in (0.01, 0.02, 0.05, 0.1, 0.2, 0.5):
-            spec = I.net([I.source_pop(100, 0.0), I.hh_pop(n_mid)],
-                         [I.proj(0, 1, "csr", p, ("lognormal", -3.0, 0.5))], dt=0.1, steps=1)
-            net = snn.Network.from_spec(spec, device=dev)
-            net.debug_propagate(0, rows)
-            nnz = net.nnz(0)
-            line = {"n_mid": n_mid, "p": p, "synapses": nnz}
-            for t in (0, 1):
-                net.set_option("tiled", t)
-                net.debug_propagate(0, rows)
-                s = torch.cuda.current_stream()
-                times = []
-                for _ in range(7):
-                    _flush_l2(flush)
-                    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-                    e0.record(s)
-                    net.launch_phase(3)
-                    e1.record(s)
-                    e1.synchronize()
-                    times.append(e0.elapsed_time(e1))
-                net.sync()
-                us = statistics.median(times) * 1e3
-                name = "row" if t == 0 else "tiled"
-                line[name + "_us"] = us
-                line[name + "_frac_hbm"] = nnz * BYTES_PER_EVENT / (us * 1e-6) / 1e9 / hbm
-            print(json.dumps(line), flush=True)
-            net.close()
-
-
 def _neuron_rate(snn, torch, dev, n, reps=50):
     spec = I.net([I.hh_pop(n)], [], dt=0.1, steps=1)
     net = snn.Network.from_spec(spec, device=dev)
@@ -234,31 +179,13 @@ def _neuron_rate(snn, torch, dev, n, reps=50):
     return {"n": n, "us": t * 1e3, "neuron_steps_per_s": n / (t * 1e-3), "tflops": flops / (t * 1e-3) / 1e12}
 
 
-def run_sweep(a):
-    import torch
-
-    import paper_1412_0595_gb300 as snn
-    dev = torch.device("cuda", 0)
-    torch.cuda.set_device(dev)
-    peaks, src = _peaks()
-    hbm = float(peaks.get("hbm_gbs", 6800.0))
-    flush = _flush_buffers(torch, dev)
-    for n in I.SWEEP_N_MID:
-        r = _neuron_rate(snn, torch, dev, n)
-        r["kind"] = "neuron_update"
-        print(json.dumps(r), flush=True)
-        for p in I.SWEEP_P:
-            for layout in ("csr", "dense"):
-                r = _forced_propagation(snn, torch, dev, n, p, layout, flush=flush)
-                r.update(kind="propagation", frac_hbm=r["gbs"] / hbm, hbm_peak=hbm, peak_source=src)
-                print(json.dumps(r), flush=True)
-
-
-def _batched(snn, torch, dev, n_inst, steps):
+def _batched(snn, torch, dev, n_inst, steps, weight_hi=0.05):
     """The batched form (n_inst instances of the small workload, middle sizes
     and conductance factors log-uniform, one network object) against the same
-    instances run one after another as stand-alone networks."""
-    specs = I.config_batched(n_inst, steps=steps)
+    instances run one after another as stand-alone networks.  weight_hi = 60
+    nS is the forced-activity variant (the 0.05 nS of the small workload
+    leaves every middle population silent under the 1/(p N_pre) scaling)."""
+    specs = I.config_batched(n_inst, steps=steps, weight_hi=weight_hi)
     batch = snn.Network.from_specs(specs, device=dev)
     tune = batch.autotune(trial_steps=100)
     batch.reset()
@@ -291,8 +218,16 @@ def _batched(snn, torch, dev, n_inst, steps):
     for net in solos:
         net.close()
     neuron_steps = (sum(n_hh) + 100 * n_inst) * steps
+    # per-instance agreement of the rates in the sense of the 2 % rule
+    # (|r_b - r_s| <= 0.02 r_s + one spike over the run), NaN-free instances only
+    spikes_b = rate_b * np.array(n_hh) * steps * specs[0]["dt"] * 1e-3
+    spikes_s = rate_s * np.array(n_hh) * steps * specs[0]["dt"] * 1e-3
+    clean = (nan_b == 0) & (nan_s == 0)
+    within = np.abs(spikes_b - spikes_s) <= 0.02 * spikes_s + 1.0
     return {"workload": f"{n_inst} instances of 100 Poisson sources -> N HH (p = 0.1), N log-uniform 1k-50k, "
-                        f"conductance factor log-uniform 0.1-10, {steps} steps",
+                        f"conductance factor log-uniform 0.1-10, weights U(0, {weight_hi}) nS, {steps} steps",
+            "instances_spiking": int((spikes_s > 0).sum()),
+            "rates_within_2pct_plus_one_spike": int((within & clean).sum()), "nan_free_instances": int(clean.sum()),
             "neurons": sum(n_hh) + 100 * n_inst, "autotune": tune,
             "batched_s": t_batch, "sequential_s": t_seq, "speedup": t_seq / t_batch,
             "batched_neuron_steps_per_s": neuron_steps / t_batch,
@@ -318,6 +253,44 @@ def _plain_forward_runs(net, steps, n=6):
     for _ in range(n):
         net.reset()
         net.step(steps)
+
+
+def _largest_sweep_network(snn, torch, dev, flush, steps=1000):
+    """The whole time step at the scaling sweep's largest point: In 100
+    (driven) -> Mid 1,000,000 (compressed rows, p = 0.5: 5e7 synapses) -> Out
+    100 (dense, 1e8 weights), 1000 steps through snn_step with the autotuned
+    launch configuration, L2 flushed before each timed run.  Reports synaptic
+    events/s, HH neuron-steps/s and the per-phase kernel times."""
+    spec = I.config_sweep(1_000_000, 0.5, "csr", steps=steps)
+    net = snn.Network.from_spec(spec, device=dev)
+    tune = net.autotune(trial_steps=200)
+    s = torch.cuda.current_stream()
+    ms, evs = [], []
+    for k in range(4):
+        net.reset()
+        _flush_l2(flush)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(s)
+        net.step(steps)
+        e1.record(s)
+        e1.synchronize()
+        if k:                                   # the first run warms up
+            ms.append(e0.elapsed_time(e1))
+            evs.append(net.synaptic_events())
+    t = statistics.median(ms) * 1e-3
+    n_neurons = sum(p["n"] for p in spec["pops"])
+    spikes = [net.counters(p)[0] for p in range(len(spec["pops"]))]
+    out = {"workload": spec["name"] + f", {steps} steps", "neurons": n_neurons, "synapses": net.nnz(0),
+           "dense_weights": net.nnz(1), "engine": net.engine, "autotune": tune, "ms": t * 1e3,
+           "synaptic_events_per_s": statistics.median(evs) / t, "neuron_steps_per_s": n_neurons * steps / t,
+           "spikes_per_population": spikes}
+    if net.engine == "plain":
+        t_n = _phase_time_ms(net, 0, 50, torch)
+        t_p = _phase_time_ms(net, 1, 50, torch)
+        out.update({"k_neuron_step_us": t_n * 1e3, "k_propagate_us": t_p * 1e3,
+                    "neuron_kernel_steps_per_s": n_neurons / (t_n * 1e-3)})
+    net.close()
+    return out
 
 
 def _differentiable(snn, torch, dev, steps=2000, K=100):
@@ -789,9 +762,13 @@ def run_ours(a):
     if not a.no_e2e:
         e2e = _e2e(a, spec, dev, torch, snn)
 
-    batched = None
+    batched = batched_forced = None
     if not a.no_batched and rank == 0:
         batched = _batched(snn, torch, dev, a.batch_instances, a.batch_steps)
+        batched_forced = _batched(snn, torch, dev, a.batch_instances, a.batch_steps, weight_hi=60.0)
+    largest = None
+    if not a.no_scale_point and rank == 0:
+        largest = _largest_sweep_network(snn, torch, dev, flush)
     differentiable = None
     if not a.no_graded and rank == 0:
         differentiable = _differentiable(snn, torch, dev)
@@ -831,6 +808,8 @@ def run_ours(a):
                 "autotune": tune,
                 "occupancy_baseline": occupancy,
                 "batched": batched,
+                "batched_forced_activity": batched_forced,
+                "largest_sweep_network": largest,
                 "differentiable": differentiable,
                 "dense_batch": dense_batch,
                 "differentiable_dense": graded_dense,
@@ -937,84 +916,6 @@ def _e2e(a, spec, dev, torch, snn):
                     "network creation, 10,000 time steps, D2H of counters"}
 
 
-def run_profile(a):
-    """A few launches of one kernel on its workload, nothing timed: the
-    command the ncu summaries under profiles/ were captured from.
-      cluster: the four-population network, cluster engine, 1000 steps per launch;
-      tiled:   forced-activity propagation, 100 rows x 1,000,000 posts, p = 0.5, CSR;
-      csr_mid: the same at p = 0.05 (below the post-tiled threshold: the row kernel);
-      dense:   the same with dense rows;
-      neuron:  8,000,000 HH neurons, one neuron phase per launch;
-      graded:  the differentiable workload (20,000 middle neurons), 200 steps
-               recorded forward and the adjoint;
-      dense_batch: tensor-core delivery for 1024 instances sharing a 4096 x 4096
-               dense projection, half of the pre neurons spiking, three launches;
-      dense_grad: the tensor-core rank-100 weight-gradient update of a 4096 x 4096
-               dense projection, three launches;
-      graded_dense: the dense differentiable workload (4096 middle neurons), 200
-               steps recorded forward and the adjoint."""
-    import torch
-
-    import paper_1412_0595_gb300 as snn
-    dev = torch.device("cuda", 0)
-    torch.cuda.set_device(dev)
-    if a.profile == "cluster":
-        net = snn.Network.from_spec(I.config_four_pop(steps=1), device=dev)
-        net.set_option("engine", 3)
-        net.set_option("persist_steps", 1000)
-        for _ in range(3):
-            net.launch_phase(4)
-    elif a.profile in ("tiled", "dense", "csr_mid"):
-        flush = _flush_buffers(torch, dev)
-        p = 0.05 if a.profile == "csr_mid" else 0.5
-        _forced_propagation(snn, torch, dev, 1_000_000, p, "dense" if a.profile == "dense" else "csr", reps=3,
-                            flush=flush)
-        return
-    elif a.profile == "dense_batch":
-        rng = np.random.default_rng(11)
-        W = torch.from_numpy(rng.lognormal(-3.0, 0.5, (4096, 4096)).astype(np.float32))
-        h = snn.DenseBatch(W, device=dev)
-        spikes = [np.sort(rng.choice(4096, 2048, replace=False)) for _ in range(1024)]
-        G = torch.zeros((1024, 4096), dtype=torch.float32, device=dev)
-        scale = torch.ones(1024, dtype=torch.float32, device=dev)
-        for _ in range(3):
-            h.deliver(spikes, scale, G, engine="tensor")
-        h.check()
-        h.close()
-        return
-    elif a.profile == "dense_grad":
-        rng = np.random.default_rng(12)
-        R = torch.from_numpy(rng.uniform(0, 1, (100, 4096)).astype(np.float32)).to(dev)
-        N = torch.from_numpy(rng.normal(0, 1, (4096, 100)).astype(np.float32)).to(dev)
-        D = torch.zeros((4096, 4096), dtype=torch.float32, device=dev)
-        h = snn.DenseGrad(device=dev)
-        for _ in range(3):
-            h.run(R, N, D, engine="tensor")
-        h.check()
-        h.close()
-        return
-    elif a.profile == "graded_dense":
-        from paper_1412_0595_gb300.network import squared_error
-        spec = I.config_graded_dense(steps=200)
-        net = snn.GradedNetwork.from_spec(spec, device=dev)
-        target = torch.from_numpy(I.target_trace(spec, 200, spec["pops"][-1]["n"])).to(dev)
-        net.backward(squared_error(net.forward_record(200, checkpoint_every=100), target)[1])
-    elif a.profile == "neuron":
-        net = snn.Network.from_spec(I.net([I.hh_pop(8_000_000)], [], dt=0.1, steps=1), device=dev)
-        net.set_option("engine", 0)
-        for _ in range(4):
-            net.launch_phase(0)
-    else:
-        from paper_1412_0595_gb300.network import squared_error
-        spec = I.config_graded(steps=200)
-        net = snn.GradedNetwork.from_spec(spec, device=dev)
-        target = torch.from_numpy(I.target_trace(spec, 200, spec["pops"][-1]["n"])).to(dev)
-        net.backward(squared_error(net.forward_record(200, checkpoint_every=100), target)[1])
-    torch.cuda.synchronize()
-    net.sync()
-    net.close()
-
-
 _KERNEL_SOURCES = {
     "k_step_cluster": ["cluster.cu", "neuron_update.cuh", "device_math.cuh", "compaction.cuh", "snn_internal.cuh"],
     "k_neuron_step": ["neuron.cu", "neuron_update.cuh", "device_math.cuh", "compaction.cuh", "snn_internal.cuh"],
@@ -1032,21 +933,6 @@ def _sources_sha256(rels):
         with open(os.path.join(ROOT, rel), "rb") as f:
             h.update(f.read())
     return h.hexdigest()
-
-
-def record_traffic(kernel, nbytes, command):
-    path = os.path.join(ROOT, "profiles", "traffic.json")
-    try:
-        with open(path) as f:
-            table = json.load(f)
-    except (OSError, ValueError):
-        table = {}
-    rels = ["paper_1412_0595_gb300/csrc/" + x for x in _KERNEL_SOURCES[kernel]]
-    table[kernel] = {"bytes_per_launch": float(nbytes), "command": command, "sources": rels,
-                     "sources_sha256": _sources_sha256(rels)}
-    with open(path, "w") as f:
-        json.dump(table, f, indent=1, sort_keys=True)
-        f.write("\n")
 
 
 def _traffic(kernel):
@@ -1067,15 +953,7 @@ def _traffic(kernel):
 
 def main():
     a = _args()
-    if a.record_traffic:
-        record_traffic(*a.record_traffic)
-    elif a.profile:
-        run_profile(a)
-    elif a.sweep:
-        run_sweep(a)
-    elif a.tiled_crossover:
-        run_tiled_crossover(a)
-    elif a.impl == "reference":
+    if a.impl == "reference":
         run_reference(a)
     else:
         run_ours(a)

@@ -470,6 +470,13 @@ snn_status create_impl(const snn_pop_desc* pops, int32_t n_pops, const snn_proj_
         q.noise = (float)d.noise_sigma;
         q.bias = (float)d.bias;
         q.dt = (float)dt;
+        // channel 1 and the drive current stay zero unless a projection
+        // targets the channel or the population is driven (or a caller
+        // writes them, see snn_write_state / snn_load_state)
+        q.g1_live = 0;
+        for (int j = 0; j < n_projs; ++j)
+            if (projs[j].post == k && projs[j].channel == 1) q.g1_live = 1;
+        q.iext_live = q.thr_drive != 0ull ? 1 : 0;
     }
     CK(cudaMemcpyAsync(net->V, v0.data(), NT * sizeof(float), cudaMemcpyHostToDevice, s), "upload V0");
     for (int k = 0; k < n_pops; ++k) {
@@ -603,6 +610,26 @@ snn_status create_impl(const snn_pop_desc* pops, int32_t n_pops, const snn_proj_
 }
 
 }  // namespace
+
+namespace snn {
+
+// Marks channel 1 and the drive current of population `pop` (all
+// populations for pop < 0) as possibly nonzero, so the step kernels read and
+// write them from then on.
+cudaError_t mark_state_live(snn_net* net, int32_t pop, bool g1, bool iext, cudaStream_t s) {
+    static const int32_t one = 1;
+    const int32_t lo = pop < 0 ? 0 : pop, hi = pop < 0 ? (int32_t)net->pops.size() : pop + 1;
+    for (int32_t k = lo; k < hi; ++k) {
+        DevPop* d = net->d_pops + k;
+        cudaError_t e = cudaSuccess;
+        if (g1) e = cudaMemcpyAsync(&d->g1_live, &one, sizeof(int32_t), cudaMemcpyHostToDevice, s);
+        if (e == cudaSuccess && iext) e = cudaMemcpyAsync(&d->iext_live, &one, sizeof(int32_t), cudaMemcpyHostToDevice, s);
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+}
+
+}  // namespace snn
 
 // ===========================================================================
 // C-ABI
@@ -777,6 +804,8 @@ snn_status snn_write_state(snn_net* net, int32_t pop, int32_t field, const void*
         CK(cudaMemcpyAsync(field_base(net, field) + P.offset, src, need,
                            src_is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, s),
            "write field");
+    if (field == SNN_FIELD_G1 || field == SNN_FIELD_IEXT)
+        CK(mark_state_live(net, pop, field == SNN_FIELD_G1, field == SNN_FIELD_IEXT, s), "mark field live");
     CK(cudaStreamSynchronize(s), "synchronize");
     return SNN_OK;
 }

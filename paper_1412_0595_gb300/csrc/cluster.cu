@@ -57,19 +57,16 @@ struct ClusterProj {
     int32_t seg_off;           // compressed rows: first row in the shared segment cache, or -1
 };
 
-// Adds this CTA's share of the outgoing rows of spiking neuron `idx` (SoA
-// index) into the shared accumulators: part `sub` of `parts` (warps) of the
-// segment of each row whose post neurons lie in [base, base + per_cta), with
-// up to four synapses per lane in flight.
+// Adds this CTA's share of the outgoing rows of spiking neuron `local` of
+// population p (its outgoing projections are s_out_list[qb .. qe)) into the
+// shared accumulators: part `sub` of `parts` (warps) of the segment of each
+// row whose post neurons lie in [base, base + per_cta), with up to four
+// synapses per lane in flight.
 __device__ __forceinline__ void pull_row(const ClusterProj* s_proj, const int32_t* s_out_list,
-                                         const longlong2* s_seg, const int32_t* s_tile_pop,
-                                         const int32_t* s_tile_local, const int32_t* s_out_begin, int idx, int rank,
+                                         const longlong2* s_seg, int local, int qb, int qe, int rank,
                                          int n_ranks, int base, int per_cta, float* acc, int sub, int parts, int lane) {
-    const int tile = idx / kTile;
-    const int p = s_tile_pop[tile];
-    const int local = s_tile_local[tile] + (idx % kTile);
     const int stride = 32 * parts;
-    for (int qq = s_out_begin[p]; qq < s_out_begin[p + 1]; ++qq) {
+    for (int qq = qb; qq < qe; ++qq) {
         const ClusterProj& Q = s_proj[s_out_list[qq]];
         const float sc = Q.scale;
         float* mine = acc + Q.channel * per_cta + (Q.post_soa - base);
@@ -219,6 +216,21 @@ __global__ void __launch_bounds__(MAXT, 1) k_step_cluster(const PersistArgs A, i
         s_n_heavy = nh;
     }
 
+    __syncthreads();                                       // heavy words chosen
+    // Each lane keeps one heavy word (if any) with the population, the local
+    // index of its bit 0 and the outgoing projection range of its neurons:
+    // local of bit b = hlocal + 2 b.
+    const int n_heavy = s_n_heavy;
+    int hword = -1, hlocal = 0, hqb = 0, hqe = 0;
+    if (lane < n_heavy) {
+        hword = s_heavy[lane];
+        const int tl = hword / (kTile / 32);
+        const int hp = s_tile_pop[tl];
+        hlocal = s_tile_local[tl] + 64 * ((hword >> 1) & 3) + (hword & 1);
+        hqb = s_out_begin[hp];
+        hqe = s_out_begin[hp + 1];
+    }
+
     NeuronPair st[PPT];
     int pop_of[PPT], local_of[PPT];
     int2 n_spk[PPT];
@@ -295,40 +307,45 @@ __global__ void __launch_bounds__(MAXT, 1) k_step_cluster(const PersistArgs A, i
         if (k > 0) {
             const unsigned long long* prev = bits + (slot ^ 1) * n_words;
             const uint32_t tag = (uint32_t)(e64 - 1ull);
+            // heavy words first: one shared load per lane, issued before the
+            // light scan's loads so the latencies overlap
+            const uint32_t hm = hword >= 0 ? word_spikes(prev[hword], tag) : 0u;
             for (int w0 = warp * 32; w0 < n_words; w0 += T) {
                 const int wd = w0 + lane;
-                const uint32_t m = (wd < n_words && !s_tile_heavy[wd / (kTile / 32)]) ? word_spikes(prev[wd], tag) : 0u;
+                const unsigned long long wv = wd < n_words ? prev[wd] : 0ull;
+                const bool heavy = wd < n_words ? s_tile_heavy[wd / (kTile / 32)] != 0 : true;
+                const uint32_t m = heavy ? 0u : word_spikes(wv, tag);
                 unsigned nz = __ballot_sync(0xffffffffu, m != 0u);
                 while (nz) {
                     const int l = __ffs(nz) - 1;
                     nz &= nz - 1u;
                     uint32_t mm = __shfl_sync(0xffffffffu, m, l);
                     const int w = w0 + l;
+                    const int tl = w / (kTile / 32);
+                    const int p = s_tile_pop[tl];
+                    const int lb = s_tile_local[tl] + 64 * ((w >> 1) & 3) + (w & 1);
+                    const int qb = s_out_begin[p], qe = s_out_begin[p + 1];
                     while (mm) {
                         const int bit = __ffs(mm) - 1;
                         mm &= mm - 1u;
-                        pull_row(s_proj, s_out_list, s_seg, s_tile_pop, s_tile_local, s_out_begin,
-                                 64 * (w >> 1) + 2 * bit + (w & 1), rank, n_ranks, base, per_cta, acc_k, 0, 1, lane);
+                        pull_row(s_proj, s_out_list, s_seg, lb + 2 * bit, qb, qe, rank, n_ranks, base, per_cta, acc_k,
+                                 0, 1, lane);
                     }
                 }
             }
-            const int n_heavy = s_n_heavy;
-            if (n_heavy > 0) {
-                const int hw = lane < n_heavy ? s_heavy[lane] : 0;
-                const uint32_t hm = lane < n_heavy ? word_spikes(prev[hw], tag) : 0u;
-                unsigned nz = __ballot_sync(0xffffffffu, hm != 0u);
-                while (nz) {
-                    const int l = __ffs(nz) - 1;
-                    nz &= nz - 1u;
-                    uint32_t mm = __shfl_sync(0xffffffffu, hm, l);
-                    const int wd = __shfl_sync(0xffffffffu, hw, l);
-                    while (mm) {
-                        const int bit = __ffs(mm) - 1;
-                        mm &= mm - 1u;
-                        pull_row(s_proj, s_out_list, s_seg, s_tile_pop, s_tile_local, s_out_begin,
-                                 64 * (wd >> 1) + 2 * bit + (wd & 1), rank, n_ranks, base, per_cta, acc_k, warp,
-                                 n_warps, lane);
-                    }
+            unsigned nz = __ballot_sync(0xffffffffu, hm != 0u);
+            while (nz) {
+                const int l = __ffs(nz) - 1;
+                nz &= nz - 1u;
+                uint32_t mm = __shfl_sync(0xffffffffu, hm, l);
+                const int lb = __shfl_sync(0xffffffffu, hlocal, l);
+                const int qb = __shfl_sync(0xffffffffu, hqb, l);
+                const int qe = __shfl_sync(0xffffffffu, hqe, l);
+                while (mm) {
+                    const int bit = __ffs(mm) - 1;
+                    mm &= mm - 1u;
+                    pull_row(s_proj, s_out_list, s_seg, lb + 2 * bit, qb, qe, rank, n_ranks, base, per_cta, acc_k,
+                             warp, n_warps, lane);
                 }
             }
             __syncthreads();                                // events in acc_k

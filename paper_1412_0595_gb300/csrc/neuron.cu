@@ -1,9 +1,9 @@
 // Fused per-neuron step kernel (Sec. 2: HH neurons advanced at discrete time
 // steps) with spike compaction, for the two-kernel step of the plain engine.
 //
-// One CTA handles one tile of kTile neurons of one population, one neuron per
-// thread, state in structure-of-arrays FP32 (coalesced 128 B per warp per
-// array).  Tiles take a ticket from a monotone counter; the ticket gives the
+// One CTA handles one tile of kTile neurons of one population, two neighbour
+// neurons per thread, state in structure-of-arrays FP32 (coalesced 256 B per
+// warp per array).  Tiles take a ticket from a monotone counter; the ticket gives the
 // step epoch (ticket / num_tiles), which drives the counter-based random
 // numbers and the parity of the double-buffered list lengths, so nothing is
 // reset between steps and no tile waits for another.
@@ -14,8 +14,13 @@
 
 namespace snn {
 
-__global__ void __launch_bounds__(kTile, 6) k_neuron_step(const NeuronArgs a) {
-    __shared__ int s_off[kTile / 32];
+// One CTA of kTile / 2 threads per tile; thread t holds the tile's neurons
+// 2 t and 2 t + 1 (8-byte loads and stores of each state array) and steps
+// them together (FP32x2 arithmetic for HH populations).  Channel 1 and the
+// drive current are read and written only for populations where they can be
+// nonzero.
+__global__ void __launch_bounds__(kTile / 2, 6) k_neuron_step(const NeuronArgs a) {
+    __shared__ int s_off[kTile / 64];
     __shared__ int s_total, s_base;
     __shared__ uint32_t s_t;
     __shared__ int s_slot;
@@ -46,33 +51,64 @@ __global__ void __launch_bounds__(kTile, 6) k_neuron_step(const NeuronArgs a) {
             cur_pop = p;
         }
         const DevPop& P = s_pop;
-        const int local = (tile - P.first_tile) * kTile + (int)threadIdx.x;
-        const bool active = local < P.n;
-        const int idx = P.offset + local;
+        const int local = (tile - P.first_tile) * kTile + 2 * (int)threadIdx.x;
+        const unsigned live = (local < P.n ? 1u : 0u) | (local + 1 < P.n ? 2u : 0u);
+        const int idx = P.offset + local;                    // even: 8-byte aligned pairs
         if (tile == P.first_tile && threadIdx.x == 0) P.nspk[slot ^ 1] = 0;   // next step's count
 
-        bool spike = false, is_nan = false;
-        if (active) {
-            NeuronState s{};
-            if (P.kind != SNN_POP_SOURCE)
-                s = NeuronState{a.V[idx], a.m[idx], a.h[idx], a.n[idx], a.g0[idx], a.g1[idx], a.iext[idx]};
-            float isyn;
-            spike = neuron_step(P, key, t, local, a.hs, a.n_sub, s, &isyn);
-            if (P.kind != SNN_POP_SOURCE) {
-                is_nan = isnan(s.V);
-                a.V[idx] = s.V; a.m[idx] = s.m; a.h[idx] = s.h; a.n[idx] = s.n;
-                a.g0[idx] = s.g0; a.g1[idx] = s.g1; a.iext[idx] = s.ie;
-                if (a.isyn_rec) a.isyn_rec[idx] = isyn;
+        unsigned spike = 0u, is_nan = 0u;
+        if (live) {
+            NeuronPair s{};
+            const bool hh_like = P.kind != SNN_POP_SOURCE;
+            if (hh_like) {
+                s.V = *reinterpret_cast<const float2*>(a.V + idx);
+                s.m = *reinterpret_cast<const float2*>(a.m + idx);
+                s.h = *reinterpret_cast<const float2*>(a.h + idx);
+                s.n = *reinterpret_cast<const float2*>(a.n + idx);
+                s.g0 = *reinterpret_cast<const float2*>(a.g0 + idx);
+                if (P.g1_live) s.g1 = *reinterpret_cast<const float2*>(a.g1 + idx);
+                if (P.iext_live) s.ie = *reinterpret_cast<const float2*>(a.iext + idx);
+            }
+            float2 isyn;
+            spike = neuron_step_pair(P, key, t, local, a.hs, a.n_sub, s, &isyn) & live;
+            if (hh_like) {
+                is_nan = (isnan(s.V.x) ? 1u : 0u) | (isnan(s.V.y) ? 2u : 0u);
+                is_nan &= live;
+                if (live == 3u) {
+                    *reinterpret_cast<float2*>(a.V + idx) = s.V;
+                    *reinterpret_cast<float2*>(a.m + idx) = s.m;
+                    *reinterpret_cast<float2*>(a.h + idx) = s.h;
+                    *reinterpret_cast<float2*>(a.n + idx) = s.n;
+                    *reinterpret_cast<float2*>(a.g0 + idx) = s.g0;
+                    if (P.g1_live) *reinterpret_cast<float2*>(a.g1 + idx) = s.g1;
+                    if (P.iext_live) *reinterpret_cast<float2*>(a.iext + idx) = s.ie;
+                    if (a.isyn_rec) *reinterpret_cast<float2*>(a.isyn_rec + idx) = isyn;
+                } else {                                     // the second half is a padding slot
+                    a.V[idx] = s.V.x; a.m[idx] = s.m.x; a.h[idx] = s.h.x; a.n[idx] = s.n.x;
+                    a.g0[idx] = s.g0.x;
+                    if (P.g1_live) a.g1[idx] = s.g1.x;
+                    if (P.iext_live) a.iext[idx] = s.ie.x;
+                    if (a.isyn_rec) a.isyn_rec[idx] = isyn.x;
+                }
             }
         }
 
-        const unsigned ballot = __ballot_sync(0xffffffffu, spike);
-        const unsigned nan_ballot = __ballot_sync(0xffffffffu, is_nan);
-        if (lane == 0 && nan_ballot) atomicAdd(P.nan_count, (unsigned long long)__popc(nan_ballot));
-        const int total = tile_claim(spike, ballot, s_off, &s_total, &s_base, P.nspk + slot);
+        const unsigned b0 = __ballot_sync(0xffffffffu, spike & 1u);
+        const unsigned b1 = __ballot_sync(0xffffffffu, spike & 2u);
+        const int nans = __popc(__ballot_sync(0xffffffffu, is_nan & 1u)) + __popc(__ballot_sync(0xffffffffu, is_nan & 2u));
+        if (lane == 0 && nans) atomicAdd(P.nan_count, (unsigned long long)nans);
+        const int total = tile_claim_pair(spike != 0u, b0, b1, s_off, &s_total, &s_base, P.nspk + slot);
         if (spike) {
-            P.spk[s_base + s_off[warp] + __popc(ballot & ((1u << lane) - 1u))] = local;
-            P.neuron_spikes[local] += 1;
+            const unsigned lt = (1u << lane) - 1u;
+            const int pos = s_base + s_off[warp] + __popc(b0 & lt) + __popc(b1 & lt);
+            if (spike & 1u) {
+                P.spk[pos] = local;
+                P.neuron_spikes[local] += 1;
+            }
+            if (spike & 2u) {
+                P.spk[pos + (int)(spike & 1u)] = local + 1;
+                P.neuron_spikes[local + 1] += 1;
+            }
         }
         if (threadIdx.x == 0 && total) atomicAdd(P.spike_count, (unsigned long long)total);
     }
@@ -110,7 +146,7 @@ static int neuron_grid_cap() {
     if (cap[dev] == 0) {
         int sms = 0, per_sm = 0;
         if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return 0;
-        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_neuron_step, kTile, 0) != cudaSuccess) return 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_neuron_step, kTile / 2, 0) != cudaSuccess) return 0;
         cap[dev] = std::max(1, sms * per_sm);
     }
     return cap[dev];
@@ -120,7 +156,7 @@ cudaError_t launch_neuron_step(const NeuronArgs& a, cudaStream_t s) {
     if (a.num_tiles == 0) return cudaSuccess;
     const int cap = neuron_grid_cap();
     if (cap == 0) return cudaErrorUnknown;
-    k_neuron_step<<<std::min(a.num_tiles, cap), kTile, 0, s>>>(a);
+    k_neuron_step<<<std::min(a.num_tiles, cap), kTile / 2, 0, s>>>(a);
     return cudaGetLastError();
 }
 

@@ -53,6 +53,8 @@ struct DevPop {
     float izh[8];                  // Izhikevich: a0, a1, b0, b1, c0, c2, d0, d2
     float noise, bias;             // Izhikevich input: bias + noise * z
     float dt;                      // step length (ms), for u
+    int32_t g1_live;               // channel 1 can be nonzero (a projection targets it, or it was written)
+    int32_t iext_live;             // the drive current can be nonzero (driven, or written)
 };
 
 struct DevProj {
@@ -372,6 +374,7 @@ cudaError_t persistent_capacity(int sm_count, int* blocks);
 // Compressed rows whose segment in a CTA's slice the cluster engine keeps in
 // shared memory (16 bytes each).
 constexpr int kClusterSegCacheRows = 2048;
+cudaError_t mark_state_live(snn_net* net, int32_t pop, bool g1, bool iext, cudaStream_t s);
 int cluster_plan(int n_total, int n_pops, int n_projs, int* per_cta);
 cudaError_t cluster_supported(int cl, int per_cta, int num_tiles, int seg_rows, bool* ok);
 cudaError_t launch_cluster_splits(const int64_t* row_ptr, const int32_t* col, int32_t n_pre, int32_t post_soa,

@@ -218,6 +218,9 @@ snn_status snn_save_state(snn_net* net, void* dst, size_t bytes, int32_t dst_is_
 
 snn_status snn_load_state(snn_net* net, const void* src, size_t bytes, int32_t src_is_device, void* stream) {
     if (!net || !src) return fail(SNN_ERR_INVALID_ARG, "bad argument");
+    // a snapshot may hold channel-1 conductances and drive currents written
+    // into the network it came from: the step kernels process them from now on
+    CK(mark_state_live(net, -1, true, true, (cudaStream_t)stream), "mark state live");
     return copy_state(net, const_cast<void*>(src), bytes, src_is_device, false, (cudaStream_t)stream);
 }
 

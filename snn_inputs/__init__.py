@@ -141,15 +141,17 @@ def config_sweep(n_mid, p, layout="csr", steps=1000):
 
 
 def config_batched(n_instances=512, steps=5000, seed=SEED, n_lo=1_000, n_hi=50_000,
-                   c_lo=0.1, c_hi=10.0):
+                   c_lo=0.1, c_hi=10.0, weight_hi=0.05):
     """n_instances copies of the small workload with middle sizes and
     conductance factors drawn log-uniform (the paper's sweep over scaling
-    factors, Sec. 2 / Fig. 1)."""
+    factors, Sec. 2 / Fig. 1).  weight_hi is the upper end of the uniform
+    weights (nS): 0.05 as in the small workload (subthreshold with the
+    1/(p N_pre) scaling), or larger for a forced-activity variant."""
     rng = np.random.default_rng([seed, _BATCH])
     sizes = np.exp(rng.uniform(math.log(n_lo), math.log(n_hi), n_instances)).astype(np.int64)
     scales = np.exp(rng.uniform(math.log(c_lo), math.log(c_hi), n_instances))
     return [config_small(steps=steps, n_hh=int(sizes[b]), user_scale=float(scales[b]), seed=seed,
-                         instance=b) for b in range(n_instances)]
+                         instance=b, weight_hi=weight_hi) for b in range(n_instances)]
 
 
 # Graded-synapse (differentiable) workload
