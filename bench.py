@@ -137,13 +137,15 @@ class Clocks:
                 "reasons": reasons, "samples": len(rows)}
 
 
-def _forced_propagation(snn, torch, dev, n_mid, p, layout, reps=7, flush=None):
+def _forced_propagation(snn, torch, dev, n_mid, p, layout, reps=7, flush=None, tiled=None):
     """Forced activity: all 100 input rows spike; times the production
     propagation kernel alone (L2 flushed before each launch) and returns
-    algorithmic bytes / time."""
+    algorithmic bytes / time.  tiled: SNN_OPT_TILED (None: the library's choice)."""
     spec = I.net([I.source_pop(100, 0.0), I.hh_pop(n_mid)],
                  [I.proj(0, 1, layout, p, ("lognormal", -3.0, 0.5))], dt=0.1, steps=1)
     net = snn.Network.from_spec(spec, device=dev)
+    if tiled is not None:
+        net.set_option("tiled", tiled)
     rows = 100
     net.debug_propagate(0, np.arange(rows, dtype=np.int32))
     nnz = net.nnz(0)
@@ -253,6 +255,39 @@ def _plain_forward_runs(net, steps, n=6):
     for _ in range(n):
         net.reset()
         net.step(steps)
+
+
+def _shared_dense_batch(snn, torch, dev, n_inst=512, n=1024, rate_hz=500.0, steps=1000):
+    """Batched instances sharing one dense projection on the time-step path
+    (snn_add_shared_dense): n_inst instances of n Poisson sources (rate_hz,
+    5 % spiking per 0.1 ms step at 500 Hz) -> n HH neurons through one shared
+    n x n weight matrix with per-instance scales; steps/s with the delivery on
+    the CUDA cores, on the tensor cores and chosen by spike density."""
+    specs = [I.net([I.source_pop(n, rate_hz), I.hh_pop(n)], [], dt=0.1, steps=1, instance=b) for b in range(n_inst)]
+    rng = np.random.default_rng([I.SEED, 11])
+    W = torch.from_numpy(rng.uniform(0.0, 0.03, (n, n)).astype(np.float32))
+    scales = np.exp(rng.uniform(np.log(0.1), np.log(10.0), n_inst))
+    net = snn.Network.from_specs(specs, device=dev)
+    net.add_shared_dense(0, 1, W, scales)
+    s = torch.cuda.current_stream()
+    out = {"workload": f"{n_inst} instances of {n} Poisson sources ({rate_hz:g} Hz) -> {n} HH, one shared {n} x {n} "
+                       f"dense projection, {steps} steps", "neurons": 2 * n * n_inst}
+    for name, engine in (("cuda_cores", 0), ("tensor_cores", 1), ("by_density", 2)):
+        net.set_option("shared_dense", engine)
+        net.reset()
+        net.step(100)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(s)
+        net.step(steps)
+        e1.record(s)
+        e1.synchronize()
+        t = e0.elapsed_time(e1) * 1e-3
+        out[name + "_steps_per_s"] = steps / t
+        out[name + "_us_per_step"] = t / steps * 1e6
+    out["tensor_over_cuda_cores"] = out["tensor_cores_steps_per_s"] / out["cuda_cores_steps_per_s"]
+    out["spike_density"] = sum(net.counters(net.pop_offsets[b])[0] for b in range(n_inst)) / (n_inst * n * (steps + 100))
+    net.close()
+    return out
 
 
 def _largest_sweep_network(snn, torch, dev, flush, steps=1000):
@@ -726,6 +761,20 @@ def run_ours(a):
             sms = net.cluster_size
             roof["sms_used"] = sms
             roof["frac_of_used_sms"] = ach / (fp32_peak * sms / SM_COUNT)
+            # the special-function (XU) pipe: 16 lanes per clock per SM, i.e.
+            # one warp instruction per 2 clocks; executed XU warp instructions
+            # per launch from the ncu table (null when the kernel changed since)
+            xu = _counter(kname, "xu_warp_inst_per_launch", "xu_sources_sha256")
+            xu_peak = SM_COUNT * sm_mhz * 1e6 * 16 / 32                 # warp instructions / s
+            if xu is not None:
+                xu_rate = xu / (t_persist * 1e-3)
+                roof["sfu"] = {"xu_warp_inst_per_launch": xu, "neuron_steps_per_launch": PERSIST * n_hh,
+                               "xu_lane_ops_per_neuron_step": 32.0 * xu / (PERSIST * n_hh),
+                               "achieved_warp_inst_per_s": xu_rate, "peak_warp_inst_per_s": xu_peak,
+                               "frac": xu_rate / xu_peak, "frac_of_used_sms": xu_rate / (xu_peak * sms / SM_COUNT),
+                               "peak_source": "152 SMs x 16 XU lanes per clock x max SM clock"}
+            else:
+                roof["sfu"] = None
         other[kname + "_us_per_step"] = 1e3 * t_persist / PERSIST
     elif t_neuron >= t_prop:
         roof = {"kernel": "k_neuron_step", "bound": "alu", "achieved": neuron_tflops, "peak": fp32_peak,
@@ -769,6 +818,9 @@ def run_ours(a):
     largest = None
     if not a.no_scale_point and rank == 0:
         largest = _largest_sweep_network(snn, torch, dev, flush)
+    shared_dense = None
+    if not a.no_dense_batch and rank == 0:
+        shared_dense = _shared_dense_batch(snn, torch, dev)
     differentiable = None
     if not a.no_graded and rank == 0:
         differentiable = _differentiable(snn, torch, dev)
@@ -810,6 +862,7 @@ def run_ours(a):
                 "batched": batched,
                 "batched_forced_activity": batched_forced,
                 "largest_sweep_network": largest,
+                "shared_dense_batch": shared_dense,
                 "differentiable": differentiable,
                 "dense_batch": dense_batch,
                 "differentiable_dense": graded_dense,
@@ -933,6 +986,21 @@ def _sources_sha256(rels):
         with open(os.path.join(ROOT, rel), "rb") as f:
             h.update(f.read())
     return h.hexdigest()
+
+
+def _counter(kernel, key, hash_key):
+    """A per-launch ncu counter of `kernel` from profiles/traffic.json, or
+    None when the kernel's sources changed since it was taken."""
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    try:
+        with open(path) as f:
+            table = json.load(f)
+    except (OSError, ValueError):
+        return None
+    row = table.get(kernel)
+    if not row or key not in row:
+        return None
+    return row[key] if _sources_sha256(row["sources"]) == row.get(hash_key) else None
 
 
 def _traffic(kernel):

@@ -26,7 +26,8 @@ from bench import (BYTES_PER_EVENT, ROOT, _KERNEL_SOURCES, _flush_buffers, _flus
 def run_tiled_crossover(a):
     """Forced activity (100 spiking rows, caches flushed before each of 7
     launches, median): the row kernel (SNN_OPT_TILED 0) against the
-    post-tiled kernel (1) at several post-population sizes and densities;
+    post-tiled kernels (1 bulk copies, 3 segments) at several post-population
+    sizes and densities;
     fraction of the measured copy bandwidth at 8 B per synapse."""
     import torch
 
@@ -45,7 +46,7 @@ def run_tiled_crossover(a):
             net.debug_propagate(0, rows)
             nnz = net.nnz(0)
             line = {"n_mid": n_mid, "p": p, "synapses": nnz}
-            for t in (0, 1):
+            for t in (0, 1, 3):
                 net.set_option("tiled", t)
                 net.debug_propagate(0, rows)
                 s = torch.cuda.current_stream()
@@ -60,7 +61,7 @@ def run_tiled_crossover(a):
                     times.append(e0.elapsed_time(e1))
                 net.sync()
                 us = statistics.median(times) * 1e3
-                name = "row" if t == 0 else "tiled"
+                name = {0: "row", 1: "tiled", 3: "segments"}[t]
                 line[name + "_us"] = us
                 line[name + "_frac_hbm"] = nnz * BYTES_PER_EVENT / (us * 1e-6) / 1e9 / hbm
             print(json.dumps(line), flush=True)
@@ -116,11 +117,12 @@ def run_profile(a):
         net.set_option("persist_steps", 1000)
         for _ in range(3):
             net.launch_phase(4)
-    elif a.profile in ("tiled", "dense", "csr_mid"):
+    elif a.profile in ("tiled", "dense", "csr_mid", "seg_mid", "seg_dense"):
         flush = _flush_buffers(torch, dev)
-        p = 0.05 if a.profile == "csr_mid" else 0.5
+        p = 0.05 if a.profile in ("csr_mid", "seg_mid") else 0.2 if a.profile == "seg_dense" else 0.5
+        tiled = 3 if a.profile.startswith("seg") else None
         _forced_propagation(snn, torch, dev, 1_000_000, p, "dense" if a.profile == "dense" else "csr", reps=3,
-                            flush=flush)
+                            flush=flush, tiled=tiled)
         return
     elif a.profile == "dense_batch":
         rng = np.random.default_rng(11)
@@ -206,7 +208,7 @@ def record_xu(kernel, xu_inst, neuron_steps, command):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--profile", choices=["cluster", "tiled", "dense", "neuron", "graded", "dense_batch", "dense_grad",
-                                          "graded_dense", "csr_mid"])
+                                          "graded_dense", "csr_mid", "seg_mid", "seg_dense"])
     ap.add_argument("--sweep", action="store_true")
     ap.add_argument("--tiled-crossover", action="store_true")
     ap.add_argument("--record-traffic", nargs=3, metavar=("KERNEL", "BYTES", "COMMAND"))

@@ -90,13 +90,17 @@ enum {
                                   recovers the network */
     SNN_OPT_CLUSTER_CTAS = 9,  /* read only (snn_get_option): CTAs of the cluster engine's plan,
                                   0 when the network does not fit one cluster */
+    SNN_OPT_SHARED_DENSE = 11, /* delivery of dense projections shared by a batch's instances
+                                  (snn_add_shared_dense): 0 CUDA cores, 1 tensor cores, 2 chosen
+                                  on the device each step (default: tensor cores when at least
+                                  3 % of the pre neurons of all instances spiked) */
     SNN_OPT_DENSE_GRAD = 10,   /* weight gradient of dense graded projections in snn_backward:
                                   0 CUDA cores (FP32 products), 1 tensor cores (default; three
                                   BF16 parts of each operand, six products, FP32 accumulation) */
     SNN_OPT_TILED = 7          /* compressed-row propagation of the plain engine: 0 one warp per
                                   row chunk with global atomics, 1 post-tiled through shared
-                                  memory, 2 choose (default: post-tiled when a row has
-                                  >= 256 synapses per 2048-post tile, over >= 16384 posts) */
+                                  memory by bulk copies, 2 choose (default), 3 post-tiled
+                                  segments streamed by warps into shared memory */
 };
 
 /* A population.  kind SNN_POP_HH: Traub-Miles HH neurons with the given
@@ -201,6 +205,27 @@ typedef struct snn_net_desc {
  * populations and 4096 projections in total; errors as snn_create_network. */
 snn_status snn_create_batch(const snn_net_desc* nets, int32_t n_instances, double dt, int32_t n_substeps,
                             uint64_t seed, const snn_allocator* alloc, void* stream, snn_net** out);
+
+/* Adds a dense projection (Eq. 2 storage) that every instance of a batch
+ * shares: instance b's population first_post + b * pops_per_instance
+ * receives, on conductance channel `channel`, s_b * W[i][j] for each spike i
+ * of its population first_pre + b * pops_per_instance, with one step of
+ * delay like every projection.  W is n_pre x n_post row-major FP32 (host or
+ * device, copied; n_pre / n_post the populations' sizes, the same in every
+ * instance), s_b = (k1 / (k2 + nConn) + k3) * user_scale[b] (Sec. 5.1; nConn
+ * = n_conn if > 0, else density * n_pre; user_scale: host, n_instances
+ * doubles).  Each step delivers all instances at once, as the product of the
+ * step's 0/1 spike matrix (instances x n_pre) with W: on the tensor cores
+ * (W split into three BF16 parts, FP32 accumulation, as snn_dense_batch) or
+ * on the CUDA cores, see SNN_OPT_SHARED_DENSE.  The instances' post
+ * populations must lie evenly spaced in the batch (instances of identical
+ * shape): SNN_ERR_INVALID_ARG otherwise; SNN_ERR_GSCALE for nConn + k2 <= 0.
+ * A network with shared projections steps in the plain engine.  Synchronises
+ * `stream`. */
+snn_status snn_add_shared_dense(snn_net* net, int32_t first_pre, int32_t first_post, int32_t pops_per_instance,
+                                int32_t n_instances, const float* w, int32_t w_on_device, int32_t channel, double k1,
+                                double k2, double k3, double density, double n_conn, const double* user_scale,
+                                void* stream);
 
 /* Releases the network and all its device memory (synchronises its streams). */
 snn_status snn_destroy(snn_net* net);

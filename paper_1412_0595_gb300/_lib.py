@@ -21,7 +21,8 @@ SYN_EXP, SYN_GRADED = 0, 1
 FIELD = {"V": 0, "m": 1, "h": 2, "n": 3, "g0": 4, "g1": 5, "iext": 6, "isyn": 7, "spikes": 8, "nspk": 9,
          "spike_count": 10, "nan_count": 11, "neuron_spikes": 12}
 OPT = {"record_isyn": 0, "graph_steps": 1, "prop_blocks": 2, "chunk": 3, "spin_limit": 4, "engine": 5,
-       "persist_steps": 6, "tiled": 7, "test_barrier_extra": 8, "cluster_ctas": 9, "dense_grad": 10}
+       "persist_steps": 6, "tiled": 7, "test_barrier_extra": 8, "cluster_ctas": 9, "dense_grad": 10,
+       "shared_dense": 11}
 
 
 class PopDesc(C.Structure):
@@ -77,6 +78,7 @@ def _load():
     sig = {
         "snn_create_network": ([P(PopDesc), i32, P(ProjDesc), i32, dbl, i32, u64, u32, P(Allocator), vp, P(vp)]),
         "snn_create_batch": [P(NetDesc), i32, dbl, i32, u64, P(Allocator), vp, P(vp)],
+        "snn_add_shared_dense": [vp, i32, i32, i32, i32, vp, i32, i32, dbl, dbl, dbl, dbl, dbl, P(dbl), vp],
         "snn_destroy": [vp],
         "snn_step": [vp, i64, vp],
         "snn_sync": [vp, vp],

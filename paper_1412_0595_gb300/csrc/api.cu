@@ -45,6 +45,61 @@ void Alloc::put(void* p) {
 
 }  // namespace snn
 
+namespace snn {
+
+// The step's spike lists of the pre populations of a shared dense projection,
+// gathered as one list per instance (spk_off[B + 1], spk) for the batched
+// delivery: one CTA scans the list lengths, then its warps copy the lists.
+__global__ void __launch_bounds__(1024) k_shared_spike_lists(const int32_t* pre_pop, const int32_t* pre_off, int32_t B,
+                                                             const int32_t* nspk, const int32_t* spk_all,
+                                                             const unsigned long long* ticket, int32_t num_tiles,
+                                                             int32_t* spk_off, int32_t* spk_out) {
+    __shared__ int32_t s_w[32];
+    __shared__ int32_t s_run;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    // list-length slot of the step whose spikes are delivered
+    const int slot = (int)((*ticket / (unsigned long long)num_tiles + 1ull) & 1ull);
+    if (threadIdx.x == 0) s_run = 0;
+    __syncthreads();
+    for (int b0 = 0; b0 < B; b0 += 1024) {
+        const int b = b0 + (int)threadIdx.x;
+        const int c = b < B ? nspk[2 * pre_pop[b] + slot] : 0;
+        int incl = c;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int y = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= o) incl += y;
+        }
+        if (lane == 31) s_w[warp] = incl;
+        __syncthreads();
+        if (warp == 0) {
+            const int v = s_w[lane];
+            int wi = v;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const int y = __shfl_up_sync(0xffffffffu, wi, o);
+                if (lane >= o) wi += y;
+            }
+            s_w[lane] = wi - v;
+        }
+        __syncthreads();
+        const int excl = s_run + s_w[warp] + incl - c;
+        if (b < B) spk_off[b] = excl;
+        __syncthreads();
+        if (threadIdx.x == 1023) s_run = excl + c;
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) spk_off[B] = s_run;
+    __syncthreads();                                   // the offsets are visible to the whole CTA
+    for (int b = warp; b < B; b += 32) {
+        const int o = spk_off[b], c = spk_off[b + 1] - o;
+        const int32_t* src = spk_all + pre_off[b];
+        for (int j = lane; j < c; j += 32) spk_out[o + j] = src[j];
+    }
+}
+
+}  // namespace snn
+
 using namespace snn;
 
 namespace {
@@ -197,23 +252,31 @@ int prop_blocks(snn_net* net) { return net->prop_blocks > 0 ? net->prop_blocks :
 // Post-tiled propagation pays off when a row has many synapses in each post
 // tile and the post population spans at least eight tiles; below that the
 // row kernel's global reductions stay in L2 and cost less than the staging.
-// Measured crossover (100 spiking rows, caches flushed): about 200 synapses
-// per 2048-post tile for 300,000 posts and more (p = 0.1: 76 against 94 us at
-// 1,000,000 posts), 256 for smaller post populations (p = 0.1 at 100,000
-// posts: 22.5 against 20.5 us, the row kernel still ahead).
-bool want_tiled(const snn_net* net, const ProjHost& P) {
-    if (P.d.layout != SNN_LAYOUT_CSR || net->tiled == 0) return false;
-    if (net->tiled == 1) return true;
+// Measured crossovers (100 spiking rows, caches flushed; bench_profiles.py
+// --tiled-crossover), by synapses of a row per 2048-post tile: on 524,288
+// posts and more, segments from 40 (p = 0.02 .. 0.2 at 1,000,000 posts:
+// 22-70 us against 27-80 us for the better of the other two), bulk-copied
+// pieces from 800 (p = 0.5: 90 against 147 us); on 131,072 to 524,287 posts
+// segments from 150 and pieces from 300; below, pieces from 256.
+// Mode of a compressed-row projection's propagation in the plain engine:
+// 0 row kernel, 1 post-tiled through bulk copies, 2 post-tiled segments
+// streamed by warps into the shared accumulator.
+int32_t tiled_mode(const snn_net* net, const ProjHost& P) {
+    if (P.d.layout != SNN_LAYOUT_CSR || net->tiled == 0) return 0;
+    if (net->tiled == 1) return 1;
+    if (net->tiled == 3) return 2;
     const int32_t n_pre = net->pops[P.d.pre].d.n, n_post = net->pops[P.d.post].d.n;
-    if (n_post < 8 * kPostTile || n_pre == 0) return false;
+    if (n_post < 8 * kPostTile || n_pre == 0) return 0;
     const double per_tile = (double)P.nnz / n_pre * kPostTile / n_post;
-    return per_tile >= (n_post >= 64 * kPostTile ? 192.0 : 256.0);
+    if (n_post >= 256 * kPostTile) return per_tile >= 800.0 ? 1 : per_tile >= 40.0 ? 2 : 0;
+    if (n_post >= 64 * kPostTile) return per_tile >= 300.0 ? 1 : per_tile >= 150.0 ? 2 : 0;
+    return per_tile >= 256.0 ? 1 : 0;
 }
 
 snn_status setup_tiled(snn_net* net, cudaStream_t s) {
     for (auto& P : net->projs) {
-        P.mode = want_tiled(net, P) ? 1 : 0;
-        if (P.mode == 1 && !P.split) {
+        P.mode = tiled_mode(net, P);
+        if (P.mode != 0 && !P.split) {
             const int32_t n_pre = net->pops[P.d.pre].d.n, n_post = net->pops[P.d.post].d.n;
             const int32_t nt = (n_post + kPostTile - 1) / kPostTile;
             TRY(dalloc(net, &P.split, (size_t)n_pre * (nt + 1) + 1, "row splits"));
@@ -232,6 +295,8 @@ cudaError_t launch_projections(snn_net* net, const DevProj* dev, const ProjHost*
         if (host[q]->mode == 1)
             e = launch_propagate_tiled(dev + q, kPostTile, net->ticket, std::max(1, net->num_tiles), net->sm_count,
                                        net->error, net->spin_limit, s);
+        else if (host[q]->mode == 2)
+            e = launch_propagate_seg(dev + q, net->ticket, std::max(1, net->num_tiles), net->sm_count, s);
     return e;
 }
 
@@ -243,11 +308,12 @@ cudaError_t launch_all_projections(snn_net* net, cudaStream_t s) {
 }
 
 bool use_cluster(const snn_net* net) {
-    if (net->cluster_size == 0) return false;
+    if (net->cluster_size == 0 || !net->shared.empty()) return false;
     return net->engine == 3 || net->engine == 2;
 }
 
 bool use_persistent(const snn_net* net) {
+    if (!net->shared.empty()) return false;      // shared dense projections: the plain engine's step
     if (net->engine == 1) return net->persist_grid > 0;
     if (net->engine != 2) return false;
     return net->num_tiles > 0 && net->num_tiles <= net->persist_grid;   // one resident CTA per tile
@@ -279,10 +345,26 @@ cudaError_t enqueue_persistent(snn_net* net, int64_t n_steps, cudaStream_t s) {
     return cudaSuccess;
 }
 
+cudaError_t launch_shared_dense(snn_net* net, cudaStream_t s) {
+    for (const SharedDense& d : net->shared) {
+        k_shared_spike_lists<<<1, 1024, 0, s>>>(d.pre_pop, d.pre_off, d.B, net->nspk, net->spk, net->ticket,
+                                                std::max(1, net->num_tiles), d.spk_off, d.spk);
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+        const int64_t thr = (int64_t)std::ceil(net->shared_density * (double)d.B * d.n_pre);
+        e = dense_batch_launch(d.h, d.B, d.spk_off, d.spk, d.scale, d.G, d.ldg, net->shared_engine,
+                               std::max<int64_t>(1, thr), s);
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+}
+
 cudaError_t enqueue_step(snn_net* net, cudaStream_t s) {
     cudaError_t e = launch_neuron_step(neuron_args(net), s);
     if (e != cudaSuccess) return e;
-    return launch_all_projections(net, s);
+    e = launch_all_projections(net, s);
+    if (e != cudaSuccess || net->shared.empty()) return e;
+    return launch_shared_dense(net, s);
 }
 
 void drop_graph(snn_net* net) {
@@ -696,6 +778,8 @@ snn_status snn_create_batch(const snn_net_desc* nets, int32_t n_instances, doubl
 snn_status snn_destroy(snn_net* net) {
     if (!net) return SNN_OK;
     cudaDeviceSynchronize();
+    for (SharedDense& d : net->shared) snn_dense_batch_destroy(d.h);
+    net->shared.clear();
     release(net);
     delete net;
     return SNN_OK;
@@ -841,6 +925,7 @@ snn_status snn_get_option(const snn_net* net, int32_t option, int64_t* value) {
     case SNN_OPT_TEST_BARRIER_EXTRA: *value = net->barrier_extra; break;
     case SNN_OPT_CLUSTER_CTAS: *value = net->cluster_size; break;
     case SNN_OPT_DENSE_GRAD: *value = net->dense_grad; break;
+    case SNN_OPT_SHARED_DENSE: *value = net->shared_engine; break;
     default: return fail(SNN_ERR_INVALID_ARG, "unknown option");
     }
     return SNN_OK;
@@ -878,7 +963,7 @@ snn_status snn_set_option(snn_net* net, int32_t option, int64_t value) {
         net->barrier_extra = (int32_t)value;
         break;
     case SNN_OPT_TILED:
-        if (value < 0 || value > 2) return fail(SNN_ERR_INVALID_ARG, "tiled: 0 off, 1 on, 2 choose");
+        if (value < 0 || value > 3) return fail(SNN_ERR_INVALID_ARG, "tiled: 0 off, 1 bulk copies, 2 choose, 3 segments");
         net->tiled = (int32_t)value;
         TRY(setup_tiled(net, nullptr));
         break;
@@ -889,6 +974,11 @@ snn_status snn_set_option(snn_net* net, int32_t option, int64_t value) {
     case SNN_OPT_DENSE_GRAD:
         if (value < 0 || value > 1) return fail(SNN_ERR_INVALID_ARG, "dense gradient: 0 CUDA cores, 1 tensor cores");
         net->dense_grad = (int32_t)value;
+        break;
+    case SNN_OPT_SHARED_DENSE:
+        if (value < 0 || value > 2) return fail(SNN_ERR_INVALID_ARG, "shared dense: 0 CUDA cores, 1 tensor cores, 2 by density");
+        net->shared_engine = (int32_t)value;
+        drop_graph(net);
         break;
     default: return fail(SNN_ERR_INVALID_ARG, "unknown option");
     }
@@ -918,7 +1008,15 @@ snn_status snn_synaptic_events(snn_net* net, int64_t* events, void* stream) {
     unsigned long long v = 0;
     CK(launch_count_events(net->d_projs, (int)net->projs.size(), net->d_events, s), "count events");
     CK(cudaMemcpyAsync(&v, net->d_events, sizeof(v), cudaMemcpyDeviceToHost, s), "read events");
+    std::vector<unsigned long long> cnt;
+    if (!net->shared.empty()) {                    // shared dense rows: spikes of the pre populations x n_post
+        cnt.resize(2 * net->pops.size());
+        CK(cudaMemcpyAsync(cnt.data(), net->counters, sizeof(unsigned long long) * cnt.size(), cudaMemcpyDeviceToHost, s),
+           "read counters");
+    }
     CK(cudaStreamSynchronize(s), "synchronize");
+    for (const SharedDense& d : net->shared)
+        for (int32_t p : d.pre_pops) v += cnt[2 * (size_t)p] * (unsigned long long)d.n_post;
     *events = (int64_t)v;
     return SNN_OK;
 }
@@ -1096,6 +1194,78 @@ snn_status snn_csr_bernoulli_fill(uint64_t seed, uint32_t tag, int64_t n_pre, in
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
     if (e != cudaSuccess) return cuda_fail(e, "fill rows");
     return SNN_OK;
+}
+
+snn_status snn_add_shared_dense(snn_net* net, int32_t first_pre, int32_t first_post, int32_t pops_per_instance,
+                                int32_t n_instances, const float* w, int32_t w_on_device, int32_t channel, double k1,
+                                double k2, double k3, double density, double n_conn, const double* user_scale,
+                                void* stream) {
+    if (!net || !w || !user_scale || n_instances < 1 || pops_per_instance < 1 || (channel != 0 && channel != 1))
+        return fail(SNN_ERR_INVALID_ARG, "shared dense: bad network, weights, scales, instance layout or channel");
+    if (net->graded) return fail(SNN_ERR_STATE, "shared dense: not for graded networks");
+    const int32_t np = (int32_t)net->pops.size(), B = n_instances;
+    if (first_pre < 0 || first_post < 0 || first_pre >= pops_per_instance || first_post >= pops_per_instance ||
+        (int64_t)(B - 1) * pops_per_instance + std::max(first_pre, first_post) >= np)
+        return fail(SNN_ERR_INVALID_ARG, "shared dense: populations outside the batch");
+    const int32_t n_pre = net->pops[first_pre].d.n, n_post = net->pops[first_post].d.n;
+    const int64_t off0 = net->pops[first_post].offset;
+    const int64_t ldg = B > 1 ? (int64_t)net->pops[first_post + pops_per_instance].offset - off0 : (int64_t)n_post;
+    std::vector<int32_t> pre_pop((size_t)B), pre_off((size_t)B);
+    std::vector<float> scale((size_t)B);
+    const double nc = n_conn > 0.0 ? n_conn : density * (double)n_pre;
+    if (!(k2 + nc > 0.0) || !std::isfinite(k2 + nc)) return fail(SNN_ERR_GSCALE, "shared dense: nConn + k2 <= 0");
+    for (int32_t b = 0; b < B; ++b) {
+        const int32_t pp = first_pre + b * pops_per_instance, qp = first_post + b * pops_per_instance;
+        if (net->pops[pp].d.n != n_pre || net->pops[qp].d.n != n_post)
+            return fail(SNN_ERR_INVALID_ARG, "shared dense: instance " + std::to_string(b) + " has other population sizes");
+        if (net->pops[qp].d.kind == SNN_POP_SOURCE)
+            return fail(SNN_ERR_INVALID_ARG, "shared dense: the post population must not be a source");
+        if ((int64_t)net->pops[qp].offset != off0 + b * ldg)
+            return fail(SNN_ERR_INVALID_ARG, "shared dense: post populations are not evenly spaced (instances differ)");
+        pre_pop[b] = pp;
+        pre_off[b] = net->pops[pp].offset;
+        const double sv = (k1 / (k2 + nc) + k3) * user_scale[b];
+        if (!std::isfinite(sv)) return fail(SNN_ERR_GSCALE, "shared dense: non-finite scale");
+        scale[b] = (float)sv;
+    }
+    cudaStream_t s = (cudaStream_t)stream;
+    try {
+        SharedDense d;
+        d.B = B;
+        d.n_pre = n_pre;
+        d.n_post = n_post;
+        d.channel = channel;
+        d.ldg = ldg;
+        d.G = (channel == 0 ? net->g0 : net->g1) + off0;
+        d.pre_pops = pre_pop;
+        snn_status st = snn_dense_batch_create(w, n_pre, n_post, w_on_device, net->mem.have ? &net->mem.a : nullptr,
+                                               stream, &d.h);
+        if (st != SNN_OK) return st;
+        struct Undo {
+            SharedDense* d;
+            ~Undo() { if (d) snn_dense_batch_destroy(d->h); }
+        } undo{&d};
+        TRY(dense_batch_reserve(d.h, B, s));
+        TRY(dalloc(net, &d.pre_pop, (size_t)B, "shared pre populations"));
+        TRY(dalloc(net, &d.pre_off, (size_t)B, "shared pre offsets"));
+        TRY(dalloc(net, &d.spk_off, (size_t)B + 1, "shared spike offsets"));
+        TRY(dalloc(net, &d.spk, (size_t)B * n_pre, "shared spike lists"));
+        TRY(dalloc(net, &d.scale, (size_t)B, "shared scales"));
+        CK(cudaMemcpyAsync(d.pre_pop, pre_pop.data(), sizeof(int32_t) * B, cudaMemcpyHostToDevice, s), "upload");
+        CK(cudaMemcpyAsync(d.pre_off, pre_off.data(), sizeof(int32_t) * B, cudaMemcpyHostToDevice, s), "upload");
+        CK(cudaMemcpyAsync(d.scale, scale.data(), sizeof(float) * B, cudaMemcpyHostToDevice, s), "upload");
+        if (channel == 1)
+            for (int32_t b = 0; b < B; ++b) CK(mark_state_live(net, first_post + b * pops_per_instance, true, false, s),
+                                               "channel 1 live");
+        CK(cudaStreamSynchronize(s), "synchronize");
+        undo.d = nullptr;
+        net->shared.push_back(d);
+        drop_graph(net);
+        if (net->engine == 1 || net->engine == 3) net->engine = 2;
+        return SNN_OK;
+    } catch (const std::bad_alloc&) {
+        return fail(SNN_ERR_OOM, "host allocation failed");
+    }
 }
 
 }  // extern "C"

@@ -51,6 +51,15 @@ static_assert(kTN == kTM, "S and W tiles share one tile shape");
 
 using namespace snn::tc;
 
+// Device-side choice between the two delivery paths inside a time step (so
+// one captured sequence serves every spike count): gate 0 always runs, gate 1
+// runs when the step's spikes (spk_off[B]) reach thr, gate 2 when they do not.
+__device__ __forceinline__ bool gated_off(int32_t gate, const int32_t* spk_off, int32_t B, int64_t thr) {
+    if (gate == 0) return false;
+    const bool dense = (int64_t)spk_off[B] >= thr;
+    return gate == 1 ? !dense : dense;
+}
+
 // Element offset of (row, k) inside the tiled K-major layout with `kt` K tiles per row band.
 __host__ __device__ __forceinline__ int64_t tiled_offset(int64_t row, int64_t k, int64_t kt) {
     return snn::tc::tiled_offset(row, k, kt, kTK);
@@ -77,7 +86,8 @@ __global__ void k_split_weights(const float* W, int32_t n_pre, int32_t n_post, i
 // consecutive K elements, which are contiguous in the tiled layout), then
 // 1.0 at every spike of instance b (rows b >= B stay zero).
 __global__ void k_build_spikes(const int32_t* spk_off, const int32_t* spk, int32_t B, int32_t n_pre, int64_t kp,
-                               uint16_t* S, uint32_t* error) {
+                               uint16_t* S, uint32_t* error, int32_t gate, int64_t thr) {
+    if (gated_off(gate, spk_off, B, thr)) return;
     const int b = blockIdx.x;
     const int64_t kt = kp / kTK;
     for (int64_t k8 = threadIdx.x; k8 < kp / 8; k8 += blockDim.x)
@@ -100,7 +110,9 @@ constexpr uint32_t kIdesc = idesc_bf16(kTM, kTN);
 __global__ void __launch_bounds__(kThreadsMma, 1)
     k_dense_batch_mma(const uint16_t* __restrict__ S, const uint16_t* __restrict__ parts, int64_t np, int64_t kp,
                       int32_t B, int32_t n_post, const float* __restrict__ scale, float* G, int64_t ldg,
-                      uint32_t* error, uint32_t spin_limit, int32_t k_per_cta) {
+                      uint32_t* error, uint32_t spin_limit, int32_t k_per_cta, const int32_t* spk_off,
+                      int32_t gate, int64_t thr) {
+    if (gated_off(gate, spk_off, B, thr)) return;          // uniform over the CTA, before any barrier
     extern __shared__ __align__(1024) unsigned char s_raw[];
     __shared__ __align__(8) unsigned long long s_full[kStages], s_done[kStages];
     __shared__ uint32_t s_tmem;
@@ -229,7 +241,9 @@ __global__ void __launch_bounds__(kThreadsMma, 1)
 // 1024 posts); each thread sums its four posts over the instance's spikes.
 __global__ void __launch_bounds__(256) k_dense_batch_rows(const float* __restrict__ W, int32_t n_post,
                                                           const int32_t* spk_off, const int32_t* spk,
-                                                          const float* scale, float* G, int64_t ldg) {
+                                                          const float* scale, float* G, int64_t ldg, int32_t B,
+                                                          int32_t gate, int64_t thr) {
+    if (gated_off(gate, spk_off, B, thr)) return;
     const int b = blockIdx.y;
     const int j = (blockIdx.x * 256 + threadIdx.x) * 4;
     if (j >= n_post) return;
@@ -364,12 +378,23 @@ snn_status snn_dense_batch_deliver(snn_dense_batch* h, int32_t B, const int32_t*
     if (B == 0) return SNN_OK;
     cudaStream_t s = (cudaStream_t)stream;
     snn_status st = SNN_OK;
-    if (engine == 0) {
-        const dim3 grid((unsigned)((h->n_post + 1023) / 1024), (unsigned)B);
-        k_dense_batch_rows<<<grid, 256, 0, s>>>(h->W, h->n_post, spk_off, spk, scale, G, ldg);
-        return cuda(cudaGetLastError(), "CUDA-core delivery");
-    }
+    if (engine == 1 && (st = snn::dense_batch_reserve(h, B, s)) != SNN_OK) return st;
+    return cuda(snn::dense_batch_launch(h, B, spk_off, spk, scale, G, ldg, engine, 0, s), "dense delivery");
+}
+
+snn_status snn_dense_batch_check(snn_dense_batch* h, void* stream) {
+    if (!h) return fail(SNN_ERR_INVALID_ARG, "dense batch is NULL");
+    return check_error(h, (cudaStream_t)stream);
+}
+
+}  // extern "C"
+
+namespace snn {
+
+// Spike-matrix capacity for B instances (allocates; not inside a capture).
+snn_status dense_batch_reserve(snn_dense_batch* h, int32_t B, cudaStream_t s) {
     const int64_t bp = (int64_t)(B + 2 * kTM - 1) / (2 * kTM) * (2 * kTM);   // whole pairs of row tiles
+    snn_status st = SNN_OK;
     if (bp > h->bp_cap) {
         if (h->S) {
             if ((st = cuda(cudaStreamSynchronize(s), "synchronize")) != SNN_OK) return st;
@@ -380,14 +405,36 @@ snn_status snn_dense_batch_deliver(snn_dense_batch* h, int32_t B, const int32_t*
         if ((st = dalloc(h, &h->S, (size_t)(bp * h->kp), "spike matrix")) != SNN_OK) return st;
         h->bp_cap = bp;
     }
-    k_build_spikes<<<(unsigned)bp, 128, 0, s>>>(spk_off, spk, B, h->n_pre, h->kp, h->S, h->error);
-    const size_t smem = kStages * (size_t)kStageBytes;
     if (!h->smem_set) {
+        const size_t smem = kStages * (size_t)kStageBytes;
         if ((st = cuda(cudaFuncSetAttribute(k_dense_batch_mma, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem),
                        "shared memory")) != SNN_OK)
             return st;
         h->smem_set = true;
     }
+    return SNN_OK;
+}
+
+// G[b] += scale[b] * (S W)[b] for the spike lists (spk_off, spk) of B
+// instances: engine 0 CUDA cores, 1 tensor cores, 2 both launched with the
+// device-side gate (tensor cores when the spikes reach `thr`).  The tensor
+// path needs dense_batch_reserve(h, >= B) first; nothing here allocates or
+// synchronises, so it may be captured.
+cudaError_t dense_batch_launch(snn_dense_batch* h, int32_t B, const int32_t* spk_off, const int32_t* spk,
+                               const float* scale, float* G, int64_t ldg, int32_t engine, int64_t thr, cudaStream_t s) {
+    if (B == 0) return cudaSuccess;
+    if (engine == 0 || engine == 2) {
+        const dim3 grid((unsigned)((h->n_post + 1023) / 1024), (unsigned)B);
+        k_dense_batch_rows<<<grid, 256, 0, s>>>(h->W, h->n_post, spk_off, spk, scale, G, ldg, B, engine == 2 ? 2 : 0,
+                                                thr);
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess || engine == 0) return e;
+    }
+    const int64_t bp = (int64_t)(B + 2 * kTM - 1) / (2 * kTM) * (2 * kTM);   // whole pairs of row tiles
+    if (bp > h->bp_cap || !h->smem_set) return cudaErrorInvalidValue;
+    const int32_t gate = engine == 2 ? 1 : 0;
+    k_build_spikes<<<(unsigned)bp, 128, 0, s>>>(spk_off, spk, B, h->n_pre, h->kp, h->S, h->error, gate, thr);
+    const size_t smem = kStages * (size_t)kStageBytes;
     // split the K range only when the output has fewer than half as many
     // tiles as SMs (measured: a split that only evens out the waves costs
     // more in its atomic epilogue than the idle SMs of the last wave)
@@ -397,14 +444,8 @@ snn_status snn_dense_batch_deliver(snn_dense_batch* h, int32_t B, const int32_t*
     ksplit = (kt + k_per - 1) / k_per;
     const dim3 grid((unsigned)(h->np / kTN), (unsigned)(bp / (2 * kTM)), (unsigned)ksplit);
     k_dense_batch_mma<<<grid, kThreadsMma, smem, s>>>(h->S, h->parts, h->np, h->kp, B, h->n_post, scale, G, ldg,
-                                                      h->error, h->spin_limit, k_per);
-    if ((st = cuda(cudaGetLastError(), "tensor-core delivery")) != SNN_OK) return st;
-    return SNN_OK;
+                                                      h->error, h->spin_limit, k_per, spk_off, gate, thr);
+    return cudaGetLastError();
 }
 
-snn_status snn_dense_batch_check(snn_dense_batch* h, void* stream) {
-    if (!h) return fail(SNN_ERR_INVALID_ARG, "dense batch is NULL");
-    return check_error(h, (cudaStream_t)stream);
-}
-
-}  // extern "C"
+}  // namespace snn

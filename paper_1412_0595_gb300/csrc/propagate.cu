@@ -23,7 +23,7 @@ constexpr int kDenseRows = 32;     // spiking rows per dense item
 constexpr int kDensePosts = 128;   // posts per dense item (32 lanes x 4)
 
 __device__ __forceinline__ int64_t items_of(const DevProj& q, int slot) {
-    if (q.mode == 1) return 0;                    // post-tiled rows have their own kernel
+    if (q.mode != 0) return 0;                    // post-tiled rows have their own kernels
     const int64_t ns = q.nspk[slot];
     if (q.layout == SNN_LAYOUT_CSR) return ns * q.chunks;
     return ((ns + kDenseRows - 1) / kDenseRows) * q.chunks;

@@ -266,6 +266,106 @@ __global__ void __launch_bounds__(kThreads) k_propagate_tiled(const DevProj* qp,
     }
 }
 
+// Segment form for rows of moderate density (tens to hundreds of synapses of
+// a row per 2048-post tile), where one bulk copy and one CTA barrier per
+// piece cost more than the piece.  A CTA item is a group of spiking rows (all
+// of them, up to kSegRows, when there are enough post spans to give every CTA
+// an item) times a span of kSegTiles post tiles: the threads gather the rows'
+// segment bounds from the split table into shared memory at once, then each
+// warp streams four rows at a time (eight lanes per row, 16-byte loads, four
+// in flight per lane) straight into the shared accumulator (shared float
+// atomics: the rows of an item hit the same posts), and the span is flushed
+// to the conductance with one vector reduction per four posts that received
+// events.
+constexpr int kSegThreads = 512;
+constexpr int kSegTiles = 2;                  // 2048-post tiles per item span (4096 posts, 16 KiB accumulator)
+constexpr int kSegRows = 512;                 // rows per item at most
+
+__global__ void __launch_bounds__(kSegThreads) k_propagate_seg(const DevProj* qp, const unsigned long long* ticket,
+                                                               int32_t num_tiles) {
+    __shared__ float s_acc[kSegTiles * kPostTile];
+    __shared__ int64_t s_beg[kSegRows], s_end[kSegRows];
+    const DevProj& q = *qp;
+    const int slot = (int)((*ticket / (unsigned long long)num_tiles + 1ull) & 1ull);
+    const int ns = q.nspk[slot];
+    if (ns == 0) return;
+    const int nt = q.n_ptiles, P = q.ptile;
+    const int n_span = (nt + kSegTiles - 1) / kSegTiles;
+    // row groups: as few as give every CTA an item, at most kSegRows rows each
+    int64_t groups = ((int64_t)gridDim.x + n_span - 1) / n_span;
+    const int64_t min_groups = (ns + kSegRows - 1) / kSegRows;
+    if (groups > ns) groups = ns;
+    if (groups < min_groups) groups = min_groups;
+    const int G = (int)((ns + groups - 1) / groups);
+    groups = (ns + G - 1) / G;
+    const int64_t items = groups * (int64_t)n_span;
+    const float sc = q.scale;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int sub = lane >> 3, sl = lane & 7;             // row slot of the warp (4) and lane within it (8)
+    constexpr int kSlots = (kSegThreads / 32) * 4;        // rows streamed at once by the CTA
+    const int32_t* __restrict__ col = q.col;
+    const float* __restrict__ w = q.w;
+    for (int j = threadIdx.x; j < kSegTiles * kPostTile; j += kSegThreads) s_acc[j] = 0.0f;
+    for (int64_t item = blockIdx.x; item < items; item += gridDim.x) {
+        const int span = (int)(item % n_span), grp = (int)(item / n_span);
+        const int r0 = grp * G, r1 = min(ns, r0 + G);
+        const int T0 = span * kSegTiles, T1 = min(nt, T0 + kSegTiles);
+        const int post0 = T0 * P;
+        for (int r = r0 + (int)threadIdx.x; r < r1; r += kSegThreads) {
+            const int64_t* sp = q.split + (int64_t)q.spk[r] * (nt + 1);
+            s_beg[r - r0] = sp[T0];
+            s_end[r - r0] = sp[T1];
+        }
+        __syncthreads();                           // bounds ready (and the accumulator clear)
+        float* acc = s_acc - post0;
+        for (int rr = warp * 4 + sub; rr < r1 - r0; rr += kSlots) {
+            const int64_t beg = s_beg[rr], end = s_end[rr];
+            // col / w are padded to a multiple of 4 entries: aligned 16-byte
+            // loads that start before `end` stay inside the allocation
+            for (int64_t k0 = (beg & ~int64_t(3)) + 4 * sl; k0 < end; k0 += 4 * 32) {
+                int4 c4[4];
+                float4 w4[4];
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    const int64_t k = k0 + 32 * u;
+                    if (k < end) {
+                        c4[u] = __ldcs(reinterpret_cast<const int4*>(col + k));
+                        w4[u] = __ldcs(reinterpret_cast<const float4*>(w + k));
+                    }
+                }
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    const int64_t k = k0 + 32 * u;
+                    if (k < end) {
+                        if (k >= beg) atomicAdd(acc + c4[u].x, sc * w4[u].x);
+                        if (k + 1 >= beg && k + 1 < end) atomicAdd(acc + c4[u].y, sc * w4[u].y);
+                        if (k + 2 >= beg && k + 2 < end) atomicAdd(acc + c4[u].z, sc * w4[u].z);
+                        if (k + 3 >= beg && k + 3 < end) atomicAdd(acc + c4[u].w, sc * w4[u].w);
+                    }
+                }
+            }
+        }
+        __syncthreads();                           // the span's events are in the accumulator
+        const int width = min(kSegTiles * P, q.n_post - post0);
+        float* gp = q.g + post0;
+        if ((width & 3) == 0) {
+            for (int j = 4 * threadIdx.x; j < width; j += 4 * kSegThreads) {
+                const float4 v = *reinterpret_cast<const float4*>(s_acc + j);
+                if (v.x != 0.f || v.y != 0.f || v.z != 0.f || v.w != 0.f)
+                    atomicAdd(reinterpret_cast<float4*>(gp + j), v);
+                *reinterpret_cast<float4*>(s_acc + j) = make_float4(0.f, 0.f, 0.f, 0.f);
+            }
+        } else {
+            for (int j = threadIdx.x; j < width; j += kSegThreads) {
+                if (s_acc[j] != 0.f) atomicAdd(gp + j, s_acc[j]);
+                s_acc[j] = 0.0f;
+            }
+        }
+        // the next item's bounds overwrite s_beg / s_end after every thread
+        // has passed this item's second barrier
+    }
+}
+
 }  // namespace
 
 cudaError_t launch_row_splits(const int64_t* row_ptr, const int32_t* col, int32_t n_pre, int32_t n_tiles, int32_t P,
@@ -274,6 +374,16 @@ cudaError_t launch_row_splits(const int64_t* row_ptr, const int32_t* col, int32_
     if (total == 0) return cudaSuccess;
     const int blocks = (int)std::min<int64_t>((total + kThreads - 1) / kThreads, 4096);
     k_row_splits<<<blocks, kThreads, 0, s>>>(row_ptr, col, n_pre, n_tiles, P, split);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_propagate_seg(const DevProj* q, const unsigned long long* ticket, int32_t num_tiles, int sm_count,
+                                 cudaStream_t s) {
+    int per_sm = 0;
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_propagate_seg, kSegThreads, 0);
+    if (e != cudaSuccess) return e;
+    const int blocks = std::max(1, sm_count * std::max(1, per_sm));
+    k_propagate_seg<<<blocks, kSegThreads, 0, s>>>(q, ticket, std::max(1, num_tiles));
     return cudaGetLastError();
 }
 

@@ -72,7 +72,7 @@ struct DevProj {
     float* acc;            // persistent engine: event accumulator (buffer 0), offset to the post population
     int32_t post_soa;      // SoA offset of the post population
     int32_t channel;       // post conductance channel
-    int32_t mode;          // compressed rows: 0 warp per row chunk, 1 post-tiled (own kernel)
+    int32_t mode;          // compressed rows: 0 warp per row chunk, 1 post-tiled bulk copies, 2 post-tiled segments
     int32_t n_ptiles;      // post tiles of the post-tiled mode
     int32_t ptile;         // posts per tile
     const int64_t* split;  // [n_pre][n_ptiles + 1] first synapse of each row in each post tile
@@ -230,7 +230,7 @@ struct ProjHost {
     float scale;
     int64_t nnz;
     int32_t max_row;
-    int32_t mode = 0;          // 1: post-tiled propagation
+    int32_t mode = 0;          // 1: post-tiled bulk copies, 2: post-tiled segments
     int64_t* split = nullptr;
     int64_t* csplit = nullptr;     // cluster engine row segments
     int64_t* row_ptr = nullptr;
@@ -238,6 +238,22 @@ struct ProjHost {
     float* w = nullptr;
 };
 
+}  // namespace snn
+
+namespace snn {
+// A dense projection shared by every instance of a batch (snn_add_shared_dense).
+struct SharedDense {
+    snn_dense_batch* h = nullptr;  // W, its BF16 parts and the spike matrix
+    int32_t B = 0, n_pre = 0, n_post = 0, channel = 0;
+    int32_t* pre_pop = nullptr;    // [B] population index of instance b's pre population (device)
+    int32_t* pre_off = nullptr;    // [B] its SoA offset (device)
+    int32_t* spk_off = nullptr;    // [B + 1] the step's spike lists (device), built each step
+    int32_t* spk = nullptr;        // [B * n_pre]
+    float* scale = nullptr;        // [B] s_b = gScale(nConn) * user_scale[b]
+    float* G = nullptr;            // conductance channel of instance 0's post population
+    int64_t ldg = 0;               // SoA distance between instances' post populations
+    std::vector<int32_t> pre_pops; // host copy of pre_pop
+};
 }  // namespace snn
 
 struct snn_net {
@@ -296,6 +312,9 @@ struct snn_net {
     uint16_t *grad_A = nullptr, *grad_B = nullptr;   // operand parts of the dense weight gradient
     size_t grad_A_cap = 0, grad_B_cap = 0;
     int32_t dense_grad = 1;                   // dense weight gradient: 0 CUDA cores, 1 tensor cores
+    std::vector<snn::SharedDense> shared;     // dense projections shared by all instances of a batch
+    int32_t shared_engine = 2;                // their delivery: 0 CUDA cores, 1 tensor cores, 2 by spike density
+    double shared_density = 0.03;             // spike density from which engine 2 uses the tensor cores
     unsigned long long* counters = nullptr;   // 2 * n_pops
     unsigned long long* ticket = nullptr;     // [0] ticket, [1] epoch base
     int32_t* tile_pop = nullptr;
@@ -367,6 +386,8 @@ cudaError_t launch_count_events(const DevProj* projs, int n_projs, unsigned long
 cudaError_t launch_row_splits(const int64_t* row_ptr, const int32_t* col, int32_t n_pre, int32_t n_tiles, int32_t P,
                               int64_t* split, cudaStream_t s);
 cudaError_t propagate_occupancy(int* per_sm);   // resident row-kernel CTAs per SM (no dynamic smem)
+cudaError_t launch_propagate_seg(const DevProj* q, const unsigned long long* ticket, int32_t num_tiles, int sm_count,
+                                 cudaStream_t s);
 cudaError_t launch_propagate_tiled(const DevProj* q, int32_t P, const unsigned long long* ticket, int32_t num_tiles,
                                    int sm_count, uint32_t* error, uint32_t spin_limit, cudaStream_t s);
 constexpr int32_t kPostTile = 2048;          // posts per tile of the post-tiled propagation (8 KiB)
@@ -374,6 +395,12 @@ cudaError_t persistent_capacity(int sm_count, int* blocks);
 // Compressed rows whose segment in a CTA's slice the cluster engine keeps in
 // shared memory (16 bytes each).
 constexpr int kClusterSegCacheRows = 2048;
+// Dense delivery for batched instances that share W (dense_batch.cu): the
+// spike-matrix capacity, and the launches without allocation (engine 0 CUDA
+// cores, 1 tensor cores, 2 both gated on the device by spike count >= thr).
+snn_status dense_batch_reserve(snn_dense_batch* h, int32_t B, cudaStream_t s);
+cudaError_t dense_batch_launch(snn_dense_batch* h, int32_t B, const int32_t* spk_off, const int32_t* spk,
+                               const float* scale, float* G, int64_t ldg, int32_t engine, int64_t thr, cudaStream_t s);
 cudaError_t mark_state_live(snn_net* net, int32_t pop, bool g1, bool iext, cudaStream_t s);
 int cluster_plan(int n_total, int n_pops, int n_projs, int* per_cta);
 cudaError_t cluster_supported(int cl, int per_cta, int num_tiles, int seg_rows, bool* ok);

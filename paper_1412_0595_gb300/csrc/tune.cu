@@ -126,6 +126,7 @@ std::string shape_key(snn_net* net) {
     for (const auto& q : net->projs)
         k += "|" + std::to_string(q.d.pre) + ">" + std::to_string(q.d.post) + ":" + std::to_string(q.d.layout) +
              ":" + std::to_string(q.nnz);
+    for (const auto& d : net->shared) k += "|shared:" + std::to_string(d.B) + "x" + std::to_string(d.n_pre);
     return k;
 }
 
@@ -242,9 +243,10 @@ snn_status snn_autotune(snn_net* net, int32_t trial_steps, snn_tuning* result, v
         const int sm = net->sm_count;
         for (int blocks : {2 * sm, 4 * sm, 8 * sm})
             for (int chunk : {512, 1024, 2048})
-                for (int tiled : {0, 2}) cands.push_back({0, blocks, chunk, tiled, 0.0});
-        if (net->persist_grid > 0) cands.push_back({1, 4 * sm, 1024, 2, 0.0});
-        if (net->cluster_size > 0) cands.push_back({3, 4 * sm, 1024, 2, 0.0});
+                for (int tiled : {0, 2, 3}) cands.push_back({0, blocks, chunk, tiled, 0.0});
+        // shared dense projections step in the plain engine only
+        if (net->persist_grid > 0 && net->shared.empty()) cands.push_back({1, 4 * sm, 1024, 2, 0.0});
+        if (net->cluster_size > 0 && net->shared.empty()) cands.push_back({3, 4 * sm, 1024, 2, 0.0});
         const snn_status st = time_candidates(net, cands, trial_steps, &best, stream);
         if (st != SNN_OK) return st;
         std::lock_guard<std::mutex> lock(g_cache_mu);

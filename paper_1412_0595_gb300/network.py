@@ -215,6 +215,20 @@ class Network:
         self.dt = float(dt)
         return self
 
+    def add_shared_dense(self, pre, post, W, user_scale, *, channel=0, k=(1.0, 0.0, 0.0), density=1.0, n_conn=0.0,
+                         pops_per_instance=None, stream=None):
+        """A dense projection W (n_pre x n_post) that every instance of this
+        batch shares (snn_add_shared_dense): instance b's population `post`
+        (index within an instance) receives s_b W[i] for each spike i of its
+        population `pre`, s_b = (k1 / (k2 + nConn) + k3) * user_scale[b]."""
+        B = len(self.pop_offsets)
+        ppi = pops_per_instance if pops_per_instance is not None else len(self.sizes) // B
+        w = _dev(W, torch.float32, self.device)
+        sc = (C.c_double * B)(*[float(x) for x in user_scale])
+        check(L.lib.snn_add_shared_dense(self.h, int(pre), int(post), int(ppi), B, w.data_ptr(), 1, int(channel),
+                                         float(k[0]), float(k[1]), float(k[2]), float(density), float(n_conn), sc,
+                                         _stream(stream)))
+
     @classmethod
     def from_specs(cls, specs, device=None, stream=None, **kw):
         """Batch of ``snn_inputs`` descriptions (same dt, substeps and seed),

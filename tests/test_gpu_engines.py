@@ -115,13 +115,15 @@ def test_persistent_engine_with_more_tiles_than_resident_ctas(gpu):
     (64, 3, 0.4, (1, 5, 64)),
     (64, 20001, 0.9, (1, 64)),            # segments of ~3,700 synapses per row and tile
     (40000, 20001, 0.01, (40000,)),       # ~1,300 pieces per CTA: several descriptor batches
+    (300, 70001, 0.05, (1, 33, 65, 300)), # segment form: row groups of up to 64 rows, ragged last span
 ])
-def test_post_tiled_propagation_matches_oracle(gpu, n_pre, n_post, p, ks):
+@pytest.mark.parametrize("mode", [1, 3])              # bulk-copy pieces, warp-streamed segments
+def test_post_tiled_propagation_matches_oracle(gpu, n_pre, n_post, p, ks, mode):
     spec = I.net([I.source_pop(n_pre, 0.0), I.hh_pop(n_post)],
                  [I.proj(0, 1, "csr", p, ("uniform", 0.0, 1.0))], dt=0.1, steps=1)
     net = gpu.Network.from_spec(spec)
     net.set_option("engine", 0)
-    net.set_option("tiled", 1)
+    net.set_option("tiled", mode)
     ref = oracle.from_spec(spec)
     rng = np.random.default_rng(2)
     for k in ks:
@@ -131,14 +133,15 @@ def test_post_tiled_propagation_matches_oracle(gpu, n_pre, n_post, p, ks):
         assert _rel_ok(net.read_host(1, "g0"), ref.get(1, "g0"))
 
 
-def test_post_tiled_steps_match_row_kernel(gpu):
+@pytest.mark.parametrize("mode", [1, 3])
+def test_post_tiled_steps_match_row_kernel(gpu, mode):
     # rows of ~6,000 synapses over 30,000 posts; sources fire often, the HH
     # population stays subthreshold so V compares tightly
     spec = I.net([I.source_pop(100, 2000.0), I.hh_pop(30000, v0_range=(-64.0, -62.0))],
                  [I.proj(0, 1, "csr", 0.2, ("uniform", 0.0, 0.5))], dt=0.1, steps=1)
     a = gpu.Network.from_spec(spec)
     b = gpu.Network.from_spec(spec)
-    for net, tiled in ((a, 0), (b, 1)):
+    for net, tiled in ((a, 0), (b, mode)):
         net.set_option("engine", 0)
         net.set_option("tiled", tiled)
         net.step(150)
