@@ -973,6 +973,7 @@ _KERNEL_SOURCES = {
     "k_step_cluster": ["cluster.cu", "neuron_update.cuh", "device_math.cuh", "compaction.cuh", "snn_internal.cuh"],
     "k_neuron_step": ["neuron.cu", "neuron_update.cuh", "device_math.cuh", "compaction.cuh", "snn_internal.cuh"],
     "k_propagate_tiled": ["propagate_tiled.cu", "snn_internal.cuh"],
+    "k_propagate_seg": ["propagate_tiled.cu", "snn_internal.cuh"],
     "k_propagate": ["propagate.cu", "snn_internal.cuh"],
     "k_dense_batch_mma": ["dense_batch.cu", "tc_common.cuh", "snn_internal.cuh"],
     "k_dense_grad_mma": ["graded_dense.cu", "tc_common.cuh", "snn_internal.cuh"],

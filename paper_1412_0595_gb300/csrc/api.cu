@@ -273,6 +273,20 @@ int32_t tiled_mode(const snn_net* net, const ProjHost& P) {
     return per_tile >= 256.0 ? 1 : 0;
 }
 
+}  // namespace
+
+// The propagation mode of every projection under the SNN_OPT_TILED value `tiled`.
+std::vector<int32_t> snn::propagation_modes(const snn_net* net, int32_t tiled) {
+    snn_net probe_opts;
+    probe_opts.tiled = tiled;
+    probe_opts.pops = net->pops;
+    std::vector<int32_t> m;
+    for (const auto& P : net->projs) m.push_back(tiled_mode(&probe_opts, P));
+    return m;
+}
+
+namespace {
+
 snn_status setup_tiled(snn_net* net, cudaStream_t s) {
     for (auto& P : net->projs) {
         P.mode = tiled_mode(net, P);

@@ -167,8 +167,9 @@ __device__ __forceinline__ float lane_dot16(const float* w, const uint16_t* idx,
 
 }  // namespace
 
-// One warp per post neuron.  kShared: the releases of the whole network
-// (n_total floats) are first copied into shared memory.
+// One warp per post neuron, or, for projections with short transposed rows,
+// one lane per post (32 posts per work item).  kShared: the releases of the
+// whole network (n_total floats) are first copied into shared memory.
 template <bool kShared, bool kNarrow>
 __global__ void __launch_bounds__(kShared ? kStagedThreads : kThreads, kShared ? 1 : 4) k_graded_spmv(const GradedArgs a) {
     extern __shared__ float s_x[];
@@ -181,18 +182,33 @@ __global__ void __launch_bounds__(kShared ? kStagedThreads : kThreads, kShared ?
     const int lane = threadIdx.x & 31;
     const int64_t warp = (int64_t)blockIdx.x * (blockDim.x / 32) + (threadIdx.x >> 5);
     const int64_t warps = (int64_t)gridDim.x * (blockDim.x / 32);
-    for (int64_t w = warp; w < a.total_posts; w += warps) {
+    for (int64_t it = warp; it < a.spmv_items; it += warps) {
         int q = 0;
-        while (a.gprojs[q].g_off + a.gprojs[q].n_post <= w) ++q;
+        while (a.gprojs[q].dense || a.gprojs[q].item_off + (a.gprojs[q].lane_rows ? (a.gprojs[q].n_post + 31) / 32
+                                                                                  : a.gprojs[q].n_post) <= it)
+            ++q;
         const GradProj& Q = a.gprojs[q];
-        if (Q.dense) continue;                       // dense projections have their own product
-        const int j = (int)(w - Q.g_off);
+        const float* xq = x + Q.pre_off;
+        if (Q.lane_rows) {                           // 32 posts, one per lane, each row summed in order
+            const int j = (int)(32 * (it - Q.item_off)) + lane;
+            if (j < Q.n_post) {
+                const int64_t jb = Q.csc_ptr[j], je = Q.csc_ptr[j + 1];
+                float acc = 0.0f;
+                for (int64_t k = jb; k < je; ++k) {
+                    const int32_t i = kNarrow ? (int32_t)__ldg(Q.csc_pre16 + k) : __ldg(Q.csc_pre + k);
+                    acc = fmaf(__ldg(Q.csc_w + k), gather<kShared>(xq, i), acc);
+                }
+                a.G[Q.g_off + j] = acc;
+            }
+            continue;
+        }
+        const int j = (int)(it - Q.item_off);
         float acc;
-        if constexpr (kNarrow) acc = lane_dot16<kShared>(Q.csc_w, Q.csc_pre16, x + Q.pre_off, Q.csc_ptr[j], Q.csc_ptr[j + 1], lane);
-        else acc = lane_dot<kShared>(Q.csc_w, Q.csc_pre, x + Q.pre_off, Q.csc_ptr[j], Q.csc_ptr[j + 1], lane);
+        if constexpr (kNarrow) acc = lane_dot16<kShared>(Q.csc_w, Q.csc_pre16, xq, Q.csc_ptr[j], Q.csc_ptr[j + 1], lane);
+        else acc = lane_dot<kShared>(Q.csc_w, Q.csc_pre, xq, Q.csc_ptr[j], Q.csc_ptr[j + 1], lane);
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-        if (lane == 0) a.G[w] = acc;
+        if (lane == 0) a.G[Q.g_off + j] = acc;
     }
 }
 
@@ -445,13 +461,13 @@ static cudaError_t launch_staged(K kernel, size_t bytes, cudaStream_t s, Args...
 }
 
 cudaError_t launch_graded_spmv(const GradedArgs& a, cudaStream_t s) {
-    if (a.total_posts == 0) return cudaSuccess;
+    if (a.spmv_items == 0) return cudaSuccess;
     const size_t bytes = sizeof(float) * (size_t)a.n_total;
     if (bytes <= kStageMaxBytes)
         return a.narrow ? launch_staged(k_graded_spmv<true, true>, bytes, s, a)
                         : launch_staged(k_graded_spmv<true, false>, bytes, s, a);
-    if (a.narrow) k_graded_spmv<false, true><<<grid_warps(a.total_posts), kThreads, 0, s>>>(a);
-    else k_graded_spmv<false, false><<<grid_warps(a.total_posts), kThreads, 0, s>>>(a);
+    if (a.narrow) k_graded_spmv<false, true><<<grid_warps(a.spmv_items), kThreads, 0, s>>>(a);
+    else k_graded_spmv<false, false><<<grid_warps(a.spmv_items), kThreads, 0, s>>>(a);
     return cudaGetLastError();
 }
 

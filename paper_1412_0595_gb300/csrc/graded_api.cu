@@ -28,6 +28,7 @@ GradedArgs graded_args(snn_net* net) {
     a.gprojs = net->d_gprojs;
     a.n_gprojs = (int32_t)net->projs.size();
     a.total_posts = net->total_posts;
+    a.spmv_items = net->spmv_items;
     a.in_begin = net->in_begin;
     a.in_list = net->in_list;
     a.out_begin = net->out_begin;
@@ -68,6 +69,7 @@ cudaError_t graded_one_step(snn_net* net, GradedArgs a, float* G, int64_t t, cud
 
 snn_status upload_gprojs(snn_net* net) {
     std::vector<GradProj> g(net->projs.size());
+    int64_t items = 0;
     for (size_t q = 0; q < g.size(); ++q) {
         const ProjHost& P = net->projs[q];
         const PopHost& pre = net->pops[P.d.pre];
@@ -90,7 +92,14 @@ snn_status upload_gprojs(snn_net* net) {
         d.csc_pre16 = P.csc_pre16;
         d.csc_w = P.csc_w;
         d.dense = P.d.layout == SNN_LAYOUT_DENSE ? 1 : 0;
+        // forward product: posts with short transposed rows (fewer than 24
+        // synapses on average) one per lane, 32 to a work item; longer rows
+        // one post per warp; dense storage has its own product
+        d.lane_rows = (!d.dense && (double)P.nnz < 24.0 * std::max(1, d.n_post)) ? 1 : 0;
+        d.item_off = items;
+        if (!d.dense) items += d.lane_rows ? (d.n_post + 31) / 32 : d.n_post;
     }
+    net->spmv_items = items;
     if (!g.empty())
         SNN_CK(cudaMemcpy(net->d_gprojs, g.data(), g.size() * sizeof(GradProj), cudaMemcpyHostToDevice),
                "upload graded projections");

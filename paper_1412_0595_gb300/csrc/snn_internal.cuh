@@ -106,6 +106,8 @@ struct GradProj {
     const uint16_t* csc_pre16;         // 16-bit when every graded pre population has at most 65,536 neurons
     const float* csc_w;
     int32_t dense;                     // 1: w is the n_pre x n_post matrix (no row / column arrays)
+    int32_t lane_rows;                 // forward product: 1 one post per lane (short rows), 0 one post per warp
+    int64_t item_off;                  // first work item of this projection in the forward product
 };
 
 struct GradedArgs {
@@ -114,6 +116,7 @@ struct GradedArgs {
     const GradProj* gprojs;
     int32_t n_gprojs;
     int64_t total_posts;               // sum of n_post over projections (length of G)
+    int64_t spmv_items;                // work items of the compressed-row forward product
     const int32_t* in_begin;           // [n_pops + 1] incoming projections per population
     const int32_t* in_list;
     const int32_t* out_begin;          // [n_pops + 1] outgoing projections per population
@@ -295,6 +298,7 @@ struct snn_net {
     int32_t* in_begin = nullptr;
     int32_t* in_list = nullptr;
     int64_t total_posts = 0;
+    int64_t spmv_items = 0;                   // work items of the graded forward product
     float *r = nullptr, *G = nullptr, *y = nullptr;
     double* d_grad_scale = nullptr;
     int64_t g_t = 0;                          // graded step counter
@@ -401,6 +405,7 @@ constexpr int kClusterSegCacheRows = 2048;
 snn_status dense_batch_reserve(snn_dense_batch* h, int32_t B, cudaStream_t s);
 cudaError_t dense_batch_launch(snn_dense_batch* h, int32_t B, const int32_t* spk_off, const int32_t* spk,
                                const float* scale, float* G, int64_t ldg, int32_t engine, int64_t thr, cudaStream_t s);
+std::vector<int32_t> propagation_modes(const snn_net* net, int32_t tiled);
 cudaError_t mark_state_live(snn_net* net, int32_t pop, bool g1, bool iext, cudaStream_t s);
 int cluster_plan(int n_total, int n_pops, int n_projs, int* per_cta);
 cudaError_t cluster_supported(int cl, int per_cta, int num_tiles, int seg_rows, bool* ok);

@@ -241,9 +241,13 @@ snn_status snn_autotune(snn_net* net, int32_t trial_steps, snn_tuning* result, v
     if (!cached) {
         std::vector<Choice> cands;
         const int sm = net->sm_count;
+        // the propagation settings that give different kernels: row kernel
+        // only, and the library's choice when it differs from that
+        std::vector<int> tileds{0};
+        if (propagation_modes(net, 2) != propagation_modes(net, 0)) tileds.push_back(2);
         for (int blocks : {2 * sm, 4 * sm, 8 * sm})
             for (int chunk : {512, 1024, 2048})
-                for (int tiled : {0, 2, 3}) cands.push_back({0, blocks, chunk, tiled, 0.0});
+                for (int tiled : tileds) cands.push_back({0, blocks, chunk, tiled, 0.0});
         // shared dense projections step in the plain engine only
         if (net->persist_grid > 0 && net->shared.empty()) cands.push_back({1, 4 * sm, 1024, 2, 0.0});
         if (net->cluster_size > 0 && net->shared.empty()) cands.push_back({3, 4 * sm, 1024, 2, 0.0});
