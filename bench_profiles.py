@@ -177,7 +177,8 @@ def record_traffic(kernel, nbytes, command):
             table = json.load(f)
     except (OSError, ValueError):
         table = {}
-    rels = ["paper_1412_0595_gb300/csrc/" + x for x in _KERNEL_SOURCES[kernel]]
+    # a key may name the workload after the kernel ("k_propagate_stream p=0.2")
+    rels = ["paper_1412_0595_gb300/csrc/" + x for x in _KERNEL_SOURCES[kernel.split(" ")[0]]]
     table[kernel] = {"bytes_per_launch": float(nbytes), "command": command, "sources": rels,
                      "sources_sha256": _sources_sha256(rels)}
     with open(path, "w") as f:

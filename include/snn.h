@@ -293,6 +293,15 @@ snn_status snn_proj_scale(snn_net* net, int32_t proj, float* scale);
 /* Number of synapses stored for projection `proj` (nnz; n_pre * n_post for dense). */
 snn_status snn_proj_nnz(snn_net* net, int32_t proj, int64_t* nnz);
 
+/* Which kernel delivers the spikes of projection `proj` in the plain engine
+ * (Sec. 3's compressed-row propagation and its post-tiled forms), as chosen
+ * by SNN_OPT_TILED: *mode = 0 one warp per row chunk (k_propagate; also every
+ * dense projection), 1 one bulk-copied piece per row and post tile
+ * (k_propagate_tiled), 2 the rows' tile segments streamed by warps into a
+ * shared accumulator (k_propagate_seg).  SNN_ERR_INVALID_ARG for a bad projection or
+ * a NULL `mode`. */
+snn_status snn_proj_mode(snn_net* net, int32_t proj, int32_t* mode);
+
 /* Runs the production propagation kernel of projection `proj` once on the
  * given ascending spike list of its pre population (host or device, n
  * entries), adding s * w to the post conductances.  For checking delivery

@@ -304,7 +304,10 @@ snn_status setup_tiled(snn_net* net, cudaStream_t s) {
 // Propagation of the projections in `dev` (n of them, host copies in `host`).
 cudaError_t launch_projections(snn_net* net, const DevProj* dev, const ProjHost* const* host, int n, cudaStream_t s) {
     PropArgs p{dev, n, net->chunk, net->ticket, std::max(1, net->num_tiles)};
-    cudaError_t e = launch_propagate(p, prop_blocks(net), s);
+    // the row kernel only when some projection takes it (it would find no items otherwise)
+    bool rows = false;
+    for (int q = 0; q < n; ++q) rows = rows || host[q]->mode == 0;
+    cudaError_t e = rows ? launch_propagate(p, prop_blocks(net), s) : cudaSuccess;
     for (int q = 0; q < n && e == cudaSuccess; ++q)
         if (host[q]->mode == 1)
             e = launch_propagate_tiled(dev + q, kPostTile, net->ticket, std::max(1, net->num_tiles), net->sm_count,
@@ -1061,6 +1064,12 @@ snn_status snn_launch_phase(snn_net* net, int32_t phase, void* stream) {
 snn_status snn_proj_scale(snn_net* net, int32_t proj, float* scale) {
     if (!net || !scale || proj < 0 || proj >= (int32_t)net->projs.size()) return fail(SNN_ERR_INVALID_ARG, "bad argument");
     *scale = net->projs[proj].scale;
+    return SNN_OK;
+}
+
+snn_status snn_proj_mode(snn_net* net, int32_t proj, int32_t* mode) {
+    if (!net || !mode || proj < 0 || proj >= (int32_t)net->projs.size()) return fail(SNN_ERR_INVALID_ARG, "bad argument");
+    *mode = net->projs[proj].mode;
     return SNN_OK;
 }
 

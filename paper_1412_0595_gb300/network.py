@@ -310,6 +310,13 @@ class Network:
         check(L.lib.snn_proj_nnz(self.h, int(q), C.byref(v)))
         return v.value
 
+    def proj_mode(self, q):
+        """Propagation kernel of projection q: 0 rows (k_propagate), 1 pieces
+        (k_propagate_tiled), 2 segments (k_propagate_seg)."""
+        v = C.c_int32()
+        check(L.lib.snn_proj_mode(self.h, int(q), C.byref(v)))
+        return v.value
+
     # ------------------------------------------------------------------ state
     def read(self, pop, field, stream=None) -> torch.Tensor:
         """A field of population `pop` as a device tensor (copied)."""

@@ -116,6 +116,7 @@ def test_persistent_engine_with_more_tiles_than_resident_ctas(gpu):
     (64, 20001, 0.9, (1, 64)),            # segments of ~3,700 synapses per row and tile
     (40000, 20001, 0.01, (40000,)),       # ~1,300 pieces per CTA: several descriptor batches
     (300, 70001, 0.05, (1, 33, 65, 300)), # segment form: row groups of up to 64 rows, ragged last span
+    (200, 50001, 0.0005, (1, 7, 200)),    # most row segments of a tile empty, odd last tile width
 ])
 @pytest.mark.parametrize("mode", [1, 3])              # bulk-copy pieces, warp-streamed segments
 def test_post_tiled_propagation_matches_oracle(gpu, n_pre, n_post, p, ks, mode):
@@ -124,6 +125,7 @@ def test_post_tiled_propagation_matches_oracle(gpu, n_pre, n_post, p, ks, mode):
     net = gpu.Network.from_spec(spec)
     net.set_option("engine", 0)
     net.set_option("tiled", mode)
+    assert net.proj_mode(0) == {1: 1, 3: 2}[mode]
     ref = oracle.from_spec(spec)
     rng = np.random.default_rng(2)
     for k in ks:
