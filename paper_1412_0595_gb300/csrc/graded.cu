@@ -24,6 +24,7 @@
 //                    synapse reads K consecutive floats.
 #include "device_math.cuh"
 #include "snn_internal.cuh"
+#include "tc_common.cuh"
 
 namespace snn {
 
@@ -169,13 +170,22 @@ __device__ __forceinline__ float lane_dot16(const float* w, const uint16_t* idx,
 
 // One warp per post neuron, or, for projections with short transposed rows,
 // one lane per post (32 posts per work item).  kShared: the releases of the
-// whole network (n_total floats) are first copied into shared memory.
+// whole network (n_total floats) are first copied into shared memory, their
+// whole 16-byte groups by asynchronous copies that every thread issues at
+// once (a load-then-store loop would wait for each load in turn), the tail
+// by plain loads.
 template <bool kShared, bool kNarrow>
 __global__ void __launch_bounds__(kShared ? kStagedThreads : kThreads, kShared ? 1 : 4) k_graded_spmv(const GradedArgs a) {
-    extern __shared__ float s_x[];
+    extern __shared__ __align__(16) float s_x[];
     const float* x = a.r;
     if constexpr (kShared) {
-        for (int i = threadIdx.x; i < a.n_total; i += blockDim.x) s_x[i] = a.r[i];
+        // (16-byte copies need a 16-byte aligned source; the release array is its own allocation)
+        const int n4 = (reinterpret_cast<uintptr_t>(a.r) & 15u) == 0 ? a.n_total / 4 : 0;
+        for (int i = threadIdx.x; i < n4; i += blockDim.x)
+            asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(tc::smem_u32(s_x + 4 * i)), "l"(a.r + 4 * i)
+                         : "memory");
+        for (int i = 4 * n4 + (int)threadIdx.x; i < a.n_total; i += blockDim.x) s_x[i] = a.r[i];
+        asm volatile("cp.async.wait_all;" ::: "memory");
         __syncthreads();
         x = s_x;
     }

@@ -189,3 +189,37 @@ def test_backward_without_forward_is_rejected(gpu):
     with pytest.raises(snn.SNNError) as e:
         net.backward(torch.zeros((10, 20), device="cuda"))
     assert e.value.name == "SNN_ERR_STATE"
+
+
+
+def _fan_in_spec(n_in, n_out, p, T):
+    """In (driven, started between -30 and -10 mV so that it releases from
+    the first step) -> Out through one graded projection: the forward
+    product's paths by the pre population's size (16- or 32-bit transposed
+    indices) and by the posts' row lengths (stages of whole posts with a warp
+    or a lane per post, or a warp per post from HBM when a post is longer than
+    a stage)."""
+    pops = [I.hh_pop(n_in, v0_range=(-30.0, -10.0), drive=dict(I.INPUT_DRIVE)), I.hh_pop(n_out)]
+    pr = I.proj(0, 1, "csr", p, ("uniform", 0.0, I.GRADED_WEIGHTS[0]))
+    pr.update(synapse="graded", v_thr=I.GRADED["v_thr"], v_slope=I.GRADED["v_slope"])
+    return I.net(pops, [pr], dt=0.05, steps=T)
+
+
+@pytest.mark.parametrize("n_in,n_out,p", [
+    (70000, 40, 0.02),      # 32-bit pre indices, 1,400 synapses per post
+    (6000, 24, 0.8),        # 4,800 synapses per post: longer than a stage
+    (3000, 600, 0.002),     # 6 synapses per post: a lane per post
+])
+def test_forward_product_paths_match_oracle(gpu, n_in, n_out, p):
+    # the scale gradient sums G over every post and step, so an error in the
+    # product shows in it directly
+    T = 20
+    spec = _fan_in_spec(n_in, n_out, p, T)
+    net, ref, target = _pair(gpu, spec, T)
+    loss, y, gs, gw = _mse(gpu, net, target, 10)
+    rloss, ry = ref.forward(target.astype(np.float64))
+    assert loss == pytest.approx(rloss, rel=1e-4)
+    assert np.abs(y.cpu().numpy() - ry).max() < 1e-3
+    rgs, rgw = ref.backward()
+    assert _rel_l2(gs.cpu().numpy(), rgs) < 1e-3
+    assert _cos(gw[0].cpu().numpy(), rgw[0]) > 0.9999
