@@ -404,6 +404,21 @@ def _differentiable(snn, torch, dev, steps=2000, K=100):
     # the transposed pre indices are 16-bit when every pre population has at most 65,536 neurons
     per_syn = 6 if max(spec["pops"][d["pre"]]["n"] for d in spec["projs"]) <= 65536 else 8
     fwd_gbs = nnz * per_syn * steps / (t_f * 1e-3) / 1e9
+    # the forward product alone (k_graded_spmv), L2 flushed before each launch
+    flush = _flush_buffers(torch, dev)
+    s = torch.cuda.current_stream()
+    times = []
+    for _ in range(12):
+        _flush_l2(flush)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(s)
+        net.launch_product()
+        e1.record(s)
+        e1.synchronize()
+        times.append(e0.elapsed_time(e1))
+    del flush
+    prod_us = statistics.median(times[2:]) * 1e3
+    prod_gbs = nnz * per_syn / (prod_us * 1e-6) / 1e9
     out = {"workload": f"graded HH: In 100 -> Mid 20,000 (+ recurrent) -> Out 100, p = 0.05, {steps} steps of 0.05 ms",
            "synapses": nnz, "checkpoint_every": K, "loss": loss,
            "forward_ms": t_f, "backward_ms": t_b, "adjoint_total_ms": t_f + t_b,
@@ -412,6 +427,8 @@ def _differentiable(snn, torch, dev, steps=2000, K=100):
            "gradients": 3 + nnz, "grad_scale": gs.cpu().tolist(),
            "forward_bytes_per_synapse": per_syn,
            "forward_synapse_stream_gbs": fwd_gbs, "forward_frac_hbm": fwd_gbs / hbm,
+           "product_kernel": {"kernel": "k_graded_spmv", "us": prod_us, "gbs": prod_gbs, "frac_hbm": prod_gbs / hbm,
+                              "bytes": nnz * per_syn, "l2": "flushed before each launch"},
            "finite": bool(torch.isfinite(gs).all() and all(torch.isfinite(g).all() for g in gw))}
     net.close()
     return out

@@ -469,6 +469,13 @@ snn_status snn_forward_record(snn_net* net, int64_t n_steps, int32_t checkpoint_
  * Synchronises `stream`. */
 snn_status snn_backward(snn_net* net, const float* dL_dy, float* grad_scale, float* const* grad_w, void* stream);
 
+/* Enqueues the graded forward product alone (Sec. 2's synaptic input of the
+ * graded form, G_q[j] = sum_i w_ij r_i over the compressed-row projections,
+ * from the current releases, into the network's G vector), for timing the
+ * kernel: the state does not advance.  SNN_ERR_STATE for a spiking
+ * network. */
+snn_status snn_graded_launch_product(snn_net* net, void* stream);
+
 /* ---- checkpoint / resume --------------------------------------------------
  * A snapshot holds the whole dynamic state: V, m, h, n, conductances, drive
  * currents, spike lists and lengths, all counters, the persistent engine's

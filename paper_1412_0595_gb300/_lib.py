@@ -94,6 +94,7 @@ def _load():
         "snn_proj_scale": [vp, i32, P(C.c_float)],
         "snn_proj_nnz": [vp, i32, P(i64)],
         "snn_proj_mode": [vp, i32, P(i32)],
+        "snn_graded_launch_product": [vp, vp],
         "snn_debug_propagate": [vp, i32, vp, i32, i32, vp],
         "snn_event_list": [vp, i32, vp, i32, i32, vp, vp, i64, P(i64), vp],
         "snn_csr_bernoulli_rows": [u64, u32, i64, i64, dbl, vp, P(i64), P(Allocator), vp],

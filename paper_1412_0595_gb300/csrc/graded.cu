@@ -364,10 +364,28 @@ __global__ void __launch_bounds__(kNeuronThreads) k_graded_reverse(const GradedA
 // dL/dV_i = local part + r'_i sum over outgoing rows of w * dL/dG (one warp per neuron).
 // One warp per pre-synaptic neuron; the dL/dG vector is gathered through L1
 // (it fits there, and a shared-memory copy would take the L1's space).
-__global__ void __launch_bounds__(kThreads) k_graded_gather(const GradedArgs a, const AdjArgs b) {
+// kShared: dL/dG of the step (total_posts floats) is first copied into shared
+// memory, as the forward product stages the releases, so the rows' random
+// reads of it cost bank conflicts instead of L1 / L2 round trips.
+template <bool kShared>
+__global__ void __launch_bounds__(kShared ? kStagedThreads : kThreads, kShared ? 1 : 4) k_graded_gather(const GradedArgs a,
+                                                                                                         const AdjArgs b) {
+    extern __shared__ __align__(16) float s_nu[];
+    const float* nu_all = b.nu_step;
+    if constexpr (kShared) {
+        const int n = (int)a.total_posts;
+        const int n4 = (reinterpret_cast<uintptr_t>(b.nu_step) & 15u) == 0 ? n / 4 : 0;
+        for (int i = threadIdx.x; i < n4; i += blockDim.x)
+            asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(tc::smem_u32(s_nu + 4 * i)),
+                         "l"(b.nu_step + 4 * i) : "memory");
+        for (int i = 4 * n4 + (int)threadIdx.x; i < n; i += blockDim.x) s_nu[i] = b.nu_step[i];
+        asm volatile("cp.async.wait_all;" ::: "memory");
+        __syncthreads();
+        nu_all = s_nu;
+    }
     const int lane = threadIdx.x & 31;
-    const int64_t warp = (int64_t)blockIdx.x * (kThreads / 32) + (threadIdx.x >> 5);
-    const int64_t warps = (int64_t)gridDim.x * (kThreads / 32);
+    const int64_t warp = (int64_t)blockIdx.x * (blockDim.x / 32) + (threadIdx.x >> 5);
+    const int64_t warps = (int64_t)gridDim.x * (blockDim.x / 32);
     for (int64_t w = warp; w < a.n_total; w += warps) {
         const int tile = (int)(w / kTile);
         const int pop = a.tile_pop[tile];
@@ -378,7 +396,7 @@ __global__ void __launch_bounds__(kThreads) k_graded_gather(const GradedArgs a, 
         float acc = 0.0f;
         for (int k = a.out_begin[pop]; k < a.out_begin[pop + 1]; ++k) {
             const GradProj& q = a.gprojs[a.out_list[k]];
-            const float* nu = b.nu_step + q.g_off;
+            const float* nu = nu_all + q.g_off;
             if (q.dense) {
                 // the neuron's row of the matrix against dL/dG of all posts
                 const float* row = q.w + (int64_t)local * q.n_post;
@@ -495,7 +513,9 @@ cudaError_t launch_graded_reverse(const GradedArgs& a, const AdjArgs& b, cudaStr
     k_graded_reverse<<<(a.n_total + kNeuronThreads - 1) / kNeuronThreads, kNeuronThreads, 0, s>>>(a, b);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    k_graded_gather<<<grid_warps(a.n_total), kThreads, 0, s>>>(a, b);
+    const size_t bytes = sizeof(float) * (size_t)a.total_posts;
+    if (bytes <= kStageMaxBytes) return launch_staged(k_graded_gather<true>, bytes, s, a, b);
+    k_graded_gather<false><<<grid_warps(a.n_total), kThreads, 0, s>>>(a, b);
     return cudaGetLastError();
 }
 

@@ -331,6 +331,14 @@ snn_status snn_set_weights(snn_net* net, int32_t proj, const float* w, int32_t o
     return SNN_OK;
 }
 
+snn_status snn_graded_launch_product(snn_net* net, void* stream) {
+    if (!net) return fail(SNN_ERR_INVALID_ARG, "net is NULL");
+    if (!net->graded) return fail(SNN_ERR_STATE, "not a graded network");
+    GradedArgs a = graded_args(net);
+    SNN_CK(launch_graded_spmv(a, (cudaStream_t)stream), "graded product");
+    return SNN_OK;
+}
+
 snn_status snn_forward_record(snn_net* net, int64_t n_steps, int32_t checkpoint_every, int32_t out_pop,
                               double tau_f, float* y_out, void* stream) {
     if (!net) return fail(SNN_ERR_INVALID_ARG, "net is NULL");

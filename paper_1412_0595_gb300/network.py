@@ -439,6 +439,10 @@ class GradedNetwork(Network):
         assert t.numel() == self.nnz(q)
         check(L.lib.snn_set_weights(self.h, int(q), t.data_ptr(), 1, _stream(stream)))
 
+    def launch_product(self, stream=None):
+        """Enqueues the forward product alone (timing; the state does not advance)."""
+        check(L.lib.snn_graded_launch_product(self.h, _stream(stream)))
+
     def forward_record(self, n_steps, out_pop=None, tau_f=5.0, checkpoint_every=100, stream=None):
         """Recorded run of n_steps from the creation state; returns the output
         filter y as a (n_steps, n_out) device tensor (y[t] = y(t + 1))."""
