@@ -281,40 +281,45 @@ __global__ void k_graded_release_init(const GradedArgs a) {
 // the step (lV includes the pre-synaptic gather of the later step), writes the
 // local part of the adjoint of the state before it, dL/dG per incoming
 // projection (per-step slice and time-contiguous copy) and dL/ds partials.
+// kS: the substeps per step when known at compile time (the recomputed
+// substep states then live in registers), 0 for the run-time count.
+template <int kS>
 __global__ void __launch_bounds__(kNeuronThreads) k_graded_reverse(const GradedArgs a, const AdjArgs b) {
     __shared__ double s_gs[kMaxGradedProjs];
     for (int k = threadIdx.x; k < a.n_gprojs; k += kNeuronThreads) s_gs[k] = 0.0;
     __syncthreads();
+    // a warp's 32 neurons lie in one tile of one population (the SoA length
+    // is a multiple of the tile), so pop is warp-uniform
     const int idx_t = blockIdx.x * kNeuronThreads + threadIdx.x;
-    bool active = idx_t < a.n_total;
-    int pop = 0, local = 0, idx = 0;
-    const DevPop* Pp = nullptr;
+    const int lane = threadIdx.x & 31;
+    const int tile = idx_t / kTile;
+    const int pop = a.tile_pop[tile];
+    const DevPop& P = a.pops[pop];
+    const int local = (tile - P.first_tile) * kTile + (idx_t % kTile);
+    const bool active = local < P.n;
+    const int idx = P.offset + local;
+    float aI = 0.0f, V0 = 0.0f;
     if (active) {
-        const int tile = idx_t / kTile;
-        pop = a.tile_pop[tile];
-        Pp = &a.pops[pop];
-        local = (tile - Pp->first_tile) * kTile + (idx_t % kTile);
-        active = local < Pp->n;
-        idx = Pp->offset + local;
-    }
-    if (active) {
-        const DevPop& P = *Pp;
         const size_t NT = (size_t)a.n_total;
-        const float V0 = b.st[idx], m0 = b.st[NT + idx], h0 = b.st[2 * NT + idx], n0 = b.st[3 * NT + idx];
+        V0 = b.st[idx];
+        const float m0 = b.st[NT + idx], h0 = b.st[2 * NT + idx], n0 = b.st[3 * NT + idx];
         const float ie = b.st[4 * NT + idx];
         float dIsyn_dV;
         const float isyn = graded_isyn(a, pop, local, V0, &dIsyn_dV);
         const float I_in = isyn + ie;
         const HHCell cell{P.gNa, P.ENa, P.gK, P.EK, P.gL, P.EL};
         // recompute the substep states (identical to the forward pass)
-        float Vs[kMaxSub + 1], ms[kMaxSub + 1], hs_[kMaxSub + 1], ns[kMaxSub + 1];
+        constexpr int kCap = kS > 0 ? kS : kMaxSub;
+        const int S = kS > 0 ? kS : a.n_sub;
+        float Vs[kCap + 1], ms[kCap + 1], hs_[kCap + 1], ns[kCap + 1];
         Vs[0] = V0; ms[0] = m0; hs_[0] = h0; ns[0] = n0;
-        const int S = a.n_sub;
-#pragma unroll 4
-        for (int s = 0; s < S; ++s) {
-            float V = Vs[s], m = ms[s], h = hs_[s], n = ns[s];
-            hh_substep(cell, a.hs, P.hs_over_C, I_in, V, m, h, n);
-            Vs[s + 1] = V; ms[s + 1] = m; hs_[s + 1] = h; ns[s + 1] = n;
+#pragma unroll
+        for (int s = 0; s < kCap; ++s) {
+            if (s < S) {
+                float V = Vs[s], m = ms[s], h = hs_[s], n = ns[s];
+                hh_substep(cell, a.hs, P.hs_over_C, I_in, V, m, h, n);
+                Vs[s + 1] = V; ms[s + 1] = m; hs_[s + 1] = h; ns[s + 1] = n;
+            }
         }
         float lV = b.lV[idx], lm = b.lm[idx], lh = b.lh[idx], ln = b.ln[idx];
         float ly_prev = 0.0f;
@@ -324,37 +329,47 @@ __global__ void __launch_bounds__(kNeuronThreads) k_graded_reverse(const GradedA
             lV += a.a_filter * ly;
             ly_prev = (1.0f - a.a_filter) * ly;
         }
-        float aI = 0.0f;
         const float c = P.hs_over_C;
-        for (int s = S - 1; s >= 0; --s) {
-            const float V = Vs[s], m = ms[s], h = hs_[s], n = ns[s];
-            const HHRates r = hh_rates(V);
-            const HHDerivs d = hh_rate_derivs(V, r);
-            const float m2 = m * m, m3 = m2 * m, n3 = n * n * n;
-            const float dI_dV = P.gNa * m3 * h + P.gK * n3 * n + P.gL;
-            const float dI_dm = 3.0f * P.gNa * m2 * h * (V - P.ENa);
-            const float dI_dh = P.gNa * m3 * (V - P.ENa);
-            const float dI_dn = 4.0f * P.gK * n3 * (V - P.EK);
-            const float nV = lV * (1.0f - c * dI_dV) + lm * a.hs * (d.am * (1.0f - m) - d.bm * m) +
-                             lh * a.hs * (d.ah * (1.0f - h) - d.bh * h) + ln * a.hs * (d.an * (1.0f - n) - d.bn * n);
-            const float nm = lV * (-c * dI_dm) + lm * (1.0f - a.hs * (r.am + r.bm));
-            const float nh = lV * (-c * dI_dh) + lh * (1.0f - a.hs * (r.ah + r.bh));
-            const float nn = lV * (-c * dI_dn) + ln * (1.0f - a.hs * (r.an + r.bn));
-            aI = fmaf(lV, c, aI);
-            lV = nV; lm = nm; lh = nh; ln = nn;
+#pragma unroll
+        for (int s = kCap - 1; s >= 0; --s) {
+            if (s < S) {
+                const float V = Vs[s], m = ms[s], h = hs_[s], n = ns[s];
+                const HHRates r = hh_rates(V);
+                const HHDerivs d = hh_rate_derivs(V, r);
+                const float m2 = m * m, m3 = m2 * m, n3 = n * n * n;
+                const float dI_dV = P.gNa * m3 * h + P.gK * n3 * n + P.gL;
+                const float dI_dm = 3.0f * P.gNa * m2 * h * (V - P.ENa);
+                const float dI_dh = P.gNa * m3 * (V - P.ENa);
+                const float dI_dn = 4.0f * P.gK * n3 * (V - P.EK);
+                const float nV = lV * (1.0f - c * dI_dV) + lm * a.hs * (d.am * (1.0f - m) - d.bm * m) +
+                                 lh * a.hs * (d.ah * (1.0f - h) - d.bh * h) + ln * a.hs * (d.an * (1.0f - n) - d.bn * n);
+                const float nm = lV * (-c * dI_dm) + lm * (1.0f - a.hs * (r.am + r.bm));
+                const float nh = lV * (-c * dI_dh) + lh * (1.0f - a.hs * (r.ah + r.bh));
+                const float nn = lV * (-c * dI_dn) + ln * (1.0f - a.hs * (r.an + r.bn));
+                aI = fmaf(lV, c, aI);
+                lV = nV; lm = nm; lh = nh; ln = nn;
+            }
         }
         b.lV_loc[idx] = fmaf(aI, dIsyn_dV, lV);
         b.lm[idx] = lm; b.lh[idx] = lh; b.ln[idx] = ln;
         if (pop == a.out_pop) b.ly[local] = ly_prev;
-        const int qb = a.in_begin[pop], qe = a.in_begin[pop + 1];
-        for (int k = qb; k < qe; ++k) {
-            const int qi = a.in_list[k];
-            const GradProj& q = a.gprojs[qi];
+    }
+    // dL/dG of the step and the scale gradients: the warp sums its neurons'
+    // contributions before one shared atomic per projection
+    const int qb = a.in_begin[pop], qe = a.in_begin[pop + 1];
+    for (int k = qb; k < qe; ++k) {
+        const int qi = a.in_list[k];
+        const GradProj& q = a.gprojs[qi];
+        double gs = 0.0;
+        if (active) {
             const float nu = aI * q.scale * (q.E - V0);
             b.nu_step[q.g_off + local] = nu;
             b.nu_km[(size_t)(q.g_off + local) * b.kp + b.tl] = nu;
-            atomicAdd(&s_gs[qi], (double)aI * (double)(q.E - V0) * (double)a.G[q.g_off + local]);
+            gs = (double)aI * (double)(q.E - V0) * (double)a.G[q.g_off + local];
         }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) gs += __shfl_xor_sync(0xffffffffu, gs, o);
+        if (lane == 0 && gs != 0.0) atomicAdd(&s_gs[qi], gs);
     }
     __syncthreads();
     for (int k = threadIdx.x; k < a.n_gprojs; k += kNeuronThreads)
@@ -510,7 +525,9 @@ cudaError_t launch_graded_release_init(const GradedArgs& a, cudaStream_t s) {
 }
 
 cudaError_t launch_graded_reverse(const GradedArgs& a, const AdjArgs& b, cudaStream_t s) {
-    k_graded_reverse<<<(a.n_total + kNeuronThreads - 1) / kNeuronThreads, kNeuronThreads, 0, s>>>(a, b);
+    const int grid = (a.n_total + kNeuronThreads - 1) / kNeuronThreads;
+    if (a.n_sub == 4) k_graded_reverse<4><<<grid, kNeuronThreads, 0, s>>>(a, b);
+    else k_graded_reverse<0><<<grid, kNeuronThreads, 0, s>>>(a, b);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     const size_t bytes = sizeof(float) * (size_t)a.total_posts;
