@@ -430,8 +430,12 @@ __global__ void __launch_bounds__(kShared ? kStagedThreads : kThreads, kShared ?
                 }
                 continue;
             }
-            for (int64_t e = q.row_ptr[local] + lane; e < q.row_ptr[local + 1]; e += 32)
-                acc = fmaf(q.w[e], nu[q.col[e]], acc);
+            const int64_t rb = q.row_ptr[local], re = q.row_ptr[local + 1];
+            if (q.col16) {
+                for (int64_t e = rb + lane; e < re; e += 32) acc = fmaf(q.w[e], nu[q.col16[e]], acc);
+            } else {
+                for (int64_t e = rb + lane; e < re; e += 32) acc = fmaf(q.w[e], nu[q.col[e]], acc);
+            }
         }
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);

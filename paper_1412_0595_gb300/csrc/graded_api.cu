@@ -86,6 +86,7 @@ snn_status upload_gprojs(snn_net* net) {
         d.g_off = P.g_off;
         d.row_ptr = P.row_ptr;
         d.col = P.col;
+        d.col16 = P.col16;
         d.w = P.w;
         d.csc_ptr = P.csc_ptr;
         d.csc_pre = P.csc_pre;
@@ -209,6 +210,15 @@ snn_status graded_setup(snn_net* net, cudaStream_t s) {
             SNN_CK(cudaMemcpyAsync(P.csc_w, cw.data(), cw.size() * sizeof(float), cudaMemcpyHostToDevice, s), "upload");
             SNN_CK(cudaMemcpyAsync(P.csc_perm, perm.data(), perm.size() * sizeof(int64_t), cudaMemcpyHostToDevice, s),
                    "upload");
+        }
+        // the adjoint gather streams the compressed rows: their post indices in
+        // 16 bits when the post population allows (6 instead of 8 bytes per synapse)
+        if (n_post <= 65536 && P.nnz) {
+            SNN_TRY(net_alloc(net, &P.col16, (size_t)P.nnz, "16-bit post indices"));
+            std::vector<uint16_t> c16(col.begin(), col.end());
+            SNN_CK(cudaMemcpyAsync(P.col16, c16.data(), c16.size() * sizeof(uint16_t), cudaMemcpyHostToDevice, s),
+                   "upload");
+            SNN_CK(cudaStreamSynchronize(s), "synchronize");      // c16 leaves scope
         }
         SNN_CK(cudaStreamSynchronize(s), "synchronize");
         P.g_off = g_off;

@@ -100,6 +100,7 @@ struct GradProj {
     int64_t g_off;                     // block of this projection in a step's G vector
     const int64_t* row_ptr;            // compressed rows (pre-major)
     const int32_t* col;
+    const uint16_t* col16;             // the post indices in 16 bits when the post population has at most 65,536 neurons, else null
     const float* w;
     const int64_t* csc_ptr;            // transposed copy (post-major)
     const int32_t* csc_pre;            // pre indices, 32-bit, or
@@ -224,6 +225,7 @@ struct ProjHost {
     uint16_t* csc_pre16 = nullptr;
     float* csc_w = nullptr;
     int64_t* csc_perm = nullptr;   // transposed position -> compressed-row position
+    uint16_t* col16 = nullptr;     // graded: 16-bit post indices of the compressed rows (small post populations)
     float* dpart = nullptr;        // graded dense: partial rows of the forward product
     unsigned* dcount = nullptr;    // graded dense: per post block ticket
     int32_t dchunks = 1;           // graded dense: pre-row ranges of the forward product
