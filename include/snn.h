@@ -94,6 +94,11 @@ enum {
                                   (snn_add_shared_dense): 0 CUDA cores, 1 tensor cores, 2 chosen
                                   on the device each step (default: tensor cores when at least
                                   3 % of the pre neurons of all instances spiked) */
+    SNN_OPT_GRADED_STORE = 12, /* snn_forward_record of a graded network: 1 (default) keeps every
+                                  step's start state, releases and G on the device when they take
+                                  at most a quarter of the free device memory, so that
+                                  snn_backward reads them instead of recomputing each checkpoint
+                                  segment (same results, bit for bit); 0 always recomputes */
     SNN_OPT_DENSE_GRAD = 10,   /* weight gradient of dense graded projections in snn_backward:
                                   0 CUDA cores (FP32 products), 1 tensor cores (default; three
                                   BF16 parts of each operand, six products, FP32 accumulation) */

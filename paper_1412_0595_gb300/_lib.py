@@ -22,7 +22,7 @@ FIELD = {"V": 0, "m": 1, "h": 2, "n": 3, "g0": 4, "g1": 5, "iext": 6, "isyn": 7,
          "spike_count": 10, "nan_count": 11, "neuron_spikes": 12}
 OPT = {"record_isyn": 0, "graph_steps": 1, "prop_blocks": 2, "chunk": 3, "spin_limit": 4, "engine": 5,
        "persist_steps": 6, "tiled": 7, "test_barrier_extra": 8, "cluster_ctas": 9, "dense_grad": 10,
-       "shared_dense": 11}
+       "shared_dense": 11, "graded_store": 12}
 
 
 class PopDesc(C.Structure):

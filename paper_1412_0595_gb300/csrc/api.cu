@@ -943,6 +943,7 @@ snn_status snn_get_option(const snn_net* net, int32_t option, int64_t* value) {
     case SNN_OPT_CLUSTER_CTAS: *value = net->cluster_size; break;
     case SNN_OPT_DENSE_GRAD: *value = net->dense_grad; break;
     case SNN_OPT_SHARED_DENSE: *value = net->shared_engine; break;
+    case SNN_OPT_GRADED_STORE: *value = net->graded_store; break;
     default: return fail(SNN_ERR_INVALID_ARG, "unknown option");
     }
     return SNN_OK;
@@ -991,6 +992,10 @@ snn_status snn_set_option(snn_net* net, int32_t option, int64_t value) {
     case SNN_OPT_DENSE_GRAD:
         if (value < 0 || value > 1) return fail(SNN_ERR_INVALID_ARG, "dense gradient: 0 CUDA cores, 1 tensor cores");
         net->dense_grad = (int32_t)value;
+        break;
+    case SNN_OPT_GRADED_STORE:
+        if (value < 0 || value > 1) return fail(SNN_ERR_INVALID_ARG, "graded store: 0 recompute, 1 store when it fits");
+        net->graded_store = (int32_t)value;
         break;
     case SNN_OPT_SHARED_DENSE:
         if (value < 0 || value > 2) return fail(SNN_ERR_INVALID_ARG, "shared dense: 0 CUDA cores, 1 tensor cores, 2 by density");

@@ -366,6 +366,23 @@ snn_status snn_forward_record(snn_net* net, int64_t n_steps, int32_t checkpoint_
         net->rec_ckpt_cap = (size_t)n_ckpt * 6 * NT;
     }
     SNN_TRY(ensure_segment_buffers(net, checkpoint_every, n_out));
+    // the whole trajectory (step-start states, releases, G) when it takes at
+    // most a quarter of the free device memory: snn_backward then reads it
+    // instead of recomputing every checkpoint segment
+    const size_t G = std::max<int64_t>(1, net->total_posts);
+    bool store = false;
+    if (net->graded_store) {
+        size_t free_b = 0, total_b = 0;
+        store = cudaMemGetInfo(&free_b, &total_b) == cudaSuccess &&
+                (double)n_steps * (double)(6 * NT + G) * sizeof(float) <= 0.25 * (double)free_b;
+        if (store && net->traj_cap_steps < (size_t)n_steps) {
+            store = net_alloc(net, &net->traj_state, (size_t)n_steps * 5 * NT, "trajectory states") == SNN_OK &&
+                    net_alloc(net, &net->traj_r, (size_t)n_steps * NT, "trajectory releases") == SNN_OK &&
+                    net_alloc(net, &net->traj_G, (size_t)n_steps * G, "trajectory conductances") == SNN_OK;
+            net->traj_cap_steps = store ? (size_t)n_steps : 0;
+        }
+    }
+    net->rec_stored = store;
     net->rec_T = n_steps;
     net->rec_K = checkpoint_every;
     net->rec_out_pop = out_pop;
@@ -377,14 +394,19 @@ snn_status snn_forward_record(snn_net* net, int64_t n_steps, int32_t checkpoint_
     a.y_out = y_out;
     SNN_TRY(graded_reset(net, s));
     for (int64_t t = 0; t < n_steps; ++t) {
-        if (t % checkpoint_every == 0) {
+        float* Gt = net->G;
+        if (store) {
+            a.rec_state = net->traj_state + (size_t)t * 5 * NT;
+            a.rec_r = net->traj_r + (size_t)t * NT;
+            Gt = net->traj_G + (size_t)t * G;
+        } else if (t % checkpoint_every == 0) {
             float* c = net->rec_ckpt + (size_t)(t / checkpoint_every) * 6 * NT;
             SNN_CK(cudaMemcpyAsync(c, net->V, 4 * NT * sizeof(float), cudaMemcpyDeviceToDevice, s), "checkpoint");
             SNN_CK(cudaMemcpyAsync(c + 4 * NT, net->iext, NT * sizeof(float), cudaMemcpyDeviceToDevice, s), "checkpoint");
             SNN_CK(cudaMemcpyAsync(c + 5 * NT, net->y, NT * sizeof(float), cudaMemcpyDeviceToDevice, s), "checkpoint");
         }
         a.t_rec = (int32_t)t;
-        SNN_CK(graded_one_step(net, a, net->G, t, s), "recorded step");
+        SNN_CK(graded_one_step(net, a, Gt, t, s), "recorded step");
     }
     net->g_t = n_steps;
     SNN_CK(cudaStreamSynchronize(s), "synchronize");
@@ -419,38 +441,43 @@ snn_status snn_backward(snn_net* net, const float* dL_dy, float* grad_scale, flo
     b.nu_km = net->nu_km;
     b.kp = kp;
     b.grad_scale = net->d_grad_scale;
-    b.r_seg = net->seg_r;
     const int64_t n_seg = (T + K - 1) / K;
+    const bool stored = net->rec_stored;
     for (int64_t seg = n_seg - 1; seg >= 0; --seg) {
         const int64_t t0 = seg * K;
         const int32_t L = (int32_t)std::min<int64_t>(K, T - t0);
-        // restore the checkpoint and recompute the segment, recording it
-        const float* c = net->rec_ckpt + (size_t)seg * 6 * NT;
-        SNN_CK(cudaMemcpyAsync(net->V, c, 4 * NT * sizeof(float), cudaMemcpyDeviceToDevice, s), "restore");
-        SNN_CK(cudaMemcpyAsync(net->iext, c + 4 * NT, NT * sizeof(float), cudaMemcpyDeviceToDevice, s), "restore");
-        SNN_CK(cudaMemcpyAsync(net->y, c + 5 * NT, NT * sizeof(float), cudaMemcpyDeviceToDevice, s), "restore");
+        // the segment's step-start states, releases and G: kept by the
+        // recorded forward, or recomputed from the segment's checkpoint
+        float* seg_state = stored ? net->traj_state + (size_t)t0 * 5 * NT : net->seg_state;
+        float* seg_r = stored ? net->traj_r + (size_t)t0 * NT : net->seg_r;
+        float* seg_G = stored ? net->traj_G + (size_t)t0 * G : net->seg_G;
+        b.r_seg = seg_r;
         GradedArgs a = graded_args(net);
-        // releases from the restored V, without resetting the filter
-        {
+        if (!stored) {
+            const float* c = net->rec_ckpt + (size_t)seg * 6 * NT;
+            SNN_CK(cudaMemcpyAsync(net->V, c, 4 * NT * sizeof(float), cudaMemcpyDeviceToDevice, s), "restore");
+            SNN_CK(cudaMemcpyAsync(net->iext, c + 4 * NT, NT * sizeof(float), cudaMemcpyDeviceToDevice, s), "restore");
+            SNN_CK(cudaMemcpyAsync(net->y, c + 5 * NT, NT * sizeof(float), cudaMemcpyDeviceToDevice, s), "restore");
+            // releases from the restored V, without resetting the filter
             GradedArgs ri = a;
             ri.out_pop = -1;
             SNN_CK(launch_graded_release_init(ri, s), "segment releases");
-        }
-        for (int32_t tl = 0; tl < L; ++tl) {
-            GradedArgs f = a;
-            f.rec_state = net->seg_state + (size_t)tl * 5 * NT;
-            f.rec_r = net->seg_r + (size_t)tl * NT;
-            f.t_rec = (int32_t)(t0 + tl);
-            SNN_CK(graded_one_step(net, f, net->seg_G + (size_t)tl * G, t0 + tl, s), "segment recompute");
+            for (int32_t tl = 0; tl < L; ++tl) {
+                GradedArgs f = a;
+                f.rec_state = seg_state + (size_t)tl * 5 * NT;
+                f.rec_r = seg_r + (size_t)tl * NT;
+                f.t_rec = (int32_t)(t0 + tl);
+                SNN_CK(graded_one_step(net, f, seg_G + (size_t)tl * G, t0 + tl, s), "segment recompute");
+            }
         }
         // reverse sweep over the segment
         for (int32_t tl = L - 1; tl >= 0; --tl) {
             GradedArgs r = a;
-            r.G = net->seg_G + (size_t)tl * G;
+            r.G = seg_G + (size_t)tl * G;
             r.dL_dy = dL_dy;
             r.t_rec = (int32_t)(t0 + tl);
-            b.st = net->seg_state + (size_t)tl * 5 * NT;
-            b.r_step = net->seg_r + (size_t)tl * NT;
+            b.st = seg_state + (size_t)tl * 5 * NT;
+            b.r_step = seg_r + (size_t)tl * NT;
             b.tl = tl;
             SNN_CK(launch_graded_reverse(r, b, s), "reverse step");
         }
@@ -458,7 +485,7 @@ snn_status snn_backward(snn_net* net, const float* dL_dy, float* grad_scale, flo
             const ProjHost& P = net->projs[q];
             if (P.d.layout == SNN_LAYOUT_DENSE) {
                 DenseGradArgs g{};
-                g.R = net->seg_r + net->pops[P.d.pre].offset;     // releases of the pre population
+                g.R = seg_r + net->pops[P.d.pre].offset;          // releases of the pre population
                 g.ldr = (int64_t)NT;
                 g.N = net->nu_km + (size_t)P.g_off * kp;           // dL/dG of the projection's posts
                 g.ldn = kp;

@@ -296,6 +296,12 @@ struct snn_net {
     // graded (differentiable) networks
     bool graded = false;
     bool graded_narrow = false;               // 16-bit transposed pre indices
+    int32_t graded_store = 1;                 // SNN_OPT_GRADED_STORE
+    bool rec_stored = false;                  // the last recorded forward kept every step (traj_*)
+    float* traj_state = nullptr;              // [T][5][n_total] step-start V, m, h, n, I_ext
+    float* traj_r = nullptr;                  // [T][n_total] releases used by each step
+    float* traj_G = nullptr;                  // [T][total_posts] G of each step
+    size_t traj_cap_steps = 0;
     snn::GradProj* d_gprojs = nullptr;
     int32_t* in_begin = nullptr;
     int32_t* in_list = nullptr;

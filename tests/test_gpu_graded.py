@@ -141,6 +141,26 @@ def test_checkpoint_interval_does_not_change_the_gradient(gpu):
             assert _rel_l2(gw[q], out[0][2][q]) < 1e-5
 
 
+@pytest.mark.parametrize("spec_fn", [I.config_graded_small, I.config_graded_dense_small])
+def test_stored_trajectory_gives_the_recomputed_gradients(gpu, spec_fn):
+    # the recorded forward keeps every step (SNN_OPT_GRADED_STORE 1) or only
+    # checkpoints whose segments the backward recomputes (0): the recompute is
+    # bit-identical, so are the states the adjoint reads
+    T = 300
+    spec = spec_fn(steps=T)
+    net, ref, target = _pair(gpu, spec, T)
+    out = []
+    for store in (0, 1):
+        net.set_option("graded_store", store)
+        l, y, gs, gw = _mse(gpu, net, target, 64)
+        out.append((l, y.cpu().numpy(), gs.cpu().numpy(), [g.cpu().numpy() for g in gw]))
+    (l0, y0, s0, w0), (l1, y1, s1, w1) = out
+    assert l0 == l1 and np.array_equal(y0, y1)
+    assert np.allclose(s0, s1, rtol=1e-6, atol=0)             # FP64 sums of FP32 terms in atomic order
+    for a, b in zip(w0, w1):
+        assert np.array_equal(a, b)
+
+
 def test_autograd_function_and_a_descent_step(gpu):
     # y from the autograd node, any torch loss on top; autograd's dL/dy
     # reaches the network's adjoint
