@@ -431,7 +431,11 @@ __global__ void __launch_bounds__(kShared ? kStagedThreads : kThreads, kShared ?
                 continue;
             }
             const int64_t rb = q.row_ptr[local], re = q.row_ptr[local + 1];
-            if (q.col16) {
+            if (kShared && q.col16) {
+                // 16-byte weight and 8-byte index loads of 4 synapses per lane,
+                // four 128-synapse blocks in flight, dL/dG from shared memory
+                acc += lane_dot16<true>(q.w, q.col16, nu, rb, re, lane);
+            } else if (q.col16) {
                 for (int64_t e = rb + lane; e < re; e += 32) acc = fmaf(q.w[e], nu[q.col16[e]], acc);
             } else {
                 for (int64_t e = rb + lane; e < re; e += 32) acc = fmaf(q.w[e], nu[q.col[e]], acc);

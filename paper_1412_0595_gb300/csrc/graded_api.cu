@@ -214,8 +214,12 @@ snn_status graded_setup(snn_net* net, cudaStream_t s) {
         // the adjoint gather streams the compressed rows: their post indices in
         // 16 bits when the post population allows (6 instead of 8 bytes per synapse)
         if (n_post <= 65536 && P.nnz) {
-            SNN_TRY(net_alloc(net, &P.col16, (size_t)P.nnz, "16-bit post indices"));
-            std::vector<uint16_t> c16(col.begin(), col.end());
+            // padded like the weights (a multiple of 4 plus 4), so 8-byte loads of
+            // four indices that start before a row's end stay inside the allocation
+            const size_t padded16 = (size_t)((P.nnz + 3) / 4 * 4 + 4);
+            SNN_TRY(net_alloc(net, &P.col16, padded16, "16-bit post indices"));
+            std::vector<uint16_t> c16(padded16, 0);
+            std::copy(col.begin(), col.end(), c16.begin());
             SNN_CK(cudaMemcpyAsync(P.col16, c16.data(), c16.size() * sizeof(uint16_t), cudaMemcpyHostToDevice, s),
                    "upload");
             SNN_CK(cudaStreamSynchronize(s), "synchronize");      // c16 leaves scope
