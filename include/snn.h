@@ -453,8 +453,10 @@ snn_status snn_set_weights(snn_net* net, int32_t proj, const float* w, int32_t o
  * and writes the output filter: y_out[t][k] = y_k(t + 1) (device, n_steps x
  * n_out floats, step-major, owned by the caller), where y follows the output
  * population's V with y += (dt / tau_f)(V - y), starting at V(0).  Any loss
- * L(y) is the caller's; snn_backward takes its gradient dL/dy.  Stores the
- * state every checkpoint_every steps (1..512) for snn_backward.
+ * L(y) is the caller's; snn_backward takes its gradient dL/dy.  Keeps, for
+ * snn_backward, every step's start state, releases and G when they fit
+ * (SNN_OPT_GRADED_STORE), else the state every checkpoint_every steps
+ * (1..512); checkpoint_every is also the adjoint's segment length.
  * Synchronises `stream`.  SNN_ERR_STATE for a spiking network;
  * SNN_ERR_INVALID_ARG for y_out == NULL or bad sizes. */
 snn_status snn_forward_record(snn_net* net, int64_t n_steps, int32_t checkpoint_every, int32_t out_pop,
@@ -466,7 +468,8 @@ snn_status snn_forward_record(snn_net* net, int64_t n_steps, int32_t checkpoint_
  * compressed-row order, or n_pre x n_post row-major for dense storage),
  * given dL_dy (device, n_steps x n_out floats in y_out's layout, read during
  * the call, owned by the caller), by the discrete adjoint of the recorded
- * steps: each checkpoint segment is recomputed, then swept in reverse
+ * steps: each segment's states are read from the kept trajectory or
+ * recomputed from its checkpoint (the same bits), then swept in reverse
  * (filter, substeps, synaptic current, pre-synaptic gather), and the weight
  * gradients of the segment are summed over its steps in one pass (for dense
  * storage a rank-K update, see snn_dense_grad_run and SNN_OPT_DENSE_GRAD).
