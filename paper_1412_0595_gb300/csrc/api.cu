@@ -254,10 +254,11 @@ int prop_blocks(snn_net* net) { return net->prop_blocks > 0 ? net->prop_blocks :
 // row kernel's global reductions stay in L2 and cost less than the staging.
 // Measured crossovers (100 spiking rows, caches flushed; bench_profiles.py
 // --tiled-crossover), by synapses of a row per 2048-post tile: on 524,288
-// posts and more, segments from 40 (p = 0.02 .. 0.2 at 1,000,000 posts:
-// 22-70 us against 27-80 us for the better of the other two), bulk-copied
-// pieces from 800 (p = 0.5: 90 against 147 us); on 131,072 to 524,287 posts
-// segments from 150 and pieces from 300; below, pieces from 256.
+// posts and more, segments from 16 (p = 0.01 .. 0.2 at 1,000,000 posts:
+// 16-66 us against 18-76 us for the better of the other two), bulk-copied
+// pieces from 800 (p = 0.5: 86 against 143 us); on 131,072 to 524,287 posts
+// segments from 96 (p = 0.05 at 300,000 posts: 20.5 against 24.6 us) and
+// pieces from 300; below, pieces from 256.
 // Mode of a compressed-row projection's propagation in the plain engine:
 // 0 row kernel, 1 post-tiled through bulk copies, 2 post-tiled segments
 // streamed by warps into the shared accumulator.
@@ -268,8 +269,8 @@ int32_t tiled_mode(const snn_net* net, const ProjHost& P) {
     const int32_t n_pre = net->pops[P.d.pre].d.n, n_post = net->pops[P.d.post].d.n;
     if (n_post < 8 * kPostTile || n_pre == 0) return 0;
     const double per_tile = (double)P.nnz / n_pre * kPostTile / n_post;
-    if (n_post >= 256 * kPostTile) return per_tile >= 800.0 ? 1 : per_tile >= 40.0 ? 2 : 0;
-    if (n_post >= 64 * kPostTile) return per_tile >= 300.0 ? 1 : per_tile >= 150.0 ? 2 : 0;
+    if (n_post >= 256 * kPostTile) return per_tile >= 800.0 ? 1 : per_tile >= 16.0 ? 2 : 0;
+    if (n_post >= 64 * kPostTile) return per_tile >= 300.0 ? 1 : per_tile >= 96.0 ? 2 : 0;
     return per_tile >= 256.0 ? 1 : 0;
 }
 
