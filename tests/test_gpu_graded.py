@@ -243,3 +243,25 @@ def test_forward_product_paths_match_oracle(gpu, n_in, n_out, p):
     rgs, rgw = ref.backward()
     assert _rel_l2(gs.cpu().numpy(), rgs) < 1e-3
     assert _cos(gw[0].cpu().numpy(), rgw[0]) > 0.9999
+
+
+def test_product_launch_leaves_the_state_and_rejects_spiking_networks(gpu):
+    # snn_graded_launch_product (the timing entry point of the forward
+    # product) advances nothing; a spiking network has no graded product
+    import paper_1412_0595_gb300 as snn
+    from paper_1412_0595_gb300 import _lib as L
+    from paper_1412_0595_gb300.network import _stream
+    spec = I.config_graded_small(steps=20)
+    net = gpu.GradedNetwork.from_spec(spec)
+    net.step(5)
+    before = [net.read_host(p, f).copy() for p in range(3) for f in ("V", "m", "h", "n")]
+    for _ in range(3):
+        net.launch_product()
+    net.sync()
+    after = [net.read_host(p, f) for p in range(3) for f in ("V", "m", "h", "n")]
+    assert all(np.array_equal(x, y) for x, y in zip(before, after))
+    assert net.t == 5
+    spiking = gpu.Network.from_spec(I.config_small(steps=10, n_hh=300))
+    with pytest.raises(snn.SNNError) as e:
+        L.check(L.lib.snn_graded_launch_product(spiking.h, _stream(None)))
+    assert e.value.name == "SNN_ERR_STATE"
